@@ -1,0 +1,369 @@
+"""Benchmark: time of one Gaussian RBF interpolation solve to relative residual
+1e-13 (GMRES(30) + RASM, cell-list truncated matvec) on a GB300.
+
+One step = the whole path on one problem: cell binning, subdomain lists and
+RASM factors, and the GMRES solve (every row of the hot path), inputs resident
+in HBM when the step starts. L2 is flushed (a 256 MB write) before every timed
+step; the step's working set (Krylov basis, subdomain inverses) is itself
+several times L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload lattice1024|lattice64|lattice7168] [--mode f64|mixed]
+
+With --gpus N > 1 (launched by torchrun) each rank solves its own replica of
+the problem ("replicas only": the problems are independent), times are the
+max over ranks, and value stays the time per solve.
+
+--impl reference times the CPU oracle (plain FP64 C, OpenMP) on the host
+cores on a bounded sample of the same workload and projects the full solve
+from the GPU run's operation counts (see cpu_baseline.sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_0909_5413_gb300 import workloads as W  # noqa: E402
+
+METRIC = "RBF solve time at 1e-13 rel. residual (GMRES+RASM)"
+UNIT = "ms"
+
+# Algorithmic FP64 flops of one in-cutoff pair in the FP64 matvec (FMA = 2):
+# dx, dy (2); r2 = dx*dx + dy*dy (3); t = r2 * s (1); exp(-t): rounding FMA +
+# subtract + two reduction FMAs + five polynomial FMAs + table multiply (18);
+# accumulate FMA (2).
+FLOPS_PER_PAIR_F64 = 26
+# FP64 peak for plain (non-tensor) arithmetic: 152 SMs x 2 FP64 FMA/clk x 2 flops
+# x 2.07 GHz (matches the 1.25 TFLOP/s nominal figure for GB300).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the FP64 matvec from ncu (profiles/), per kernel revision.
+MATVEC_F64_REV = "thread-per-target-v1"
+MATVEC_F64_TRAFFIC = {}   # {rev: bytes per launch at the bench workload}
+
+WORKLOADS = {
+    "lattice64": (W.config_small, "64x64 jittered lattice on [-1,1]^2 (N=4,096)"),
+    "lattice1024": (W.config_1m, "1024x1024 jittered lattice on [-1,1]^2 (N=1,048,576)"),
+    "lattice7168": (W.config_51m, "7168x7168 jittered lattice on [-1,1]^2 (N=51,380,224)"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lattice1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(name: str, p, mode: str) -> dict:
+    return {"workload": name, "description": WORKLOADS[name][1], "n_points": p.n,
+            "h_over_sigma": round(p.h / p.sigma, 6), "cutoff_sigmas": 8.6,
+            "rasm": "4x4 lattice-point cores + 1-point ring", "gmres_restart": 30, "rtol": 1e-13,
+            "precision": mode, "l2": "flushed (256 MB write) before each timed step",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(p, gpu_counts: dict | None, sample_steps: int = 6) -> dict:
+    """Time the CPU oracle on the full workload: setup, one matvec, one RASM
+    apply and a short GMRES run (sample_steps Arnoldi steps); project a full
+    solve with the GPU solve's counts (iterations, cycles)."""
+    from oracle import oracle as O
+
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    t0 = time.perf_counter()
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pr.matvec(p.f)
+    t_mv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pr.rasm_apply(p.f)
+    t_ap = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, info = pr.solve(p.f, max_iters=sample_steps)
+    t_s = time.perf_counter() - t0
+    # the sample ran: 2 true-residual matvecs, sample_steps x (apply + matvec + ortho), 1 final apply
+    t_ortho = max(0.0, (t_s - (sample_steps + 2) * t_mv - (sample_steps + 1) * t_ap) / sample_steps)
+    iters = gpu_counts["iters"] if gpu_counts else sample_steps
+    cycles = gpu_counts["restarts"] if gpu_counts else 1
+    proj = t_setup + (iters + cycles + 1) * t_mv + (iters + cycles) * t_ap + iters * t_ortho
+    return {"value": proj * 1e3, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"full workload N={p.n}: oracle setup ({t_setup:.2f} s), one FP64 matvec ({t_mv:.3f} s), "
+                       f"one RASM apply ({t_ap:.3f} s), {sample_steps} GMRES steps ({t_s:.2f} s) timed; "
+                       f"projected to {iters} steps / {cycles} cycles"),
+            "measured_s": round(t_setup + t_mv + t_ap + t_s, 3)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    name = args.workload
+    p = WORKLOADS[name][0]()
+    # iteration counts of the oracle's own solve on the small case scale to
+    # this workload only through the GPU run; without a GPU run here, use the
+    # oracle's own short-sample count projected to its measured convergence
+    # rate on the same lattice family (iterations do not depend on N, Sec. 3.2).
+    from oracle import oracle as O
+    small = W.lattice_problem(64, p.h / p.sigma, seed=p.seed)
+    prs = O.Problem(small.xy, small.sigma, small.cutoff, small.x0, small.x0, small.core_size, small.overlap)
+    _, sinfo = prs.solve(small.f)
+    counts = {"iters": sinfo.iters, "restarts": sinfo.restarts}
+    times = []
+    cb = None
+    for step in range(args.warmup + args.steps):
+        cb = oracle_sample(p, counts)
+        if step >= args.warmup:
+            times.append(cb["value"])
+    v = statistics.mean(times)
+    cb["value"] = v
+    cb["sample"] += f"; step count taken from the oracle's full solve of the 64x64 lattice ({sinfo.iters} steps)"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(name, p, "f64"), "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- GPU path
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_0909_5413_gb300 import rbf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    name = args.workload
+    p = WORKLOADS[name][0]()
+    mode = args.mode
+    cfg = rbf.config_for(p, mixed=(mode == "mixed"), factor_precision=rbf.RBF_FP32 if mode == "mixed" else rbf.RBF_FP64)
+    xy = torch.from_numpy(p.xy).cuda()
+    f = torch.from_numpy(p.f).cuda()
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ctx = rbf.Context(local)
+    h = ctx.handle
+
+    def step(c):
+        w.zero_()
+        ctx.bin(xy, c)
+        ctx.rasm_setup(c)
+        st, info = ctx.solve(f, w, c, check=False)
+        return st, info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(cfg)
+    torch.cuda.synchronize()
+    rbf.rbf_profile_enable(h, True)
+    for k in range(6):
+        rbf.rbf_profile_read(h, k)   # discard warm-up records
+    launches0 = ctx.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, infos, stats = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, info = step(cfg)
+        e1.record()
+        barrier()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info.as_dict())
+        stats.append(st)
+    clk = clocks.stop()
+    launches = ctx.launches - launches0
+    prof = {k: rbf.rbf_profile_read(h, k) for k in range(6)}
+    rbf.rbf_profile_enable(h, False)
+    ms = statistics.mean(times)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = infos[-1]
+    ok = all(s == 0 for s in stats) and info["relres"] <= 1e-13
+
+    # dominant kernel: the truncated matvec of the timed precision
+    pairs = rbf.rbf_count_neighbors(h)
+    if mode == "f64":
+        n_mv, t_mv = prof[rbf.RBF_PROF_MATVEC_F64]
+    else:
+        n_mv, t_mv = prof[rbf.RBF_PROF_MATVEC_F32]
+    roofline = None
+    if n_mv:
+        avg_s = t_mv / n_mv / 1e3
+        if mode == "f64":
+            achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
+            roofline = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                        "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV),
+                        "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
+                        "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR_F64,
+                        "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
+                        "pairs_per_s": pairs / avg_s}
+        else:
+            roofline = {"kernel": "k_matvec_f32", "bound": "alu", "achieved": pairs / avg_s / 1e12, "peak": None,
+                        "unit": "Tpairs/s", "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3,
+                        "launches": n_mv}
+    breakdown = {nm: {"launches": prof[k][0], "ms": round(prof[k][1], 3)} for nm, k in
+                 (("matvec_f64", 0), ("matvec_f32", 1), ("rasm_apply", 2), ("orthogonalisation", 3),
+                  ("rasm_setup", 4), ("binning", 5))}
+
+    # the other precision, for the "mixed vs FP64" comparison
+    extra = None
+    if not args.no_extra:
+        other = "mixed" if mode == "f64" else "f64"
+        c2 = rbf.config_for(p, mixed=(other == "mixed"),
+                            factor_precision=rbf.RBF_FP32 if other == "mixed" else rbf.RBF_FP64)
+        step(c2)
+        ts, inf2 = [], None
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st2, i2 = step(c2)
+            e1.record()
+            barrier()
+            ts.append(e0.elapsed_time(e1))
+            inf2 = i2.as_dict()
+        extra = {"precision": other, "ms_per_step": statistics.mean(ts), "status": st2, **inf2}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        xy_h = torch.from_numpy(p.xy.copy()).pin_memory()
+        f_h = torch.from_numpy(p.f.copy()).pin_memory()
+        w_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+        ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False)
+        te = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False)
+            e1.record()
+            barrier()
+            te.append(e0.elapsed_time(e1))
+        e2e = {"value": statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": xy_h.numel() * 8 + f_h.numel() * 8,
+               "d2h_bytes_per_step": w_h.numel() * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_sample(p, info)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if mode == "f64" else "f32-inner/f64-outer", "data": "synthetic",
+               "config": workload_config(name, p, mode), "ok": ok, "solve": info,
+               "step_ms": [round(t, 3) for t in times], "roofline": roofline, "breakdown_ms": breakdown,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "other_precision": extra}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

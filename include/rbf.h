@@ -1,0 +1,198 @@
+/*
+ * rbf.h -- C ABI of the GB300 Gaussian RBF interpolation library (librbf.so).
+ *
+ * The library solves the interpolation system of Eq. rbf2 with a Gaussian
+ * basis and no polynomial block (the Gaussian is positive definite, Sec. 2.1):
+ *
+ *     sum_j w_j k(|x_i - x_j|^2) = f_i,   k(r2) = exp(-r2 / (2 sigma^2))
+ *
+ * (optionally times 1/(2 pi sigma^2), the normalised form of Sec. 2.3), with
+ * entries of pairs farther apart than the cutoff r_c dropped (Sec. 2.3), by
+ * GMRES preconditioned with the restricted additive Schwarz method of
+ * Eq. rasm over small overlapping box subdomains (Sec. 2.2 - 2.4).
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library reads or writes them only in stream order on `stream`.
+ *    Pointers named *_host are host pointers owned by the caller.
+ *  - Point arrays are AoS FP64 pairs (x0, y0, x1, y1, ...); vectors are FP64
+ *    and indexed in the caller's point order ("user order") unless a call
+ *    says otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Every call returns an rbf_status; nothing aborts, traps or exits.
+ *    rbf_last_error() gives a human-readable detail of the last failure.
+ *  - The context owns every internal device buffer (sorted points, index
+ *    lists, factors, Krylov basis) until rbf_destroy() or the next rbf_bin().
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef RBF_H
+#define RBF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBF_OK = 0,
+    RBF_ERR_INVALID_ARG = 1,          /* bad pointer, size or parameter */
+    RBF_ERR_OOM = 2,                  /* a device allocation failed */
+    RBF_ERR_CUDA = 3,                 /* a CUDA runtime call failed (see rbf_last_error) */
+    RBF_ERR_NOT_SPD = 4,              /* a subdomain matrix had a pivot <= 0 */
+    RBF_ERR_SUBDOMAIN_TOO_LARGE = 5,  /* an overlap list exceeds max_sub_points */
+    RBF_ERR_NOT_CONVERGED = 6,        /* tolerance not reached within max_iters */
+    RBF_ERR_TIMEOUT = 7,              /* a bounded device wait gave up */
+    RBF_ERR_STATE = 8                 /* call out of order (e.g. apply before setup) */
+} rbf_status;
+
+enum { RBF_FP64 = 0, RBF_FP32 = 1 };
+
+typedef struct rbf_ctx rbf_ctx;
+typedef void* rbf_stream;
+
+/* Kernel and binning parameters (Sec. 2.3, Sec. 3.1). */
+typedef struct {
+    double sigma;      /* Gaussian width sigma > 0 */
+    double cutoff;     /* r_c > 0; pairs with r2 > r_c^2 are dropped */
+    double cell_size;  /* cell side c of the cell list; <= 0 selects c = r_c */
+    int normalized;    /* 1: multiply the kernel by 1/(2 pi sigma^2) (Sec. 2.3) */
+} rbf_params;
+
+/* Subdomain boxes (Sec. 2.2, Sec. 3.1): core box (bx, by) covers
+ * [x0 + bx B, x0 + (bx+1) B) x [y0 + by B, y0 + (by+1) B) (clamped at the
+ * edges); its overlap box adds `overlap` on every side (half-open). */
+typedef struct {
+    double x0, y0;        /* box origin */
+    double core_size;     /* B > 0 */
+    double overlap;       /* delta >= 0 */
+    int max_sub_points;   /* cap on an overlap list, 1..64 (0 = 64) */
+    int precision;        /* storage of the subdomain inverses: RBF_FP64 or RBF_FP32 */
+} rbf_rasm_params;
+
+/* GMRES settings (Sec. 2.2, Sec. 3.1: GMRES with RASM, rtol 1e-13). */
+typedef struct {
+    double rtol;          /* stop when ||f - A w||_2 / ||f||_2 <= rtol (true residual) */
+    int restart;          /* m of GMRES(m), 1..32 (0 = 30) */
+    int max_iters;        /* total Arnoldi steps (inner steps summed) (0 = 10000) */
+    int mixed;            /* 1: FP32 inner GMRES + FP64 iterative refinement */
+    int max_refine;       /* mixed only: outer refinement steps (0 = 40) */
+    double inner_rtol;    /* mixed only: relative tolerance of each inner solve (0 = 1e-5) */
+} rbf_solve_params;
+
+typedef struct {
+    int iters;            /* Arnoldi steps taken (all cycles, all refinements) */
+    int restarts;         /* GMRES cycles completed */
+    int refinements;      /* outer FP64 refinement steps (mixed), 0 otherwise */
+    double relres;        /* final true relative residual, FP64 matvec */
+    double relres_est;    /* last GMRES residual estimate |g_{j+1}| / ||f|| */
+    int matvecs;          /* FP64 matvecs + FP32 matvecs */
+    int applies;          /* preconditioner applications */
+} rbf_solve_info;
+
+/* Create a context on CUDA device `device` (makes it current). */
+rbf_status rbf_create(rbf_ctx** out, int device);
+/* Release every buffer the context owns. NULL is a no-op. */
+void rbf_destroy(rbf_ctx* ctx);
+
+/* Cell-list binning (the matrix-free matvec's data structure, Sec. 2.3):
+ * bounding box; cell (cx, cy) = floor((x - xmin) / c), clamped to the grid,
+ * with ncx = floor((xmax - xmin) / c) + 1; stable sort of the points by cell
+ * id cy*ncx + cx (ties keep the user order). Copies xy_dev (n x 2 FP64) into
+ * the context in cell order. Synchronises `stream` once (grid size).
+ * Invalidates any previous RASM setup. Errors: INVALID_ARG for n < 1 or
+ * sigma, cutoff <= 0, or a grid over 2^28 cells. */
+rbf_status rbf_bin(rbf_ctx* ctx, const double* xy_dev, int64_t n, const rbf_params* params, rbf_stream stream);
+
+/* y = A~ w (Sec. 2.3 truncated Gaussian matvec, matrix-free), vectors of n
+ * FP64 in user order. precision RBF_FP64 evaluates every pair in FP64;
+ * RBF_FP32 evaluates in FP32 on cell-local coordinates (inner solves of the
+ * mixed form) and returns the result widened to FP64. Needs rbf_bin. */
+rbf_status rbf_matvec(rbf_ctx* ctx, const double* w_dev, double* y_dev, int precision, rbf_stream stream);
+
+/* RASM setup (Sec. 2.2, Eq. rasm; Sec. 2.4): builds core and overlap index
+ * lists of every box, forms A_i = R_i A~ R_i^T over each overlap list and
+ * factors it (Cholesky); stores the core rows of A_i^{-1}. Synchronises
+ * `stream`. Errors: SUBDOMAIN_TOO_LARGE if an overlap list exceeds
+ * max_sub_points, NOT_SPD on a pivot <= 0, STATE without rbf_bin. */
+rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* params, rbf_stream stream);
+
+/* z = M^{-1} r = sum_i ~R_i^T A_i^{-1} R_i r (Eq. rasm), n FP64 in user
+ * order. Errors: STATE without rbf_rasm_setup. */
+rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_stream stream);
+
+/* Solve A~ w = f by right-preconditioned restarted GMRES with RASM (Sec. 2.2,
+ * Sec. 3.1). w_dev holds the initial guess on entry (zeros for none) and the
+ * solution on return, so a later call continues from it. info (host,
+ * optional) is filled. Synchronises `stream`. Returns NOT_CONVERGED (with the
+ * best w) if rtol is not met within max_iters. Needs rbf_rasm_setup. */
+rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* params,
+                     rbf_solve_info* info, rbf_stream stream);
+
+/* End-to-end call on host buffers: copies xy_host (n x 2) and f_host to the
+ * device, runs rbf_bin, rbf_rasm_setup and rbf_solve from w = 0, and copies w
+ * back into w_host. Host buffers should be pinned for full copy speed. */
+rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const double* f_host, double* w_host,
+                                int64_t n, const rbf_params* params, const rbf_rasm_params* rasm,
+                                const rbf_solve_params* solve, rbf_solve_info* info, rbf_stream stream);
+
+/* ---- parity / inspection getters (synchronous; device outputs caller-owned) ---- */
+
+/* Grid after rbf_bin: cells per axis and bounding box {xmin, ymin, xmax, ymax} (host). */
+rbf_status rbf_get_grid(rbf_ctx* ctx, int64_t* ncx, int64_t* ncy, double* bbox_host);
+/* perm_dev[p] = user index of the p-th point in cell order (n int32);
+ * cell_start_dev[c] = first position of cell c (ncx*ncy + 1 int32). */
+rbf_status rbf_get_bins(rbf_ctx* ctx, int32_t* perm_dev, int32_t* cell_start_dev, rbf_stream stream);
+/* Subdomain counts after rbf_rasm_setup (host outputs). */
+rbf_status rbf_get_subdomain_sizes(rbf_ctx* ctx, int64_t* nbx, int64_t* nby, int64_t* core_total,
+                                   int64_t* overlap_total);
+/* Core and overlap lists, CSR over subdomains s = by*nbx + bx (ptr arrays of
+ * nsub + 1 int32), entries are user indices ascending within each list. */
+rbf_status rbf_get_subdomains(rbf_ctx* ctx, int32_t* core_ptr_dev, int32_t* core_idx_dev, int32_t* ov_ptr_dev,
+                              int32_t* ov_idx_dev, rbf_stream stream);
+/* Total number of (i, j) pairs with r2 <= r_c^2 (i = j included), host output. */
+rbf_status rbf_count_neighbors(rbf_ctx* ctx, int64_t* total, rbf_stream stream);
+/* Neighbour lists, CSR over targets in user order (ptr: n + 1 int64; idx:
+ * `capacity` int32), each row the user indices j with r2_ij <= r_c^2,
+ * ascending. INVALID_ARG if capacity is below the total. */
+rbf_status rbf_get_neighbors(rbf_ctx* ctx, int64_t* ptr_dev, int32_t* idx_dev, int64_t capacity,
+                             rbf_stream stream);
+
+/* ---- profiling and diagnostics ---- */
+
+/* Kernel classes timed by the built-in profiler. */
+enum {
+    RBF_PROF_MATVEC_F64 = 0,   /* FP64 truncated matvec launches */
+    RBF_PROF_MATVEC_F32 = 1,   /* FP32 truncated matvec launches */
+    RBF_PROF_RASM_APPLY = 2,   /* subdomain GEMV apply launches */
+    RBF_PROF_ORTHO = 3,        /* one Arnoldi orthogonalisation (three passes over V + reductions) */
+    RBF_PROF_RASM_SETUP = 4,   /* subdomain factor/inverse launch */
+    RBF_PROF_BIN = 5,          /* the whole binning sequence */
+    RBF_PROF_COUNT = 6
+};
+/* enable != 0: record a CUDA event pair on the launching stream around every
+ * launch of the classes above (a fixed cost of two event records each). */
+rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable);
+/* Synchronises the recorded events and returns, for kernel class `kernel`,
+ * the number of recorded launches and their summed device time; clears that
+ * class's record. */
+rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double* total_ms);
+/* out[i] = exp(-t[i]) for n FP64 values on the device: variant 0 is the
+ * library's own table-driven exp used by the FP64 matvec, variant 1 CUDA's
+ * exp(); for accuracy checks of the former against the latter. */
+rbf_status rbf_debug_exp(rbf_ctx* ctx, const double* t_dev, double* out_dev, int64_t n, int variant,
+                         rbf_stream stream);
+
+/* ---- diagnostics ---- */
+const char* rbf_status_string(rbf_status status);
+const char* rbf_last_error(rbf_ctx* ctx);
+/* Number of kernels this context has launched so far. */
+uint64_t rbf_launch_count(rbf_ctx* ctx);
+/* Device bytes the context currently holds. */
+int64_t rbf_device_bytes(rbf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBF_H */

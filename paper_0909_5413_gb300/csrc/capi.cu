@@ -1,0 +1,457 @@
+// capi.cu -- the extern "C" entry points declared in include/rbf.h, plus the
+// context's allocation and error bookkeeping.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace rbf {
+
+rbf_status fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+rbf_status cuda_fail(rbf_ctx* ctx, cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, RBF_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    }
+    return fail(ctx, RBF_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void release(rbf_ctx* ctx, void* p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < ctx->owned.size(); ++i) {
+        if (ctx->owned[i].first == p) {
+            ctx->dev_bytes -= (int64_t)ctx->owned[i].second;
+            ctx->owned.erase(ctx->owned.begin() + (long)i);
+            break;
+        }
+    }
+    cudaFree(p);
+}
+
+template <class T>
+rbf_status ensure(rbf_ctx* ctx, DevArray<T>& a, size_t count)
+{
+    if (count == 0) count = 1;
+    if (a.p && a.count >= count) return RBF_OK;
+    release(ctx, a.p);
+    a.p = nullptr;
+    a.count = 0;
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, RBF_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->owned.emplace_back(p, bytes);
+    ctx->dev_bytes += (int64_t)bytes;
+    a.p = (T*)p;
+    a.count = count;
+    return RBF_OK;
+}
+
+template rbf_status ensure<int32_t>(rbf_ctx*, DevArray<int32_t>&, size_t);
+template rbf_status ensure<int64_t>(rbf_ctx*, DevArray<int64_t>&, size_t);
+template rbf_status ensure<double>(rbf_ctx*, DevArray<double>&, size_t);
+template rbf_status ensure<float>(rbf_ctx*, DevArray<float>&, size_t);
+template rbf_status ensure<GmresDev>(rbf_ctx*, DevArray<GmresDev>&, size_t);
+
+constexpr int64_t kMaxProfPairs = 1 << 16;
+
+rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st)
+{
+    if (!ctx->prof) return RBF_OK;
+    rbf_prof_slot& s = ctx->prof_slots[id];
+    if (s.used >= kMaxProfPairs) return RBF_OK;
+    while ((int64_t)s.ev.size() < 2 * (s.used + 1)) {
+        cudaEvent_t e;
+        RBF_CUDA(ctx, cudaEventCreate(&e));
+        s.ev.push_back(e);
+    }
+    RBF_CUDA(ctx, cudaEventRecord(s.ev[2 * s.used], st));
+    return RBF_OK;
+}
+
+rbf_status prof_end(rbf_ctx* ctx, int id, cudaStream_t st)
+{
+    if (!ctx->prof) return RBF_OK;
+    rbf_prof_slot& s = ctx->prof_slots[id];
+    if (s.used >= kMaxProfPairs) return RBF_OK;
+    RBF_CUDA(ctx, cudaEventRecord(s.ev[2 * s.used + 1], st));
+    s.used++;
+    return RBF_OK;
+}
+
+// 2^(j/64), 64 / ln 2 and a two-part ln 2 / 64, evaluated in long double.
+ExpConsts make_exp_consts()
+{
+    ExpConsts c;
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    c.inv_l = (double)(64.0L / ln2);
+    double l = (double)(ln2 / 64.0L);
+    uint64_t bits;
+    std::memcpy(&bits, &l, sizeof(bits));
+    bits &= ~((uint64_t(1) << 21) - 1);   // keep 32 significant bits
+    std::memcpy(&c.l_hi, &bits, sizeof(bits));
+    c.l_lo = (double)(ln2 / 64.0L - (long double)c.l_hi);
+    for (int j = 0; j < 64; ++j) c.tab[j] = (double)exp2l((long double)j / 64.0L);
+    return c;
+}
+
+namespace {
+
+__global__ void k_debug_exp(const double* __restrict__ t, double* __restrict__ out, int64_t n, int variant,
+                            ExpConsts ec)
+{
+    __shared__ double tab[64];
+    if (threadIdx.x < 64) tab[threadIdx.x] = ec.tab[threadIdx.x];
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = variant == 0 ? exp_neg(t[i], tab, ec.inv_l, ec.l_hi, ec.l_lo) : exp(-t[i]);
+}
+
+}  // namespace
+
+}  // namespace rbf
+
+using namespace rbf;
+
+static cudaStream_t S(rbf_stream s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+const char* rbf_status_string(rbf_status s)
+{
+    switch (s) {
+    case RBF_OK: return "ok";
+    case RBF_ERR_INVALID_ARG: return "invalid argument";
+    case RBF_ERR_OOM: return "out of device memory";
+    case RBF_ERR_CUDA: return "CUDA error";
+    case RBF_ERR_NOT_SPD: return "subdomain matrix not positive definite";
+    case RBF_ERR_SUBDOMAIN_TOO_LARGE: return "subdomain overlap list too large";
+    case RBF_ERR_NOT_CONVERGED: return "not converged";
+    case RBF_ERR_TIMEOUT: return "device wait timed out";
+    case RBF_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* rbf_last_error(rbf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t rbf_launch_count(rbf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t rbf_device_bytes(rbf_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+rbf_status rbf_create(rbf_ctx** out, int device)
+{
+    if (!out) return RBF_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return RBF_ERR_INVALID_ARG;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return RBF_ERR_CUDA;
+    rbf_ctx* ctx = new rbf_ctx();
+    ctx->device = device;
+    ctx->expc = make_exp_consts();
+    e = cudaMallocHost(&ctx->gm_host, sizeof(GmresDev));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return RBF_ERR_OOM;
+    }
+    *out = ctx;
+    return RBF_OK;
+}
+
+void rbf_destroy(rbf_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (auto& a : ctx->owned) cudaFree(a.first);
+    ctx->owned.clear();
+    for (auto& s : ctx->prof_slots)
+        for (cudaEvent_t e : s.ev) cudaEventDestroy(e);
+    if (ctx->gm_host) cudaFreeHost(ctx->gm_host);
+    delete ctx;
+}
+
+rbf_status rbf_bin(rbf_ctx* ctx, const double* xy_dev, int64_t n, const rbf_params* p, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!xy_dev || !p || n < 1 || n > (int64_t)0x7fffffff - 1)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: need xy, params and 1 <= n < 2^31 (n = %lld)", (long long)n);
+    if (!(p->sigma > 0.0) || !(p->cutoff > 0.0) || !std::isfinite(p->sigma))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: sigma and cutoff must be positive");
+    if (((uintptr_t)xy_dev) % 8 != 0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: xy must be 8-byte aligned");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->binned = false;
+    ctx->rasm_ready = false;
+    ctx->n = n;
+    ctx->sigma = p->sigma;
+    ctx->rc = p->cutoff;
+    ctx->rc2 = p->cutoff * p->cutoff;
+    ctx->cell = (p->cell_size > 0.0) ? p->cell_size : p->cutoff;
+    ctx->s = 1.0 / (2.0 * p->sigma * p->sigma);
+    ctx->normalized = p->normalized ? 1 : 0;
+    ctx->knorm = p->normalized ? 1.0 / (2.0 * M_PI * p->sigma * p->sigma) : 1.0;
+    double k = std::ceil(ctx->rc / ctx->cell);
+    if (!(k >= 1.0) || k > 64.0)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: cutoff / cell_size = %g gives a stencil outside 1..64", k);
+    ctx->kst = (int)k;
+    RBF_CHECK(bin_points(ctx, xy_dev, S(stream)));
+    ctx->binned = true;
+    return RBF_OK;
+}
+
+rbf_status rbf_matvec(rbf_ctx* ctx, const double* w_dev, double* y_dev, int precision, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_matvec: call rbf_bin first");
+    if (!w_dev || !y_dev) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_matvec: null vector");
+    if (precision != RBF_FP64 && precision != RBF_FP32)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_matvec: precision must be RBF_FP64 or RBF_FP32");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(ensure(ctx, ctx->vec_a, ctx->n));
+    RBF_CHECK(ensure(ctx, ctx->vec_b, ctx->n));
+    RBF_CHECK(permute_to_sorted(ctx, w_dev, ctx->vec_a.p, S(stream)));
+    if (precision == RBF_FP64)
+        RBF_CHECK(matvec_sorted_f64(ctx, ctx->vec_a.p, ctx->vec_b.p, S(stream)));
+    else
+        RBF_CHECK(matvec_sorted_f32(ctx, ctx->vec_a.p, ctx->vec_b.p, S(stream)));
+    return permute_to_user(ctx, ctx->vec_b.p, y_dev, S(stream));
+}
+
+rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* p, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_rasm_setup: call rbf_bin first");
+    if (!p || !(p->core_size > 0.0) || !(p->overlap >= 0.0) || !std::isfinite(p->x0) || !std::isfinite(p->y0))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: need core_size > 0, overlap >= 0");
+    int cap = p->max_sub_points > 0 ? p->max_sub_points : kMaxSub;
+    if (cap > kMaxSub) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: max_sub_points > %d", kMaxSub);
+    if (p->precision != RBF_FP64 && p->precision != RBF_FP32)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: precision must be RBF_FP64 or RBF_FP32");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->rasm_ready = false;
+    ctx->x0 = p->x0;
+    ctx->y0 = p->y0;
+    ctx->B = p->core_size;
+    ctx->delta = p->overlap;
+    ctx->rasm_precision = p->precision;
+    double fx = std::floor((ctx->bbox[2] - ctx->x0) / ctx->B), fy = std::floor((ctx->bbox[3] - ctx->y0) / ctx->B);
+    if (!(fx < 1.0e9) || !(fy < 1.0e9)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes");
+    ctx->nbx = fx < 0.0 ? 1 : (int64_t)fx + 1;
+    ctx->nby = fy < 0.0 ? 1 : (int64_t)fy + 1;
+    ctx->nsub = ctx->nbx * ctx->nby;
+    if (ctx->nsub > ((int64_t)1 << 30)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes");
+    RBF_CHECK(build_subdomains(ctx, S(stream)));
+    if (ctx->max_ov > cap)
+        return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE, "rbf_rasm_setup: an overlap list has %d points (cap %d)",
+                    ctx->max_ov, cap);
+    RBF_CHECK(rasm_factor(ctx, S(stream)));
+    ctx->rasm_ready = true;
+    return RBF_OK;
+}
+
+rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_rasm_apply: call rbf_rasm_setup first");
+    if (!r_dev || !z_dev) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_apply: null vector");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(ensure(ctx, ctx->vec_a, ctx->n));
+    RBF_CHECK(ensure(ctx, ctx->vec_b, ctx->n));
+    RBF_CHECK(permute_to_sorted(ctx, r_dev, ctx->vec_a.p, S(stream)));
+    RBF_CHECK(rasm_apply_sorted(ctx, ctx->vec_a.p, ctx->vec_b.p, S(stream)));
+    return permute_to_user(ctx, ctx->vec_b.p, z_dev, S(stream));
+}
+
+rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* p,
+                     rbf_solve_info* info, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_solve: call rbf_rasm_setup first");
+    if (!f_dev || !w_dev || !p) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: null argument");
+    if (!(p->rtol > 0.0) || p->restart < 0 || p->restart > kMaxRestart || p->max_iters < 0)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: need rtol > 0, 0 <= restart <= %d", kMaxRestart);
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(ensure(ctx, ctx->vec_d, ctx->n));
+    RBF_CHECK(ensure(ctx, ctx->vec_e, ctx->n));
+    RBF_CHECK(permute_to_sorted(ctx, f_dev, ctx->vec_d.p, S(stream)));
+    RBF_CHECK(permute_to_sorted(ctx, w_dev, ctx->vec_e.p, S(stream)));
+    rbf_solve_info local;
+    std::memset(&local, 0, sizeof(local));
+    rbf_status st = gmres_solve(ctx, ctx->vec_d.p, ctx->vec_e.p, p, &local, S(stream));
+    if (info) *info = local;
+    if (st != RBF_OK && st != RBF_ERR_NOT_CONVERGED) return st;
+    rbf_status st2 = permute_to_user(ctx, ctx->vec_e.p, w_dev, S(stream));
+    if (st2 != RBF_OK) return st2;
+    RBF_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    return st;
+}
+
+rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const double* f_host, double* w_host,
+                                int64_t n, const rbf_params* params, const rbf_rasm_params* rasm,
+                                const rbf_solve_params* solve, rbf_solve_info* info, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!xy_host || !f_host || !w_host || n < 1)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_interpolate_host: null buffer or n < 1");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    static_assert(sizeof(double) == 8, "double");
+    rbf::DevArray<double> xy, f, w;
+    // staging buffers are owned by the context for the duration of the call
+    RBF_CHECK(ensure(ctx, xy, (size_t)(2 * n)));
+    rbf_status st = ensure(ctx, f, (size_t)n);
+    if (st == RBF_OK) st = ensure(ctx, w, (size_t)n);
+    cudaStream_t s = S(stream);
+    if (st == RBF_OK) {
+        cudaError_t e = cudaMemcpyAsync(xy.p, xy_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(f.p, f_host, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.p, 0, sizeof(double) * n, s);
+        if (e != cudaSuccess) st = cuda_fail(ctx, e, "rbf_interpolate_host: copy in");
+    }
+    if (st == RBF_OK) st = rbf_bin(ctx, xy.p, n, params, stream);
+    if (st == RBF_OK) st = rbf_rasm_setup(ctx, rasm, stream);
+    if (st == RBF_OK || st == RBF_ERR_NOT_CONVERGED) {
+        rbf_status ss = rbf_solve(ctx, f.p, w.p, solve, info, stream);
+        if (ss == RBF_OK || ss == RBF_ERR_NOT_CONVERGED) {
+            cudaError_t e = cudaMemcpyAsync(w_host, w.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) ss = cuda_fail(ctx, e, "rbf_interpolate_host: copy out");
+        }
+        st = ss;
+    }
+    release(ctx, xy.p);
+    release(ctx, f.p);
+    release(ctx, w.p);
+    return st;
+}
+
+rbf_status rbf_get_grid(rbf_ctx* ctx, int64_t* ncx, int64_t* ncy, double* bbox_host)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_get_grid: call rbf_bin first");
+    if (ncx) *ncx = ctx->ncx;
+    if (ncy) *ncy = ctx->ncy;
+    if (bbox_host) std::memcpy(bbox_host, ctx->bbox, sizeof(ctx->bbox));
+    return RBF_OK;
+}
+
+rbf_status rbf_get_bins(rbf_ctx* ctx, int32_t* perm_dev, int32_t* cell_start_dev, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_get_bins: call rbf_bin first");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = S(stream);
+    if (perm_dev)
+        RBF_CUDA(ctx, cudaMemcpyAsync(perm_dev, ctx->perm.p, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice, s));
+    if (cell_start_dev)
+        RBF_CUDA(ctx, cudaMemcpyAsync(cell_start_dev, ctx->cell_start.p, sizeof(int32_t) * (ctx->ncx * ctx->ncy + 1),
+                                      cudaMemcpyDeviceToDevice, s));
+    RBF_CUDA(ctx, cudaStreamSynchronize(s));
+    return RBF_OK;
+}
+
+rbf_status rbf_get_subdomain_sizes(rbf_ctx* ctx, int64_t* nbx, int64_t* nby, int64_t* core_total,
+                                   int64_t* overlap_total)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_get_subdomain_sizes: call rbf_rasm_setup first");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    int32_t tot[2] = {0, 0};
+    RBF_CUDA(ctx, cudaMemcpy(&tot[0], ctx->core_ptr.p + ctx->nsub, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    RBF_CUDA(ctx, cudaMemcpy(&tot[1], ctx->ov_ptr.p + ctx->nsub, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (nbx) *nbx = ctx->nbx;
+    if (nby) *nby = ctx->nby;
+    if (core_total) *core_total = tot[0];
+    if (overlap_total) *overlap_total = tot[1];
+    return RBF_OK;
+}
+
+rbf_status rbf_get_subdomains(rbf_ctx* ctx, int32_t* core_ptr_dev, int32_t* core_idx_dev, int32_t* ov_ptr_dev,
+                              int32_t* ov_idx_dev, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_get_subdomains: call rbf_rasm_setup first");
+    if (!core_ptr_dev || !core_idx_dev || !ov_ptr_dev || !ov_idx_dev)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_get_subdomains: null output");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(export_subdomains(ctx, core_ptr_dev, core_idx_dev, ov_ptr_dev, ov_idx_dev, S(stream)));
+    RBF_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    return RBF_OK;
+}
+
+rbf_status rbf_count_neighbors(rbf_ctx* ctx, int64_t* total, rbf_stream stream)
+{
+    if (!ctx || !total) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_count_neighbors: call rbf_bin first");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    return neighbor_lists(ctx, nullptr, nullptr, 0, total, S(stream));
+}
+
+rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    ctx->prof = enable != 0;
+    return RBF_OK;
+}
+
+rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double* total_ms)
+{
+    if (!ctx || kernel < 0 || kernel >= RBF_PROF_COUNT) return RBF_ERR_INVALID_ARG;
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    rbf_prof_slot& s = ctx->prof_slots[kernel];
+    double tot = 0.0;
+    for (int64_t i = 0; i < s.used; ++i) {
+        RBF_CUDA(ctx, cudaEventSynchronize(s.ev[2 * i + 1]));
+        float ms = 0.f;
+        RBF_CUDA(ctx, cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]));
+        tot += ms;
+    }
+    if (launches) *launches = s.used;
+    if (total_ms) *total_ms = tot;
+    s.used = 0;
+    return RBF_OK;
+}
+
+rbf_status rbf_debug_exp(rbf_ctx* ctx, const double* t_dev, double* out_dev, int64_t n, int variant,
+                         rbf_stream stream)
+{
+    if (!ctx || !t_dev || !out_dev || n < 0 || (variant != 0 && variant != 1)) return RBF_ERR_INVALID_ARG;
+    if (n == 0) return RBF_OK;
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_LAUNCH(ctx, k_debug_exp, blocks_for(n, 256), 256, 0, S(stream), t_dev, out_dev, n, variant, ctx->expc);
+    return RBF_OK;
+}
+
+rbf_status rbf_get_neighbors(rbf_ctx* ctx, int64_t* ptr_dev, int32_t* idx_dev, int64_t capacity, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_get_neighbors: call rbf_bin first");
+    if (!ptr_dev || !idx_dev || capacity < 0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_get_neighbors: bad output");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    int64_t total = 0;
+    return neighbor_lists(ctx, ptr_dev, idx_dev, capacity, &total, S(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// common.cuh -- internal declarations shared by the librbf.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rbf.h"
+#include "exp64.cuh"
+
+namespace rbf {
+
+constexpr int kMaxRestart = 32;   // GMRES(m): m <= 32 (the CGS2 kernels keep V_k[i] in registers)
+constexpr int kMaxSub = 64;       // overlap list cap (subdomain matrix dimension)
+constexpr int kNumSMs = 152;      // GB300
+
+// Device-resident small state of one GMRES cycle (Hessenberg, Givens, g).
+struct GmresDev {
+    double H[(kMaxRestart + 1) * kMaxRestart];   // row-major (m+1) x m, stride kMaxRestart
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double g[kMaxRestart + 1];
+    double y[kMaxRestart];
+    double h1[kMaxRestart + 1];   // first Gram-Schmidt pass coefficients
+    double h2[kMaxRestart + 1];   // second pass coefficients
+    double nrm2;                  // |v|^2 after the second pass
+    double beta2;                 // |r|^2 of the cycle's starting residual
+    double fnorm2;                // |f|^2
+    double inv_h;                 // 1 / H[j+1][j] (0 on breakdown)
+    double inv_beta;              // 1 / beta
+    double est;                   // |g_{j+1}| / |f|
+    double rtol;
+    int j;                        // last completed step
+    int done;                     // 1: cycle may stop (estimate met or breakdown)
+    int breakdown;
+    int pad;
+};
+
+template <class T>
+struct DevArray {
+    T* p = nullptr;
+    size_t count = 0;
+};
+
+}  // namespace rbf
+
+struct rbf_prof_slot {
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+    int64_t used = 0;
+};
+
+struct rbf_ctx {
+    int device = 0;
+    bool prof = false;
+    rbf_prof_slot prof_slots[RBF_PROF_COUNT];
+    rbf::ExpConsts expc;
+    std::string err;
+    uint64_t launches = 0;
+    int64_t dev_bytes = 0;
+    std::vector<std::pair<void*, size_t>> owned;   // every live allocation
+
+    // ---- binning (rbf_bin)
+    bool binned = false;
+    int64_t n = 0;
+    double sigma = 0, rc = 0, rc2 = 0, cell = 0, s = 0, knorm = 1.0;
+    int normalized = 0;
+    int64_t ncx = 0, ncy = 0;
+    int kst = 1;                   // stencil half-width ceil(rc / c)
+    double bbox[4] = {0, 0, 0, 0};
+    rbf::DevArray<int32_t> perm, iperm, cell_start, cell_s, counts, cell_u, tmp_i32;
+    rbf::DevArray<double> xy_s;    // sorted coordinates, interleaved (x, y)
+    rbf::DevArray<double> bbox_part, bbox_dev;
+
+    // ---- subdomains (rbf_rasm_setup)
+    bool rasm_ready = false;
+    int rasm_precision = RBF_FP64;
+    double x0 = 0, y0 = 0, B = 0, delta = 0;
+    int64_t nbx = 0, nby = 0, nsub = 0;
+    int max_ov = 0, max_core = 0;
+    rbf::DevArray<int32_t> core_ptr, core_idx, ov_ptr, ov_idx, core_of, sub_cnt, sub_fill;
+    rbf::DevArray<int64_t> w_off, w_size;
+    rbf::DevArray<double> W64;
+    rbf::DevArray<float> W32;
+    rbf::DevArray<int> status_dev;
+
+    // ---- solver workspace
+    rbf::DevArray<double> V, vec_a, vec_b, vec_c, vec_d, vec_e, partial;
+    rbf::DevArray<rbf::GmresDev> gm;
+    rbf::GmresDev* gm_host = nullptr;   // pinned mirror for the per-step status read
+    rbf::DevArray<int64_t> scan_tmp;
+    rbf::DevArray<int32_t> nbr_cnt;
+    rbf::DevArray<int64_t> nbr_ptr_tmp;
+};
+
+namespace rbf {
+
+rbf_status fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...);
+rbf_status cuda_fail(rbf_ctx* ctx, cudaError_t e, const char* where);
+
+template <class T>
+rbf_status ensure(rbf_ctx* ctx, DevArray<T>& a, size_t count);
+void release(rbf_ctx* ctx, void* p);
+
+#define RBF_CUDA(ctx, call)                                                \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::rbf::cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+#define RBF_CHECK(call)                     \
+    do {                                    \
+        rbf_status s_ = (call);             \
+        if (s_ != RBF_OK) return s_;        \
+    } while (0)
+
+// Launch a kernel, count it, and report a launch error.
+#define RBF_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)                       \
+    do {                                                                              \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                   \
+        (ctx)->launches++;                                                            \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess) return ::rbf::cuda_fail((ctx), e_, #kernel);           \
+    } while (0)
+
+inline unsigned blocks_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+    return (unsigned)b;
+}
+
+// Profiler hooks: event pair around one launch (or launch sequence) of class id.
+rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st);
+rbf_status prof_end(rbf_ctx* ctx, int id, cudaStream_t st);
+
+// ---- scan.cu
+// out[0] = 0, out[i+1] = in[0] + ... + in[i] for i < n (int32 or int64 in, int64 or int32 out)
+rbf_status exclusive_scan_i32(rbf_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+rbf_status exclusive_scan_i64(rbf_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+rbf_status reduce_max_i32(rbf_ctx* ctx, const int32_t* in, int64_t n, int32_t* out_host, cudaStream_t st);
+
+// ---- bin.cu
+rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st);
+rbf_status permute_to_sorted(rbf_ctx* ctx, const double* user, double* sorted, cudaStream_t st);
+rbf_status permute_to_user(rbf_ctx* ctx, const double* sorted, double* user, cudaStream_t st);
+rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capacity, int64_t* total,
+                          cudaStream_t st);
+
+// ---- subdomain.cu
+rbf_status build_subdomains(rbf_ctx* ctx, cudaStream_t st);
+rbf_status export_subdomains(rbf_ctx* ctx, int32_t* core_ptr, int32_t* core_idx, int32_t* ov_ptr,
+                             int32_t* ov_idx, cudaStream_t st);
+
+// ---- matvec.cu  (vectors in cell order)
+rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+
+// ---- rasm.cu  (vectors in cell order)
+rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st);
+rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStream_t st);
+
+// ---- gmres.cu
+rbf_status gmres_solve(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,
+                       rbf_solve_info* info, cudaStream_t st);
+
+}  // namespace rbf

@@ -1,0 +1,455 @@
+// gmres.cu -- restarted GMRES(m) with right preconditioning (Sec. 2.2: GMRES
+// with the RASM preconditioner; Sec. 3.1: relative tolerance 1e-13), all on
+// the device:
+//   * Arnoldi vectors V (m+1) x N in cell order;
+//   * classical Gram-Schmidt applied twice, in three fused passes over V:
+//       h1 = V^T v;  v -= V h1 and h2 = V^T v (same pass);  v -= V h2 and |v|^2;
+//   * block partial sums reduced in a fixed order (deterministic);
+//   * the Hessenberg column, the Givens rotations, the residual estimate
+//     |g_{j+1}| and the stop flag are updated by a single-thread kernel; the
+//     host reads the small status once per Arnoldi step.
+// Mixed form: the same cycle runs on FP32 vectors with the FP32 matvec and
+// FP32 subdomain inverses, while its dot products, Hessenberg and Givens stay
+// FP64; each inner solve corrects w by FP64 iterative refinement on the true
+// FP64 residual.
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace rbf {
+
+rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStream_t st);
+rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t st);
+rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float* y, cudaStream_t st);
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocksMax = 8 * kNumSMs;
+
+// MODE 0: acc_k = sum_i V_k[i] x[i]
+// MODE 1: x[i] -= sum_k coef_k V_k[i];  acc_k = sum_i V_k[i] x[i] (updated x)
+// MODE 2: x[i] -= sum_k coef_k V_k[i];  acc_0 = sum_i x[i]^2
+// partial[block * 32 + k] receives the block's sums (fixed order).
+template <int MODE, int NV, class T>
+__global__ void __launch_bounds__(kDotThreads)
+    k_mdot(const T* __restrict__ V, int64_t ldv, int nv, T* __restrict__ x, int64_t n, const double* __restrict__ coef,
+           double* __restrict__ partial)
+{
+    __shared__ double red[kDotThreads / 32][NV];
+    __shared__ double cf[NV];
+    if (MODE != 0) {
+        if (threadIdx.x < NV) cf[threadIdx.x] = (threadIdx.x < (unsigned)nv) ? coef[threadIdx.x] : 0.0;
+        __syncthreads();
+    }
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = (double)x[i];
+        if (MODE == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (k < nv) acc[k] = fma((double)V[k * ldv + i], xi, acc[k]);
+        } else {
+            double v[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = (k < nv) ? (double)V[k * ldv + i] : 0.0;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) xi = fma(-cf[k], v[k], xi);
+            T xs = (T)xi;
+            x[i] = xs;
+            xi = (double)xs;
+            if (MODE == 1) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], xi, acc[k]);
+            } else {
+                acc[0] = fma(xi, xi, acc[0]);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NR = (MODE == 2) ? 1 : NV;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double a = acc[k];
+        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+        if (lane == 0) red[warp][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < NR) {
+        double a = 0.0;
+        for (int w = 0; w < kDotThreads / 32; ++w) a += red[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * 32 + threadIdx.x] = a;
+    }
+}
+
+// out[k] = sum over blocks of partial[b*32 + k], k < nv: one warp per k, fixed order.
+__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv, double* __restrict__ out)
+{
+    int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= nv) return;
+    double a = 0.0;
+    for (int b = lane; b < nblocks; b += 32) a += partial[(int64_t)b * 32 + k];
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if (lane == 0) out[k] = a;
+}
+
+// r = f - t (FP64); partial sums of |r|^2.
+__global__ void __launch_bounds__(kDotThreads)
+    k_residual(const double* __restrict__ f, const double* __restrict__ t, double* __restrict__ r, int64_t n,
+               double* __restrict__ partial)
+{
+    __shared__ double red[kDotThreads / 32];
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = f[i] - t[i];
+        r[i] = v;
+        a = fma(v, v, a);
+    }
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
+        partial[(int64_t)blockIdx.x * 32] = s;
+    }
+}
+
+// Start of a cycle: beta = |r|, g = beta e_1, estimate beta / |f|. For an
+// inner solve of the mixed form (inner = 1) the reference norm is |r| itself.
+__global__ void k_cycle_init(GmresDev* g, int m, int inner)
+{
+    if (inner) g->fnorm2 = g->beta2;
+    double beta = sqrt(g->beta2);
+    double fn = sqrt(g->fnorm2);
+    for (int q = 0; q <= m; ++q) g->g[q] = 0.0;
+    g->g[0] = beta;
+    g->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+    g->est = fn > 0.0 ? beta / fn : 0.0;
+    g->done = (g->est <= g->rtol) ? 1 : 0;
+    g->breakdown = 0;
+    g->j = -1;
+}
+
+// Arnoldi step j: Hessenberg column, previous rotations, new rotation, g update.
+__global__ void k_arnoldi(GmresDev* g, int j)
+{
+    const int M = kMaxRestart;
+    for (int q = 0; q <= j; ++q) g->H[q * M + j] = g->h1[q] + g->h2[q];
+    double hn = sqrt(fmax(g->nrm2, 0.0));
+    g->H[(j + 1) * M + j] = hn;
+    for (int q = 0; q < j; ++q) {
+        double a = g->H[q * M + j], b = g->H[(q + 1) * M + j];
+        g->H[q * M + j] = g->cs[q] * a + g->sn[q] * b;
+        g->H[(q + 1) * M + j] = -g->sn[q] * a + g->cs[q] * b;
+    }
+    double a = g->H[j * M + j], b = g->H[(j + 1) * M + j];
+    double c, s;
+    if (b == 0.0) { c = 1.0; s = 0.0; }
+    else if (fabs(b) > fabs(a)) { double t = a / b; s = 1.0 / sqrt(1.0 + t * t); c = s * t; }
+    else { double t = b / a; c = 1.0 / sqrt(1.0 + t * t); s = c * t; }
+    g->cs[j] = c;
+    g->sn[j] = s;
+    g->H[j * M + j] = c * a + s * b;
+    g->H[(j + 1) * M + j] = 0.0;
+    g->g[j + 1] = -s * g->g[j];
+    g->g[j] = c * g->g[j];
+    g->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
+    g->breakdown = (hn == 0.0) ? 1 : 0;
+    double fn = sqrt(g->fnorm2);
+    g->est = fabs(g->g[j + 1]) / fn;
+    g->done = (g->est <= g->rtol || g->breakdown) ? 1 : 0;
+    g->j = j;
+}
+
+// y = H(0:k, 0:k)^{-1} g(0:k), upper triangular.
+__global__ void k_solve_y(GmresDev* g, int k)
+{
+    const int M = kMaxRestart;
+    for (int q = k - 1; q >= 0; --q) {
+        double v = g->g[q];
+        for (int p = q + 1; p < k; ++p) v -= g->H[q * M + p] * g->y[p];
+        g->y[q] = v / g->H[q * M + q];
+    }
+}
+
+template <class T>
+__global__ void k_scale(T* __restrict__ x, int64_t n, const double* __restrict__ factor)
+{
+    double f = *factor;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (T)((double)x[i] * f);
+}
+
+// t = sum_{q<k} y_q V_q
+template <class T>
+__global__ void k_combine(const T* __restrict__ V, int64_t ldv, int k, const double* __restrict__ y,
+                          T* __restrict__ t, int64_t n)
+{
+    __shared__ double ys[kMaxRestart];
+    if (threadIdx.x < (unsigned)k) ys[threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int q = 0; q < k; ++q) a = fma(ys[q], (double)V[q * ldv + i], a);
+        t[i] = (T)a;
+    }
+}
+
+// w += u (u in T, w FP64)
+template <class T>
+__global__ void k_axpy(double* __restrict__ w, const T* __restrict__ u, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] += (double)u[i];
+}
+
+// FP32 copy of an FP64 vector scaled by a device factor: out = in * (*factor)
+__global__ void k_to_f32_scaled(const double* __restrict__ in, int64_t n, const double* __restrict__ factor,
+                                float* __restrict__ out)
+{
+    double f = *factor;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)(in[i] * f);
+}
+
+__global__ void k_w64_to_w32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+unsigned dot_blocks(int64_t n)
+{
+    int64_t b = (n + kDotThreads - 1) / kDotThreads;
+    if (b > kDotBlocksMax) b = kDotBlocksMax;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+unsigned stream_blocks(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 16 * kNumSMs) b = 16 * kNumSMs;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <int MODE, int NV, class T>
+rbf_status launch_mdot_nv(rbf_ctx* ctx, const T* V, int64_t ldv, int nv, T* x, int64_t n, const double* coef,
+                          double* out, cudaStream_t st)
+{
+    unsigned nb = dot_blocks(n);
+    RBF_LAUNCH(ctx, (k_mdot<MODE, NV, T>), nb, kDotThreads, 0, st, V, ldv, nv, x, n, coef, ctx->partial.p);
+    int nr = (MODE == 2) ? 1 : nv;
+    RBF_LAUNCH(ctx, k_reduce, 1, 32 * nr, 0, st, ctx->partial.p, (int)nb, nr, out);
+    return RBF_OK;
+}
+
+template <int MODE, class T>
+rbf_status launch_mdot(rbf_ctx* ctx, const T* V, int64_t ldv, int nv, T* x, int64_t n, const double* coef,
+                       double* out, cudaStream_t st)
+{
+    if (nv <= 4) return launch_mdot_nv<MODE, 4, T>(ctx, V, ldv, nv, x, n, coef, out, st);
+    if (nv <= 8) return launch_mdot_nv<MODE, 8, T>(ctx, V, ldv, nv, x, n, coef, out, st);
+    if (nv <= 16) return launch_mdot_nv<MODE, 16, T>(ctx, V, ldv, nv, x, n, coef, out, st);
+    return launch_mdot_nv<MODE, 32, T>(ctx, V, ldv, nv, x, n, coef, out, st);
+}
+
+struct StepStatus {
+    double est;
+    int done;
+};
+
+rbf_status read_status(rbf_ctx* ctx, cudaStream_t st, StepStatus* s)
+{
+    const size_t off = offsetof(GmresDev, est);
+    const size_t len = offsetof(GmresDev, pad) - off;
+    RBF_CUDA(ctx, cudaMemcpyAsync((char*)ctx->gm_host + off, (char*)ctx->gm.p + off, len, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    s->est = ctx->gm_host->est;
+    s->done = ctx->gm_host->done;
+    return RBF_OK;
+}
+
+// Operators of one GMRES flavour on vectors of type T.
+struct OpsF64 {
+    static rbf_status amul(rbf_ctx* c, const double* x, double* y, cudaStream_t st, const float2*)
+    {
+        return matvec_sorted_f64(c, x, y, st);
+    }
+    static rbf_status minv(rbf_ctx* c, const double* x, double* y, cudaStream_t st)
+    {
+        return rasm_apply_sorted(c, x, y, st);
+    }
+};
+
+struct OpsF32 {
+    static rbf_status amul(rbf_ctx* c, const float* x, float* y, cudaStream_t st, const float2* loc)
+    {
+        return matvec_f32_raw(c, loc, x, y, st);
+    }
+    static rbf_status minv(rbf_ctx* c, const float* x, float* y, cudaStream_t st)
+    {
+        return rasm_apply_sorted_f32(c, x, y, st);
+    }
+};
+
+// One GMRES cycle on vectors of type T starting from V_0 = r / |r| (V_0 holds
+// r on entry and beta2 is in g->beta2). Accumulates the correction
+// M^{-1} V y into w (FP64). Returns the number of Arnoldi steps.
+template <class T, class Ops>
+rbf_status gmres_cycle(rbf_ctx* ctx, T* V, int64_t ldv, int m, int max_steps, T* tmp_u, T* tmp_t, double* w,
+                       const float2* loc, bool scale_v0, cudaStream_t st, int* steps, double* est, int* applies)
+{
+    const int64_t n = ctx->n;
+    GmresDev* g = ctx->gm.p;
+    int k = 0;
+    StepStatus ss{0.0, 0};
+    if (scale_v0) RBF_LAUNCH(ctx, (k_scale<T>), stream_blocks(n), 256, 0, st, V, n, &g->inv_beta);
+    for (int j = 0; j < m && j < max_steps; ++j) {
+        T* vj = V + (int64_t)j * ldv;
+        T* vn = V + (int64_t)(j + 1) * ldv;
+        RBF_CHECK(Ops::minv(ctx, vj, tmp_u, st));
+        ++*applies;
+        RBF_CHECK(Ops::amul(ctx, tmp_u, vn, st, loc));
+        RBF_CHECK(prof_begin(ctx, RBF_PROF_ORTHO, st));
+        RBF_CHECK((launch_mdot<0, T>(ctx, V, ldv, j + 1, vn, n, nullptr, g->h1, st)));
+        RBF_CHECK((launch_mdot<1, T>(ctx, V, ldv, j + 1, vn, n, g->h1, g->h2, st)));
+        RBF_CHECK((launch_mdot<2, T>(ctx, V, ldv, j + 1, vn, n, g->h2, &g->nrm2, st)));
+        RBF_CHECK(prof_end(ctx, RBF_PROF_ORTHO, st));
+        RBF_LAUNCH(ctx, k_arnoldi, 1, 1, 0, st, g, j);
+        RBF_LAUNCH(ctx, (k_scale<T>), stream_blocks(n), 256, 0, st, vn, n, &g->inv_h);
+        k = j + 1;
+        RBF_CHECK(read_status(ctx, st, &ss));
+        if (ss.done) break;
+    }
+    RBF_LAUNCH(ctx, k_solve_y, 1, 1, 0, st, g, k);
+    RBF_LAUNCH(ctx, (k_combine<T>), stream_blocks(n), 256, 0, st, V, ldv, k, g->y, tmp_t, n);
+    RBF_CHECK(Ops::minv(ctx, tmp_t, tmp_u, st));
+    ++*applies;
+    RBF_LAUNCH(ctx, (k_axpy<T>), stream_blocks(n), 256, 0, st, w, tmp_u, n);
+    *steps = k;
+    *est = ss.est;
+    return RBF_OK;
+}
+
+// True FP64 residual r = f - A w into r64, |r|^2 into g->beta2; returns |r| / |f|.
+rbf_status true_residual(rbf_ctx* ctx, const double* f, const double* w, double* t, double* r64, cudaStream_t st,
+                         double fnorm, double* relres)
+{
+    GmresDev* g = ctx->gm.p;
+    RBF_CHECK(matvec_sorted_f64(ctx, w, t, st));
+    unsigned nb = dot_blocks(ctx->n);
+    RBF_LAUNCH(ctx, k_residual, nb, kDotThreads, 0, st, f, t, r64, ctx->n, ctx->partial.p);
+    RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nb, 1, &g->beta2);
+    RBF_CUDA(ctx, cudaMemcpyAsync(&ctx->gm_host->beta2, &g->beta2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *relres = std::sqrt(ctx->gm_host->beta2) / fnorm;
+    return RBF_OK;
+}
+
+}  // namespace
+
+rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve_params* p, rbf_solve_info* info,
+                       cudaStream_t st)
+{
+    const int64_t n = ctx->n;
+    const int m = p->restart > 0 ? p->restart : 30;
+    const int max_iters = p->max_iters > 0 ? p->max_iters : 10000;
+    const bool mixed = p->mixed != 0;
+    RBF_CHECK(ensure(ctx, ctx->gm, 1));
+    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)kDotBlocksMax * 32));
+    RBF_CHECK(ensure(ctx, ctx->vec_a, n));
+    RBF_CHECK(ensure(ctx, ctx->vec_b, n));
+    GmresDev* g = ctx->gm.p;
+
+    // device state: zero, rtol
+    std::memset(ctx->gm_host, 0, sizeof(GmresDev));
+    ctx->gm_host->rtol = mixed ? (p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5) : p->rtol;
+    RBF_CUDA(ctx, cudaMemcpyAsync(g, ctx->gm_host, sizeof(GmresDev), cudaMemcpyHostToDevice, st));
+    // |f|^2
+    RBF_CHECK((launch_mdot<0, double>(ctx, f, 0, 1, const_cast<double*>(f), n, nullptr, &g->fnorm2, st)));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&ctx->gm_host->fnorm2, &g->fnorm2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    const double fnorm = std::sqrt(ctx->gm_host->fnorm2);
+    if (!std::isfinite(fnorm)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: f is not finite");
+    if (fnorm == 0.0) {
+        RBF_CUDA(ctx, cudaMemsetAsync(w, 0, sizeof(double) * n, st));
+        info->relres = 0.0;
+        return RBF_OK;
+    }
+
+    int it = 0, cycles = 0, refine = 0, matvecs = 0, applies = 0;
+    double relres = 0.0, est = 0.0;
+    rbf_status result = RBF_ERR_NOT_CONVERGED;
+
+    if (!mixed) {
+        RBF_CHECK(ensure(ctx, ctx->V, (size_t)(m + 1) * n));
+        double* V = ctx->V.p;
+        for (;;) {
+            RBF_CHECK(true_residual(ctx, f, w, ctx->vec_a.p, V, st, fnorm, &relres));
+            ++matvecs;
+            if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
+            if (relres <= p->rtol) { result = RBF_OK; break; }
+            if (it >= max_iters) break;
+            RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 0);
+            int steps = 0;
+            RBF_CHECK((gmres_cycle<double, OpsF64>(ctx, V, n, m, max_iters - it, ctx->vec_b.p, ctx->vec_a.p, w,
+                                                   nullptr, true, st, &steps, &est, &applies)));
+            it += steps;
+            matvecs += steps;
+            ++cycles;
+        }
+    } else {
+        // FP32 inner GMRES inside FP64 iterative refinement:
+        //   r = f - A w (FP64);  solve A d = r in FP32 to inner_rtol;  w += d.
+        const int max_refine = p->max_refine > 0 ? p->max_refine : 40;
+        if (ctx->rasm_precision == RBF_FP64 || !ctx->W32.p) {
+            RBF_CHECK(ensure(ctx, ctx->W32, ctx->W64.count));
+            RBF_LAUNCH(ctx, k_w64_to_w32, stream_blocks((int64_t)ctx->W64.count), 256, 0, st, ctx->W64.p,
+                       (int64_t)ctx->W64.count, ctx->W32.p);
+        }
+        float2* loc = nullptr;
+        RBF_CHECK(ensure_local_coords(ctx, &loc, st));
+        // FP32 Krylov basis plus two FP32 work vectors, in V's storage
+        const int64_t ldv = ((n + 63) / 64) * 64;
+        RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 3) * ldv + 1) / 2 + 1));
+        float* Vf = (float*)ctx->V.p;
+        float* uf = Vf + (int64_t)(m + 1) * ldv;
+        float* tf = uf + ldv;
+        double* r64 = ctx->vec_b.p;
+        for (;;) {
+            RBF_CHECK(true_residual(ctx, f, w, ctx->vec_a.p, r64, st, fnorm, &relres));
+            ++matvecs;
+            if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
+            if (relres <= p->rtol) { result = RBF_OK; break; }
+            if (it >= max_iters || refine >= max_refine) break;
+            // inner solve from d = 0: V_0 = r / |r| in FP32 (beta2 already on the device)
+            RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 1);
+            RBF_LAUNCH(ctx, k_to_f32_scaled, stream_blocks(n), 256, 0, st, r64, n, &g->inv_beta, Vf);
+            int steps = 0;
+            RBF_CHECK((gmres_cycle<float, OpsF32>(ctx, Vf, ldv, m, max_iters - it, uf, tf, w, loc, false, st, &steps,
+                                                  &est, &applies)));
+            it += steps;
+            matvecs += steps;
+            ++cycles;
+            ++refine;
+        }
+    }
+    info->iters = it;
+    info->restarts = cycles;
+    info->refinements = refine;
+    info->relres = relres;
+    info->relres_est = est;
+    info->matvecs = matvecs;
+    info->applies = applies;
+    if (result != RBF_OK)
+        fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: relative residual %.3e after %d steps (rtol %.1e)", relres, it,
+             p->rtol);
+    return result;
+}
+
+}  // namespace rbf

@@ -1,0 +1,404 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Index work (binning, neighbour and subdomain lists) must match bit for bit.
+FP64 matvec: relative error <= 1e-13 (each entry is one exp plus an FMA chain;
+the two sides differ only in rounding order and in the exp implementation).
+Solves: the true relative residual, recomputed by the oracle's own FP64
+matvec, must be <= 1e-13.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0909_5413_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    from paper_0909_5413_gb300 import rbf as R
+    R.load()
+    return R
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda") if dtype is None else t.to("cuda", dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def make_ctx(rbf, xy, sigma, rc, cell=0.0, normalized=False):
+    ctx = rbf.Context(0)
+    xyd = dev(xy)
+    rbf.rbf_bin(ctx.handle, xyd, xy.shape[0], rbf.RbfParams(sigma, rc, cell, int(normalized)))
+    return ctx, xyd
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def random_points(n, seed, lo=-1.0, hi=1.0):
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(rng.uniform(lo, hi, size=(n, 2)))
+
+
+# ------------------------------------------------------------------ binning
+
+def bin_cases():
+    p = W.config_small()
+    yield "lattice64", p.xy, p.sigma, p.cutoff, 0.0
+    yield "lattice64_half_cells", p.xy, p.sigma, p.cutoff, p.cutoff / 2
+    q = W.lattice_problem(37, 0.8, seed=37)
+    yield "lattice37_ragged", q.xy, q.sigma, q.cutoff, 0.0
+    for n in (1, 2, 15, 16, 17, 255):
+        yield f"rand{n}", random_points(n, n), 0.05, 0.3, 0.0
+    yield "one_cell", random_points(300, 9, 0.0, 0.01), 0.001, 1.0, 0.0
+    a, b = random_points(100, 11, -1.0, -0.5), random_points(100, 12, 0.5, 1.0)
+    yield "gap", np.ascontiguousarray(np.vstack([a, b])), 0.02, 0.2, 0.0
+    e = np.array([[0.0, 0.0], [0.25, 0.0], [0.5, 0.5], [0.25, 0.0], [0.75, 1.0], [1.0, 1.0]])
+    yield "edges_duplicates", e, 0.05, 0.25, 0.0
+
+
+@pytest.mark.parametrize("case", list(bin_cases()), ids=[c[0] for c in bin_cases()])
+def test_binning_bit_exact(rbf, case):
+    name, xy, sigma, rc, cell = case
+    ctx, _ = make_ctx(rbf, xy, sigma, rc, cell)
+    g, perm, cs = O.bin_points(xy, cell if cell > 0 else rc)
+    ncx, ncy, bbox = rbf.rbf_get_grid(ctx.handle)
+    assert (ncx, ncy) == (g.ncx, g.ncy)
+    assert bbox == (g.xmin, g.ymin, g.xmax, g.ymax)
+    pd = torch.empty(xy.shape[0], dtype=torch.int32, device="cuda")
+    cd = torch.empty(ncx * ncy + 1, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_bins(ctx.handle, pd, cd)
+    np.testing.assert_array_equal(host(pd), perm)
+    np.testing.assert_array_equal(host(cd), cs)
+    ctx.close()
+
+
+def test_binning_bit_exact_1m(rbf):
+    p = W.config_1m()
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    g, perm, cs = O.bin_points(p.xy, p.cutoff)
+    ncx, ncy, _ = rbf.rbf_get_grid(ctx.handle)
+    pd = torch.empty(p.n, dtype=torch.int32, device="cuda")
+    cd = torch.empty(ncx * ncy + 1, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_bins(ctx.handle, pd, cd)
+    np.testing.assert_array_equal(host(pd), perm)
+    np.testing.assert_array_equal(host(cd), cs)
+    ctx.close()
+
+
+# --------------------------------------------------------------- neighbours
+
+@pytest.mark.parametrize("n_side,cfac", [(40, 1.0), (64, 1.0), (33, 0.5), (21, 1.0 / 3.0)])
+def test_neighbor_lists_bit_exact(rbf, n_side, cfac):
+    p = W.lattice_problem(n_side, 0.8, seed=n_side)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff, p.cutoff * cfac)
+    total = rbf.rbf_count_neighbors(ctx.handle)
+    ptr = torch.empty(p.n + 1, dtype=torch.int64, device="cuda")
+    idx = torch.empty(total, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_neighbors(ctx.handle, ptr, idx, total)
+    rptr, ridx = O.neighbors(p.xy, p.cutoff, c=p.cutoff * cfac)
+    np.testing.assert_array_equal(host(ptr), rptr)
+    np.testing.assert_array_equal(host(idx), ridx)
+    ctx.close()
+
+
+def test_neighbor_capacity_error(rbf):
+    p = W.lattice_problem(16, 0.8, seed=1)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    total = rbf.rbf_count_neighbors(ctx.handle)
+    ptr = torch.empty(p.n + 1, dtype=torch.int64, device="cuda")
+    idx = torch.empty(total, dtype=torch.int32, device="cuda")
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_get_neighbors(ctx.handle, ptr, idx, total - 1)
+    assert e.value.status == 1
+    ctx.close()
+
+
+# ------------------------------------------------------------ subdomains
+
+def sub_cases():
+    yield "lattice64", W.config_small()
+    yield "lattice37", W.lattice_problem(37, 0.8, seed=3)
+    yield "ring2", W.lattice_problem(30, 0.8, seed=4, ring_points=2)
+    yield "ring0", W.lattice_problem(16, 0.8, seed=5, ring_points=0)
+    yield "unit_square_paper", W.unit_square_problem(1.0, sigma=0.02)
+
+
+def gpu_subdomains(rbf, ctx):
+    nbx, nby, ct, ot = rbf.rbf_get_subdomain_sizes(ctx.handle)
+    ns = nbx * nby
+    cp = torch.empty(ns + 1, dtype=torch.int32, device="cuda")
+    op = torch.empty(ns + 1, dtype=torch.int32, device="cuda")
+    ci = torch.empty(max(ct, 1), dtype=torch.int32, device="cuda")
+    oi = torch.empty(max(ot, 1), dtype=torch.int32, device="cuda")
+    rbf.rbf_get_subdomains(ctx.handle, cp, ci, op, oi)
+    return (nbx, nby), host(cp), host(ci)[:ct], host(op), host(oi)[:ot]
+
+
+@pytest.mark.parametrize("case", list(sub_cases()), ids=[c[0] for c in sub_cases()])
+def test_subdomain_lists_bit_exact(rbf, case):
+    _, p = case
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 0))
+    (nbx, nby), cp, ci, op, oi = gpu_subdomains(rbf, ctx)
+    (rbx, rby), rcp, rci, rop, roi = O.subdomains(p.xy, p.x0, p.x0, p.core_size, p.overlap)
+    assert (nbx, nby) == (rbx, rby)
+    np.testing.assert_array_equal(cp, rcp)
+    np.testing.assert_array_equal(ci, rci)
+    np.testing.assert_array_equal(op, rop)
+    np.testing.assert_array_equal(oi, roi)
+    ctx.close()
+
+
+def test_subdomain_lists_bit_exact_1m(rbf):
+    p = W.config_1m()
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 0))
+    (nbx, nby), cp, ci, op, oi = gpu_subdomains(rbf, ctx)
+    (rbx, rby), rcp, rci, rop, roi = O.subdomains(p.xy, p.x0, p.x0, p.core_size, p.overlap)
+    assert (nbx, nby) == (rbx, rby) == (256, 256)
+    np.testing.assert_array_equal(cp, rcp)
+    np.testing.assert_array_equal(ci, rci)
+    np.testing.assert_array_equal(op, rop)
+    np.testing.assert_array_equal(oi, roi)
+    ctx.close()
+
+
+def test_subdomain_too_large_is_reported(rbf):
+    p = W.lattice_problem(32, 0.8, seed=6)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, 8 * p.h, p.h, 64, 0))
+    assert e.value.status == 5
+    ctx.close()
+
+
+def test_duplicate_points_not_spd(rbf):
+    p = W.lattice_problem(12, 0.8, seed=7)
+    xy = p.xy.copy()
+    xy[5] = xy[4]
+    ctx, _ = make_ctx(rbf, xy, p.sigma, p.cutoff)
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 0))
+    assert e.value.status == 4
+    ctx.close()
+
+
+def test_state_errors(rbf):
+    p = W.lattice_problem(8, 0.8, seed=8)
+    ctx = rbf.Context(0)
+    v = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_matvec(ctx.handle, v, v)
+    assert e.value.status == 8
+    rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(p.sigma, p.cutoff, 0.0, 0))
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_rasm_apply(ctx.handle, v, v)
+    assert e.value.status == 8
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(-1.0, p.cutoff, 0.0, 0))
+    assert e.value.status == 1
+    ctx.close()
+
+
+# ------------------------------------------------------------------ matvec
+
+def matvec_cases():
+    yield "lattice64", W.config_small(), 0.0, False
+    yield "lattice64_normalized", W.config_small(), 0.0, True
+    yield "lattice37_half_cells", W.lattice_problem(37, 0.8, seed=9), 0.5, False
+    yield "lattice50_ratio1", W.lattice_problem(50, 1.0, seed=10), 1.0 / 3.0, False
+    yield "lattice3", W.lattice_problem(3, 0.8, seed=11), 0.0, False
+
+
+@pytest.mark.parametrize("case", list(matvec_cases()), ids=[c[0] for c in matvec_cases()])
+def test_matvec_f64_matches_oracle(rbf, case):
+    _, p, cf, normalized = case
+    cell = p.cutoff * cf if cf > 0 else 0.0
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff, cell, normalized)
+    w = np.random.default_rng(1).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y, rbf.RBF_FP64)
+    ref = O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff, normalized=normalized)
+    got = host(y)
+    assert rel_err(got, ref) <= 1e-13
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_matvec_f64_matches_oracle_1m(rbf):
+    p = W.config_1m()
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    w = np.random.default_rng(2).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y, rbf.RBF_FP64)
+    ref = O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)
+    assert rel_err(host(y), ref) <= 1e-13
+    ctx.close()
+
+
+def test_matvec_dense_limit(rbf):
+    """A cutoff beyond the domain gives the untruncated dense product."""
+    p = W.lattice_problem(20, 1.0, seed=12)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, 10.0)
+    w = np.random.default_rng(3).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y)
+    assert rel_err(host(y), O.matvec_dense(p.xy, w, p.sigma)) <= 1e-13
+    ctx.close()
+
+
+def test_matvec_f32_error(rbf):
+    """FP32 matvec on cell-local coordinates: relative error ~1e-6 (FP32 rounding of
+    the scaled offsets, |dX|^2 up to 53 in exp2 units, and ex2.approx)."""
+    p = W.config_small()
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    w = np.random.default_rng(4).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y, rbf.RBF_FP32)
+    ref = O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)
+    assert rel_err(host(y), ref) <= 2e-5
+    ctx.close()
+
+
+# ------------------------------------------------------------------- RASM
+
+# The GPU applies stored rows of A_i^{-1} while the oracle solves with the
+# Cholesky factor; both are backward stable, so they differ by about
+# cond(A_i) * eps. cond(A_i) for the 6 x 6-point boxes at h/sigma = 0.8 is
+# about 1e4, so 1e-10 leaves a wide margin; the wider ring needs more.
+@pytest.mark.parametrize("ring,tol", [(1, 1e-10), (2, 1e-8), (0, 1e-10)])
+def test_rasm_apply_matches_oracle(rbf, ring, tol):
+    p = W.lattice_problem(40, 0.8, seed=13, ring_points=ring)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 0))
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+    v = np.random.default_rng(5).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_rasm_apply(ctx.handle, dev(v), z)
+    assert rel_err(host(z), pr.rasm_apply(v)) <= tol
+    ctx.close()
+
+
+def test_rasm_apply_f32_factors(rbf):
+    p = W.config_small()
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 1))
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+    v = np.random.default_rng(6).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_rasm_apply(ctx.handle, dev(v), z)
+    assert rel_err(host(z), pr.rasm_apply(v)) <= 1e-5
+    ctx.close()
+
+
+# ------------------------------------------------------------------- solve
+
+def solve_gpu(rbf, p, mixed=False, w0=None, **kw):
+    cfg = rbf.config_for(p, mixed=mixed, **kw)
+    ctx = rbf.Context(0)
+    xyd = dev(p.xy)
+    ctx.bin(xyd, cfg)
+    ctx.rasm_setup(cfg)
+    w = dev(np.zeros(p.n) if w0 is None else w0)
+    st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+    out = host(w)
+    ctx.close()
+    return st, info, out
+
+
+def oracle_relres(p, w):
+    r = p.f - O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)
+    return float(np.linalg.norm(r) / np.linalg.norm(p.f))
+
+
+def test_solve_f64_small_matches_oracle(rbf):
+    p = W.config_small()
+    st, info, w = solve_gpu(rbf, p)
+    assert st == 0
+    assert info.relres <= 1e-13
+    assert oracle_relres(p, w) <= 1e-13
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+    wo, oinfo = pr.solve(p.f)
+    # both solve the same SPD system to 1e-13: |dw|/|w| <= cond(A~) * 2e-13
+    assert rel_err(w, wo) <= 1e-6
+    assert abs(info.iters - oinfo.iters) <= 3, (info.iters, oinfo.iters)
+    # and the dense direct solve of the untruncated system
+    wd = O.dense_solve(p.xy, p.f, p.sigma)
+    assert rel_err(w, wd) <= 1e-6
+
+
+def test_solve_f64_1m_reaches_tolerance(rbf):
+    p = W.config_1m()
+    st, info, w = solve_gpu(rbf, p)
+    assert st == 0 and info.relres <= 1e-13
+    assert oracle_relres(p, w) <= 1e-13
+
+
+def test_solve_mixed_small(rbf):
+    p = W.config_small()
+    st, info, w = solve_gpu(rbf, p, mixed=True)
+    assert st == 0, info.as_dict()
+    assert info.refinements >= 1
+    assert oracle_relres(p, w) <= 1e-13
+
+
+def test_solve_mixed_1m(rbf):
+    p = W.config_1m()
+    st, info, w = solve_gpu(rbf, p, mixed=True)
+    assert st == 0, info.as_dict()
+    assert oracle_relres(p, w) <= 1e-13
+
+
+def test_solve_edge_single_point(rbf):
+    p = W.lattice_problem(1, 0.8, seed=1)
+    xy = np.array([[0.3, -0.2]])
+    from dataclasses import replace
+    q = replace(p, xy=xy, f=np.array([2.5]), sigma=0.1, cutoff=0.86, x0=-1.0, core_size=0.5, overlap=0.1)
+    st, info, w = solve_gpu(rbf, q)
+    assert st == 0
+    np.testing.assert_allclose(w, [2.5], rtol=1e-15)
+
+
+def test_solve_zero_rhs(rbf):
+    from dataclasses import replace
+    p = W.lattice_problem(10, 0.8, seed=2)
+    q = replace(p, f=np.zeros(p.n))
+    st, info, w = solve_gpu(rbf, q, w0=np.ones(p.n))
+    assert st == 0 and np.all(w == 0.0)
+
+
+def test_solve_warm_start_resumes(rbf):
+    """A solve stopped early returns its w; a second call continues from it."""
+    p = W.lattice_problem(48, 0.8, seed=3)
+    st, info, w1 = solve_gpu(rbf, p, max_iters=20)
+    assert st == 6 and info.iters == 20
+    st2, info2, w2 = solve_gpu(rbf, p, w0=w1)
+    assert st2 == 0 and oracle_relres(p, w2) <= 1e-13
+
+
+def test_interpolate_host_matches_device_path(rbf):
+    p = W.config_small()
+    cfg = rbf.config_for(p)
+    xy_h = torch.from_numpy(p.xy.copy()).pin_memory()
+    f_h = torch.from_numpy(p.f.copy()).pin_memory()
+    w_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    ctx = rbf.Context(0)
+    st, info = ctx.interpolate_host(xy_h, f_h, w_h, cfg)
+    assert st == 0
+    _, _, w = solve_gpu(rbf, p)
+    np.testing.assert_array_equal(w_h.numpy(), w)
+    assert ctx.launches > 0
+    ctx.close()
