@@ -47,9 +47,11 @@ FLOPS_PER_PAIR_F64 = 26
 # FP64 peak for plain (non-tensor) arithmetic: 152 SMs x 2 FP64 FMA/clk x 2 flops
 # x 2.07 GHz (matches the 1.25 TFLOP/s nominal figure for GB300).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 FMA rate of a register-only FMA loop on the same part (0.506 T FMA/s).
+FP64_MEASURED_TFLOPS = 1.012
 # DRAM bytes per launch of the FP64 matvec from ncu (profiles/), per kernel revision.
 MATVEC_F64_REV = "thread-per-target-v1"
-MATVEC_F64_TRAFFIC = {}   # {rev: bytes per launch at the bench workload}
+MATVEC_F64_TRAFFIC = {"thread-per-target-v1": 29_474_008}   # lattice1024, dram read + write
 
 WORKLOADS = {
     "lattice64": (W.config_small, "64x64 jittered lattice on [-1,1]^2 (N=4,096)"),
@@ -287,6 +289,9 @@ def run_ours(args, ws, rank, local):
                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                         "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV),
                         "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
+                        "peak_measured": FP64_MEASURED_TFLOPS,
+                        "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
+                        "kernel_rev": MATVEC_F64_REV,
                         "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR_F64,
                         "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
                         "pairs_per_s": pairs / avg_s}
