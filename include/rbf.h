@@ -66,7 +66,7 @@ typedef struct {
     double x0, y0;        /* box origin */
     double core_size;     /* B > 0 */
     double overlap;       /* delta >= 0 */
-    int max_sub_points;   /* cap on an overlap list, 1..64 (0 = 64) */
+    int max_sub_points;   /* cap on an overlap list, 1..128 (0 = 128) */
     int precision;        /* storage of the subdomain inverses: RBF_FP64 or RBF_FP32 */
 } rbf_rasm_params;
 

@@ -14,7 +14,7 @@
 namespace rbf {
 
 constexpr int kMaxRestart = 32;   // GMRES(m): m <= 32 (the CGS2 kernels keep V_k[i] in registers)
-constexpr int kMaxSub = 64;       // overlap list cap (subdomain matrix dimension)
+constexpr int kMaxSub = 128;      // overlap list cap (subdomain matrix dimension)
 constexpr int kNumSMs = 152;      // GB300
 
 // Device-resident small state of one GMRES cycle (Hessenberg, Givens, g).

@@ -182,6 +182,10 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
     const int nmax = ctx->max_ov, ncmax = ctx->max_core;
     if (nmax == 0) return RBF_OK;
     size_t per = ((size_t)nmax * nmax + (size_t)ncmax * nmax + 2 * (size_t)nmax) * sizeof(double);
+    if (per > 200u * 1024u)
+        return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
+                    "rbf_rasm_setup: a %d-point overlap list with %d core points needs %zu KB of shared memory", nmax,
+                    ncmax, per / 1024);
     // as many warps per block as fit in 200 KB of shared memory (at most kSetupWarps)
     int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, (200u * 1024u) / per));
     size_t smem = per * wpb;

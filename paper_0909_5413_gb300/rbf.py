@@ -251,7 +251,7 @@ class SolverConfig:
     overlap: float
     cell_size: float = 0.0
     normalized: bool = False
-    max_sub_points: int = 64
+    max_sub_points: int = 0
     factor_precision: int = RBF_FP64
     rtol: float = 1e-13
     restart: int = 30

@@ -151,7 +151,7 @@ def gpu_subdomains(rbf, ctx):
 def test_subdomain_lists_bit_exact(rbf, case):
     _, p = case
     ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff)
-    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 64, 0))
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 0, 0))
     (nbx, nby), cp, ci, op, oi = gpu_subdomains(rbf, ctx)
     (rbx, rby), rcp, rci, rop, roi = O.subdomains(p.xy, p.x0, p.x0, p.core_size, p.overlap)
     assert (nbx, nby) == (rbx, rby)
