@@ -136,6 +136,22 @@ rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const doubl
                                 int64_t n, const rbf_params* params, const rbf_rasm_params* rasm,
                                 const rbf_solve_params* solve, rbf_solve_info* info, rbf_stream stream);
 
+/* y = A~ w in FP64, like rbf_matvec(..., RBF_FP64, ...), without allocating.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory -- code running while a CUDA
+ * graph is captured, real-time loops that must avoid the allocator's implicit
+ * synchronisation, or applications whose device memory belongs to another
+ * framework's pool. Its two cell-order work vectors live in one file-scope
+ * __device__ array sized for n <= 1,048,576 points (16 MiB, held by every GPU
+ * that loads the library until the process exits); it calls no cudaMalloc,
+ * cudaFree or other allocating routine and records no profiler events.
+ * Errors: INVALID_ARG if the binned point count exceeds 1,048,576, STATE
+ * without rbf_bin. The first call on a device looks up the array's device
+ * address with that device current: make it before any stream capture. All
+ * calls on a device share the array, so calls that overlap on the GPU race;
+ * the array keeps the last call's contents (nothing relies on it being zero). */
+rbf_status rbf_matvec_noalloc(rbf_ctx* ctx, const double* w_dev, double* y_dev, rbf_stream stream);
+
 /* ---- parity / inspection getters (synchronous; device outputs caller-owned) ---- */
 
 /* Grid after rbf_bin: cells per axis and bounding box {xmin, ymin, xmax, ymax} (host). */

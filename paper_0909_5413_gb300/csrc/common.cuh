@@ -157,6 +157,8 @@ rbf_status export_subdomains(rbf_ctx* ctx, int32_t* core_ptr, int32_t* core_idx,
 // ---- matvec.cu  (vectors in cell order)
 rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+// The FP64 matvec launch alone (no profiler events), for the allocation-free entry point.
+rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 
 // ---- rasm.cu  (vectors in cell order)
 rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st);

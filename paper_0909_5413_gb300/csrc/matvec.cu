@@ -116,6 +116,14 @@ rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStrea
     return prof_end(ctx, RBF_PROF_MATVEC_F64, st);
 }
 
+rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, k_matvec_f64, blocks_for(ctx->n, 128), 128, 0, st, (const double2*)ctx->xy_s.p, ctx->cell_s.p,
+               ctx->cell_start.p, ctx->n, (int)ctx->ncx, (int)ctx->ncy, ctx->kst, ctx->rc2, ctx->s, ctx->knorm,
+               ctx->expc, w, y);
+    return RBF_OK;
+}
+
 // Scale of the FP32 local coordinates: a^2 = log2(e) / (2 sigma^2).
 static double local_scale(const rbf_ctx* ctx) { return std::sqrt(M_LOG2E * ctx->s); }
 

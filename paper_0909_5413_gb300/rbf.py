@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_INVALID_ARG", 2: "RBF_ERR_OOM", 3: "RBF
 EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setup", "rbf_rasm_apply", "rbf_solve",
             "rbf_interpolate_host", "rbf_get_grid", "rbf_get_bins", "rbf_get_subdomain_sizes", "rbf_get_subdomains",
             "rbf_count_neighbors", "rbf_get_neighbors", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
-            "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp"]
+            "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -99,6 +99,7 @@ def load(path: str | None = None):
     L.rbf_profile_enable.argtypes = [P, C.c_int]
     L.rbf_profile_read.argtypes = [P, C.c_int, I64, D]
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
+    L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
     for name in EXPORTED:
         if name not in ("rbf_destroy", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
                         "rbf_device_bytes"):
@@ -153,6 +154,11 @@ def rbf_bin(ctx, xy_dev, n: int, params: RbfParams, stream=None) -> None:
 
 def rbf_matvec(ctx, w_dev, y_dev, precision: int = RBF_FP64, stream=None) -> None:
     _check(ctx, load().rbf_matvec(ctx, _ptr(w_dev), _ptr(y_dev), int(precision), _stream(stream)))
+
+
+def rbf_matvec_noalloc(ctx, w_dev, y_dev, stream=None) -> None:
+    """FP64 matvec that allocates nothing (static device scratch, n <= 2^20)."""
+    _check(ctx, load().rbf_matvec_noalloc(ctx, _ptr(w_dev), _ptr(y_dev), _stream(stream)))
 
 
 def rbf_rasm_setup(ctx, params: RbfRasmParams, stream=None) -> None:
