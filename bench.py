@@ -50,7 +50,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 FMA rate of a register-only FMA loop on the same part (0.506 T FMA/s).
 FP64_MEASURED_TFLOPS = 1.012
 # DRAM bytes per launch of the FP64 matvec from ncu (profiles/), per kernel revision.
-MATVEC_F64_REV = "thread-per-target-v1"
+MATVEC_F64_REV = "cellblock-mask-v2"
 MATVEC_F64_TRAFFIC = {"thread-per-target-v1": 29_474_008}   # lattice1024, dram read + write
 
 WORKLOADS = {

@@ -194,8 +194,9 @@ rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable);
  * class's record. */
 rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double* total_ms);
 /* out[i] = exp(-t[i]) for n FP64 values on the device: variant 0 is the
- * library's own table-driven exp used by the FP64 matvec, variant 1 CUDA's
- * exp(); for accuracy checks of the former against the latter. */
+ * library's table-driven exp with 64 entries (subdomain setup), variant 2 the
+ * 2048-entry one of the FP64 matvec, variant 1 CUDA's exp(); for accuracy
+ * checks of the library's against CUDA's. */
 rbf_status rbf_debug_exp(rbf_ctx* ctx, const double* t_dev, double* out_dev, int64_t n, int variant,
                          rbf_stream stream);
 

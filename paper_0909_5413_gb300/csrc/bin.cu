@@ -130,6 +130,38 @@ __global__ void k_gather_sorted(const double* __restrict__ xy, int64_t n, const 
     cell_s[p] = cell_u[i];
 }
 
+// FP32 offsets of each point from its cell's lower corner, scaled by a with
+// a^2 = log2(e) / (2 sigma^2): the FP32 kernel value is exp2(-|dX|^2).
+__global__ void k_local_coords(const double* __restrict__ xy_s, const int32_t* __restrict__ cell_s, int64_t n,
+                               int64_t ncx, double xmin, double ymin, double c, double a, float* __restrict__ loc)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t cc = cell_s[p];
+    int64_t cx = cc % ncx, cy = cc / ncx;
+    double ox = xmin + (double)cx * c, oy = ymin + (double)cy * c;
+    loc[2 * p] = (float)((xy_s[2 * p] - ox) * a);
+    loc[2 * p + 1] = (float)((xy_s[2 * p + 1] - oy) * a);
+}
+
+// Matvec work items: cell c with m points gives ceil(m / 128) items (c, 128 q).
+__global__ void k_work_count(const int32_t* __restrict__ cell_start, int64_t ncell, int32_t* __restrict__ cnt)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) cnt[c] = (cell_start[c + 1] - cell_start[c] + 127) / 128;
+}
+
+__global__ void k_work_fill(const int32_t* __restrict__ cnt, const int32_t* __restrict__ off, int64_t ncell,
+                            int32_t* __restrict__ work)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    for (int q = 0; q < cnt[c]; ++q) {
+        work[2 * (off[c] + q)] = (int32_t)c;
+        work[2 * (off[c] + q) + 1] = 128 * q;
+    }
+}
+
 __global__ void k_permute_to_sorted(const double* __restrict__ user, const int32_t* __restrict__ perm, int64_t n,
                                     double* __restrict__ sorted)
 {
@@ -236,6 +268,20 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
                ctx->perm.p);
     RBF_LAUNCH(ctx, k_gather_sorted, blocks_for(n, 256), 256, 0, st, xy, n, ctx->perm.p, ctx->cell_u.p, ctx->xy_s.p,
                ctx->iperm.p, ctx->cell_s.p);
+    RBF_CHECK(ensure(ctx, ctx->loc32, 2 * n));
+    RBF_LAUNCH(ctx, k_local_coords, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, ctx->cell_s.p, n, ctx->ncx,
+               ctx->bbox[0], ctx->bbox[1], ctx->cell, std::sqrt(M_LOG2E * ctx->s), ctx->loc32.p);
+    RBF_CHECK(ensure(ctx, ctx->mv_wcnt, ncell + 1));
+    RBF_CHECK(ensure(ctx, ctx->mv_woff, ncell + 1));
+    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell, ctx->mv_wcnt.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell, st));
+    int32_t nwork = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&nwork, ctx->mv_woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    ctx->n_work = nwork;
+    RBF_CHECK(ensure(ctx, ctx->mv_work, 2 * (size_t)std::max<int32_t>(nwork, 1)));
+    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell,
+               ctx->mv_work.p);
     return prof_end(ctx, RBF_PROF_BIN, st);
 }
 

@@ -113,17 +113,32 @@ ExpConsts make_exp_consts()
     return c;
 }
 
+void make_exp2048(double* tab, double* c)
+{
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (int j = 0; j < kExpTab2048; ++j) tab[j] = (double)exp2l(-(long double)j / 2048.0L);
+    long double c1 = -ln2 / 2048.0L;
+    c[0] = (double)c1;
+    c[1] = (double)(c1 * c1 / 2.0L);
+    c[2] = (double)(c1 * c1 * c1 / 6.0L);
+}
+
 namespace {
 
 __global__ void k_debug_exp(const double* __restrict__ t, double* __restrict__ out, int64_t n, int variant,
-                            ExpConsts ec)
+                            ExpConsts ec, const double* __restrict__ tab2048, double c1, double c2, double c3)
 {
     __shared__ double tab[64];
     if (threadIdx.x < 64) tab[threadIdx.x] = ec.tab[threadIdx.x];
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = variant == 0 ? exp_neg(t[i], tab, ec.inv_l, ec.l_hi, ec.l_lo) : exp(-t[i]);
+    if (variant == 0)
+        out[i] = exp_neg(t[i], tab, ec.inv_l, ec.l_hi, ec.l_lo);
+    else if (variant == 1)
+        out[i] = exp(-t[i]);
+    else
+        out[i] = exp_neg_r2(t[i], 2048.0 / M_LN2, tab2048, c1, c2, c3);
 }
 
 }  // namespace
@@ -176,6 +191,13 @@ rbf_status rbf_create(rbf_ctx** out, int device)
     e = cudaMallocHost(&ctx->gm_host, sizeof(GmresDev));
     if (e != cudaSuccess) {
         delete ctx;
+        return RBF_ERR_OOM;
+    }
+    std::vector<double> tab(kExpTab2048);
+    make_exp2048(tab.data(), ctx->exp2048_c);
+    if (ensure(ctx, ctx->exp2048, kExpTab2048) != RBF_OK ||
+        cudaMemcpy(ctx->exp2048.p, tab.data(), sizeof(double) * kExpTab2048, cudaMemcpyHostToDevice) != cudaSuccess) {
+        rbf_destroy(ctx);
         return RBF_ERR_OOM;
     }
     *out = ctx;
@@ -437,10 +459,11 @@ rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double*
 rbf_status rbf_debug_exp(rbf_ctx* ctx, const double* t_dev, double* out_dev, int64_t n, int variant,
                          rbf_stream stream)
 {
-    if (!ctx || !t_dev || !out_dev || n < 0 || (variant != 0 && variant != 1)) return RBF_ERR_INVALID_ARG;
+    if (!ctx || !t_dev || !out_dev || n < 0 || variant < 0 || variant > 2) return RBF_ERR_INVALID_ARG;
     if (n == 0) return RBF_OK;
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
-    RBF_LAUNCH(ctx, k_debug_exp, blocks_for(n, 256), 256, 0, S(stream), t_dev, out_dev, n, variant, ctx->expc);
+    RBF_LAUNCH(ctx, k_debug_exp, blocks_for(n, 256), 256, 0, S(stream), t_dev, out_dev, n, variant, ctx->expc,
+               ctx->exp2048.p, ctx->exp2048_c[0], ctx->exp2048_c[1], ctx->exp2048_c[2]);
     return RBF_OK;
 }
 

@@ -72,6 +72,11 @@ struct rbf_ctx {
     rbf::DevArray<int32_t> perm, iperm, cell_start, cell_s, counts, cell_u, tmp_i32;
     rbf::DevArray<double> xy_s;    // sorted coordinates, interleaved (x, y)
     rbf::DevArray<double> bbox_part, bbox_dev;
+    rbf::DevArray<float> loc32;    // FP32 cell-local offsets scaled by sqrt(log2(e) s), interleaved
+    rbf::DevArray<int32_t> mv_work, mv_wcnt, mv_woff;   // matvec work items (cell, first target) and their scan
+    int64_t n_work = 0;
+    rbf::DevArray<double> exp2048; // 2^(-j/2048), j < 2048
+    double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)
     bool rasm_ready = false;

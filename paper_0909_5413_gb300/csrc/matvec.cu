@@ -1,9 +1,18 @@
 // matvec.cu -- the truncated Gaussian matvec y = A~ w of Sec. 2.3, matrix-free:
-// for each target i (cell order), sum over the sources j of the
+// for each target i (cell order), the sum over the sources j of the
 // (2k+1) x (2k+1) neighbour cells with r2_ij <= r_c^2 of
 // exp(-r2_ij / (2 sigma^2)) w_j. Each stencil row is one contiguous range of
-// cell-ordered sources, read directly from HBM/L2 (there is no ghost exchange
-// on one GPU).
+// cell-ordered sources, read straight from HBM/L2 (no ghost exchange on one GPU).
+//
+// FP64 kernel (GB300 runs FP64 at 1/73 of the FP32 rate, so FP64 issue slots
+// are the resource to save): one block per (cell, 128 targets); the stencil's
+// sources are staged in shared memory; each target first tests every candidate
+// in FP32 on scaled cell-local offsets (a thin band around the cutoff is
+// re-tested exactly in FP64, with the same IEEE operations as the index-list
+// definition) and keeps a bitmask of accepted sources; then the warp walks the
+// accepted sources of each lane in lockstep, so FP64 instructions are issued
+// only for accepted pairs: 2 SUB + MUL + FMA for r2 and 7 for the exp, plus
+// the accumulate FMA (12 per pair).
 #include <cmath>
 
 #include "common.cuh"
@@ -11,34 +20,138 @@
 namespace rbf {
 namespace {
 
-// FP64: one thread per target; sources of a warp's targets largely coincide,
-// so their loads are served from L1.
-__global__ void __launch_bounds__(128) k_matvec_f64(const double2* __restrict__ xy, const int32_t* __restrict__ cell_s,
-                                                    const int32_t* __restrict__ cell_start, int64_t n, int ncx, int ncy,
-                                                    int k, double rc2, double s, double knorm, ExpConsts ec,
-                                                    const double* __restrict__ w, double* __restrict__ y)
+constexpr int kMvThreads = 128;
+constexpr int kMvStage = 1536;                 // sources staged per pass
+constexpr int kMvWords = kMvStage / 32;        // mask words per lane
+constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
+
+struct MvParams {
+    const double* xy;          // cell-ordered coordinates (x, y)
+    const float* loc;          // FP32 scaled offsets from the point's cell corner (x, y)
+    const int32_t* cell_s;     // cell id of each cell-ordered point
+    const int32_t* cell_start;
+    const int32_t* work;       // (cell, first target) per block
+    const double* tab;         // 2^(-j/2048)
+    int ncx, ncy, k;
+    double rc2;                // exact cutoff (squared)
+    double K;                  // 2048 s / ln 2
+    double c1, c2, c3;         // exp cubic
+    double knorm;
+    float ca;                  // cell side in the FP32 offset units
+    float rc2f_lo, rc2f_hi;    // FP32 accept / reject thresholds around rc2 in those units
+};
+
+constexpr size_t kMvSmem = kExpTab2048 * sizeof(double)            // table
+                           + 2 * kMvStage * sizeof(double)         // staged xy
+                           + kMvStage * sizeof(double)             // staged w
+                           + 2 * kMvStage * sizeof(float)          // staged FP32 offsets
+                           + (size_t)kMvWords * kMvThreads * 4;    // accept masks
+
+__global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const double* __restrict__ w,
+                                                              double* __restrict__ y)
 {
-    __shared__ double tab[64];
-    if (threadIdx.x < 64) tab[threadIdx.x] = ec.tab[threadIdx.x];
+    extern __shared__ double smem[];
+    double* tab = smem;
+    double* SX = tab + kExpTab2048;
+    double* SW = SX + 2 * kMvStage;
+    float* SF = (float*)(SW + kMvStage);
+    uint32_t* MASK = (uint32_t*)(SF + 2 * kMvStage);
+    __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kExpTab2048; i += kMvThreads) tab[i] = P.tab[i];
+    const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
+    const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
+    const int p = cb + first + tid;
+    const bool active = p < ce;
+    const int cx = cell % P.ncx, cy = cell / P.ncx;
+    const int y0 = max(cy - P.k, 0), y1 = min(cy + P.k, P.ncy - 1);
+    const int x0 = max(cx - P.k, 0), x1 = min(cx + P.k, P.ncx - 1);
+    const int nrow = y1 - y0 + 1;
+    if (tid == 0) {
+        int s = 0;
+        for (int r = 0; r < nrow; ++r) {
+            int yy = y0 + r;
+            int b = P.cell_start[yy * P.ncx + x0], e = P.cell_start[yy * P.ncx + x1 + 1];
+            row_beg[r] = b;
+            row_pre[r] = s;
+            s += e - b;
+        }
+        row_pre[nrow] = s;
+    }
+    double xi = 0.0, yi = 0.0;
+    float fx = 0.f, fy = 0.f;
+    if (active) {
+        xi = P.xy[2 * p];
+        yi = P.xy[2 * p + 1];
+        fx = P.loc[2 * p];
+        fy = P.loc[2 * p + 1];
+    }
     __syncthreads();
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    double2 xi = xy[p];
-    int c = cell_s[p];
-    int cx = c % ncx, cy = c / ncx;
-    int y0 = max(cy - k, 0), y1 = min(cy + k, ncy - 1);
-    int x0 = max(cx - k, 0), x1 = min(cx + k, ncx - 1);
+    const int S = row_pre[nrow];
     double acc = 0.0;
-    for (int yy = y0; yy <= y1; ++yy) {
-        int b = cell_start[yy * ncx + x0], e = cell_start[yy * ncx + x1 + 1];
-        for (int q = b; q < e; ++q) {
-            double2 xj = xy[q];
-            double dx = xi.x - xj.x, dy = xi.y - xj.y;
-            double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            if (r2 <= rc2) acc = fma(exp_neg(r2 * s, tab, ec.inv_l, ec.l_hi, ec.l_lo), w[q], acc);
+    for (int base = 0; base < S; base += kMvStage) {
+        const int ns = min(kMvStage, S - base);
+        if (base > 0) __syncthreads();   // the previous pass is done with the staged data
+        for (int idx = tid; idx < ns; idx += kMvThreads) {
+            int g = base + idx;
+            int r = 0;
+            while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
+            int q = row_beg[r] + (g - row_pre[r]);
+            SX[2 * idx] = P.xy[2 * q];
+            SX[2 * idx + 1] = P.xy[2 * q + 1];
+            SW[idx] = w[q];
+            int cq = P.cell_s[q];
+            SF[2 * idx] = P.loc[2 * q] + (float)(cq % P.ncx - cx) * P.ca;
+            SF[2 * idx + 1] = P.loc[2 * q + 1] + (float)(cq / P.ncx - cy) * P.ca;
+        }
+        __syncthreads();
+        // FP32 filter: one accept bit per staged source. Sources in the thin band
+        // around the cutoff get a second bit and are settled afterwards by the
+        // exact FP64 test, in a loop of its own so that no FP64 instruction is
+        // issued (predicated or not) for the ordinary candidates.
+        const int nw = (ns + 31) >> 5;
+        for (int wi = 0; wi < nw; ++wi) {
+            uint32_t m = 0, band = 0;
+            if (active) {
+                const int lim = min(32, ns - wi * 32);
+                for (int b = 0; b < lim; ++b) {
+                    const int idx = wi * 32 + b;
+                    float dx = fx - SF[2 * idx], dy = fy - SF[2 * idx + 1];
+                    float r2 = fmaf(dy, dy, dx * dx);
+                    m |= (uint32_t)(r2 < P.rc2f_lo) << b;
+                    band |= (uint32_t)(r2 >= P.rc2f_lo && r2 <= P.rc2f_hi) << b;
+                }
+            }
+            while (band != 0u) {
+                const int b = __ffs(band) - 1;
+                band &= band - 1u;
+                const int idx = wi * 32 + b;
+                double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
+                if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= P.rc2) m |= 1u << b;
+            }
+            MASK[wi * kMvThreads + tid] = m;
+        }
+        // FP64 pairs: each lane walks its own accepted sources; the warp steps together
+        int wi = 0;
+        uint32_t cur = nw > 0 ? MASK[tid] : 0u;
+        for (;;) {
+            while (cur == 0u && wi + 1 < nw) {
+                ++wi;
+                cur = MASK[wi * kMvThreads + tid];
+            }
+            const bool has = cur != 0u;
+            if (!__any_sync(0xffffffffu, has)) break;
+            if (has) {
+                const int idx = wi * 32 + (__ffs(cur) - 1);
+                cur &= cur - 1u;
+                double dx = xi - SX[2 * idx], dy = yi - SX[2 * idx + 1];
+                double r2 = fma(dy, dy, dx * dx);
+                acc = fma(exp_neg_r2(r2, P.K, tab, P.c1, P.c2, P.c3), SW[idx], acc);
+            }
         }
     }
-    y[p] = acc * knorm;
+    if (active) y[p] = acc * P.knorm;
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -48,7 +161,7 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
-// FP32 on cell-local scaled coordinates: loc[p] = (x_p - cell origin) * a with
+// FP32 on cell-local scaled coordinates: loc[p] = (x_p - cell corner) * a with
 // a^2 = log2(e) / (2 sigma^2), so the kernel is exp2(-|dX|^2); the cell shift
 // between target and source cell is added as an integer multiple of c * a.
 __global__ void __launch_bounds__(128) k_matvec_f32(const float2* __restrict__ loc, const int32_t* __restrict__ cell_s,
@@ -82,17 +195,6 @@ __global__ void __launch_bounds__(128) k_matvec_f32(const float2* __restrict__ l
     y[p] = acc * knorm;
 }
 
-__global__ void k_local_coords(const double* __restrict__ xy_s, const int32_t* __restrict__ cell_s, int64_t n,
-                               int ncx, double xmin, double ymin, double c, double a, float2* __restrict__ loc)
-{
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int cc = cell_s[p];
-    int cx = cc % ncx, cy = cc / ncx;
-    double ox = xmin + (double)cx * c, oy = ymin + (double)cy * c;
-    loc[p] = make_float2((float)((xy_s[2 * p] - ox) * a), (float)((xy_s[2 * p + 1] - oy) * a));
-}
-
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,35 +207,57 @@ __global__ void k_to_f64(const float* __restrict__ in, int64_t n, double* __rest
     if (i < n) out[i] = (double)in[i];
 }
 
+// Scale of the FP32 local coordinates: a^2 = log2(e) / (2 sigma^2).
+double local_scale(const rbf_ctx* ctx) { return std::sqrt(M_LOG2E * ctx->s); }
+
+MvParams mv_params(const rbf_ctx* ctx)
+{
+    MvParams P;
+    P.xy = ctx->xy_s.p;
+    P.loc = ctx->loc32.p;
+    P.cell_s = ctx->cell_s.p;
+    P.cell_start = ctx->cell_start.p;
+    P.work = ctx->mv_work.p;
+    P.tab = ctx->exp2048.p;
+    P.ncx = (int)ctx->ncx;
+    P.ncy = (int)ctx->ncy;
+    P.k = ctx->kst;
+    P.rc2 = ctx->rc2;
+    P.K = 2048.0 * ctx->s / M_LN2;
+    P.c1 = ctx->exp2048_c[0];
+    P.c2 = ctx->exp2048_c[1];
+    P.c3 = ctx->exp2048_c[2];
+    P.knorm = ctx->knorm;
+    double a = local_scale(ctx);
+    P.ca = (float)(ctx->cell * a);
+    double rc2f = ctx->rc2 * a * a;
+    P.rc2f_lo = (float)(rc2f * (1.0 - 1e-4));
+    P.rc2f_hi = (float)(rc2f * (1.0 + 1e-4));
+    return P;
+}
+
 }  // namespace
+
+rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+{
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMvSmem));
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared));
+    if (ctx->n_work == 0) return RBF_OK;
+    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMvThreads, kMvSmem, st, mv_params(ctx), w, y);
+    return RBF_OK;
+}
 
 rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_MATVEC_F64, st));
-    RBF_LAUNCH(ctx, k_matvec_f64, blocks_for(ctx->n, 128), 128, 0, st, (const double2*)ctx->xy_s.p, ctx->cell_s.p,
-               ctx->cell_start.p, ctx->n, (int)ctx->ncx, (int)ctx->ncy, ctx->kst, ctx->rc2, ctx->s, ctx->knorm,
-               ctx->expc, w, y);
+    RBF_CHECK(matvec_sorted_f64_plain(ctx, w, y, st));
     return prof_end(ctx, RBF_PROF_MATVEC_F64, st);
 }
 
-rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t)
 {
-    RBF_LAUNCH(ctx, k_matvec_f64, blocks_for(ctx->n, 128), 128, 0, st, (const double2*)ctx->xy_s.p, ctx->cell_s.p,
-               ctx->cell_start.p, ctx->n, (int)ctx->ncx, (int)ctx->ncy, ctx->kst, ctx->rc2, ctx->s, ctx->knorm,
-               ctx->expc, w, y);
-    return RBF_OK;
-}
-
-// Scale of the FP32 local coordinates: a^2 = log2(e) / (2 sigma^2).
-static double local_scale(const rbf_ctx* ctx) { return std::sqrt(M_LOG2E * ctx->s); }
-
-rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t st)
-{
-    // stored after the FP32 work vectors in vec_c (2 floats per point = 1 double)
-    RBF_CHECK(ensure(ctx, ctx->vec_c, (size_t)ctx->n * 2));
-    *loc = (float2*)ctx->vec_c.p;
-    RBF_LAUNCH(ctx, k_local_coords, blocks_for(ctx->n, 256), 256, 0, st, ctx->xy_s.p, ctx->cell_s.p, ctx->n,
-               (int)ctx->ncx, ctx->bbox[0], ctx->bbox[1], ctx->cell, local_scale(ctx), *loc);
+    *loc = (float2*)ctx->loc32.p;
     return RBF_OK;
 }
 
@@ -151,7 +275,8 @@ rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStrea
 {
     float2* loc = nullptr;
     RBF_CHECK(ensure_local_coords(ctx, &loc, st));
-    float* wf = (float*)(ctx->vec_c.p + ctx->n);   // second half of vec_c
+    RBF_CHECK(ensure(ctx, ctx->vec_c, (size_t)ctx->n));   // two FP32 vectors
+    float* wf = (float*)ctx->vec_c.p;
     float* yf = wf + ctx->n;
     RBF_LAUNCH(ctx, k_to_f32, blocks_for(ctx->n, 256), 256, 0, st, w, ctx->n, wf);
     RBF_CHECK(matvec_f32_raw(ctx, loc, wf, yf, st));

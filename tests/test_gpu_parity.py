@@ -213,6 +213,34 @@ def test_state_errors(rbf):
     ctx.close()
 
 
+# --------------------------------------------------------------------- exp
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_library_exp_against_cuda_exp(rbf, variant):
+    """The table-driven exps (Tang's method, 64 and 2048 entries) agree with
+    CUDA's exp() to a few ulp plus t ulp: the 2048-entry variant folds the
+    rounded constant 2048/ln 2 into its argument, an error of t * eps relative
+    (below 1e-14 for t <= 37, the cutoff range; the same order as rounding the
+    constant 1/(2 sigma^2) itself)."""
+    ctx = rbf.Context(0)
+    rng = np.random.default_rng(variant)
+    t = np.concatenate([rng.uniform(0.0, 40.0, 200000), rng.uniform(0.0, 670.0, 50000),
+                        np.array([0.0, 1e-300, 1e-12, 0.5, 36.98, 100.0, 669.9]),
+                        np.arange(0, 40, 1.0 / 64)])
+    td = dev(t)
+    a = torch.empty_like(td)
+    b = torch.empty_like(td)
+    rbf.rbf_debug_exp(ctx.handle, td, a, variant)
+    rbf.rbf_debug_exp(ctx.handle, td, b, 1)
+    got, ref = host(a), host(b)
+    rel = np.abs(got - ref) / ref
+    bound = 4 * 2.0 ** -52 + t * 2.0 ** -52
+    assert np.all(rel <= bound), (rel.max(), t[(rel / bound).argmax()])
+    inside = t <= 37.0
+    assert rel[inside].max() <= 1e-14
+    ctx.close()
+
+
 # ------------------------------------------------------------------ matvec
 
 def matvec_cases():
