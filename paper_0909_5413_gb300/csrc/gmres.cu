@@ -29,60 +29,167 @@ namespace {
 constexpr int kDotThreads = 256;
 constexpr int kDotBlocksMax = 8 * kNumSMs;
 
-// MODE 0: acc_k = sum_i V_k[i] x[i]
-// MODE 1: x[i] -= sum_k coef_k V_k[i];  acc_k = sum_i V_k[i] x[i] (updated x)
-// MODE 2: x[i] -= sum_k coef_k V_k[i];  acc_0 = sum_i x[i]^2
-// partial[block * 32 + k] receives the block's sums (fixed order).
-template <int MODE, int NV, class T>
+// Vector passes of one Arnoldi step, each a single stream over HBM. The vector
+// range is cut into chunks of kChunk elements; block partial sums go to
+// partial[chunk * 32 + k] and are reduced over chunks in a fixed order.
+constexpr int kChunkPerThread = 16;
+constexpr int kChunk = kDotThreads * kChunkPerThread;
+
+__device__ __forceinline__ double block_sum(double a, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
+    return s;
+}
+
+// Double-float accumulator for FP32 data (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26(6), 2005: TwoProduct by FMA,
+// TwoSum, and the Dot2 recurrence): a sum of exact FP32 products carried as an
+// unevaluated hi + lo pair, as accurate as accumulating in twice the FP32
+// precision. On GB300 this keeps FP64-class dot products on the FP32 pipe.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DF& s, float h, float r)
+{
+    float p = s.hi + h;                 // TwoSum(s.hi, h) = (p, q)
+    float z = p - s.hi;
+    float q = (s.hi - (p - z)) + (h - z);
+    s.hi = p;
+    s.lo = s.lo + (q + r);
+}
+
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b)
+{
+    float h = a * b;                    // TwoProduct(a, b) = (h, r)
+    float r = fmaf(a, b, -h);
+    df_add(s, h, r);
+}
+
+// Dots V_k . x for k < nv: block (k, chunk), k fastest so that the blocks
+// reading one chunk of x run together and find it in L2. FP64 accumulation
+// for FP64 vectors; Dot2 (then FP64) for FP32 vectors.
+template <class T>
 __global__ void __launch_bounds__(kDotThreads)
-    k_mdot(const T* __restrict__ V, int64_t ldv, int nv, T* __restrict__ x, int64_t n, const double* __restrict__ coef,
+    k_dots(const T* __restrict__ V, int64_t ldv, int nv, const T* __restrict__ x, int64_t n,
            double* __restrict__ partial)
 {
-    __shared__ double red[kDotThreads / 32][NV];
-    __shared__ double cf[NV];
-    if (MODE != 0) {
-        if (threadIdx.x < NV) cf[threadIdx.x] = (threadIdx.x < (unsigned)nv) ? coef[threadIdx.x] : 0.0;
-        __syncthreads();
+    __shared__ double red[kDotThreads / 32];
+    const int k = (int)(blockIdx.x % (unsigned)nv);
+    const int64_t chunk = blockIdx.x / (unsigned)nv;
+    const int64_t base = chunk * kChunk + threadIdx.x;
+    const T* v = V + k * ldv;
+    double a = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF s{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            if (i < n) df_add_prod(s, v[i], x[i]);
+        }
+        a = (double)s.hi + (double)s.lo;
+    } else {
+#pragma unroll
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            if (i < n) a = fma((double)v[i], (double)x[i], a);
+        }
     }
-    double acc[NV];
+    double s = block_sum(a, red);
+    if (threadIdx.x == 0) partial[chunk * 32 + k] = s;
+}
+
+// x -= sum_{k < nv} coef_k V_k (x rounded to T); with NORM, partial sums of |x|^2.
+// FP32 vectors: the FP64 coefficients are split into float pairs and the
+// update is carried in double-float, then rounded once to FP32.
+template <class T, bool NORM>
+__global__ void __launch_bounds__(kDotThreads)
+    k_update(const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef, T* __restrict__ x,
+             int64_t n, double* __restrict__ partial)
+{
+    __shared__ double cf[kMaxRestart + 1];
+    __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
+    __shared__ double red[kDotThreads / 32];
+    if (threadIdx.x < (unsigned)nv) {
+        double c = coef[threadIdx.x];
+        cf[threadIdx.x] = c;
+        float h = (float)c;
+        cf_hi[threadIdx.x] = h;
+        cf_lo[threadIdx.x] = (float)(c - (double)h);
+    }
+    __syncthreads();
+    const int64_t chunk = blockIdx.x;
+    const int64_t base = chunk * kChunk + threadIdx.x;
+    double a = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF xl[kChunkPerThread];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double xi = (double)x[i];
-        if (MODE == 0) {
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            xl[u].hi = i < n ? (float)x[i] : 0.f;
+            xl[u].lo = 0.f;
+        }
+        for (int k = 0; k < nv; ++k) {
+            const T* v = V + k * ldv;
+            const float ch = cf_hi[k], cl = cf_lo[k];
 #pragma unroll
-            for (int k = 0; k < NV; ++k)
-                if (k < nv) acc[k] = fma((double)V[k * ldv + i], xi, acc[k]);
-        } else {
-            double v[NV];
+            for (int u = 0; u < kChunkPerThread; ++u) {
+                int64_t i = base + (int64_t)u * kDotThreads;
+                if (i < n) {
+                    float vi = v[i];
+                    float h = ch * vi;
+                    float r = fmaf(ch, vi, -h);
+                    df_add(xl[u], -h, fmaf(-cl, vi, -r));
+                }
+            }
+        }
+        DF s{0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < NV; ++k) v[k] = (k < nv) ? (double)V[k * ldv + i] : 0.0;
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            if (i < n) {
+                float xs = xl[u].hi + xl[u].lo;
+                x[i] = xs;
+                if (NORM) df_add_prod(s, xs, xs);
+            }
+        }
+        a = (double)s.hi + (double)s.lo;
+    } else {
+        // vector index outermost, the thread's 16 elements innermost: 16 independent loads in flight
+        double xl[kChunkPerThread];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) xi = fma(-cf[k], v[k], xi);
-            T xs = (T)xi;
-            x[i] = xs;
-            xi = (double)xs;
-            if (MODE == 1) {
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            xl[u] = i < n ? (double)x[i] : 0.0;
+        }
+        for (int k = 0; k < nv; ++k) {
+            const T* v = V + k * ldv;
+            const double c = cf[k];
 #pragma unroll
-                for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], xi, acc[k]);
-            } else {
-                acc[0] = fma(xi, xi, acc[0]);
+            for (int u = 0; u < kChunkPerThread; ++u) {
+                int64_t i = base + (int64_t)u * kDotThreads;
+                if (i < n) xl[u] = fma(-c, (double)v[i], xl[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kChunkPerThread; ++u) {
+            int64_t i = base + (int64_t)u * kDotThreads;
+            if (i < n) {
+                T xs = (T)xl[u];
+                x[i] = xs;
+                if (NORM) a = fma((double)xs, (double)xs, a);
             }
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NR = (MODE == 2) ? 1 : NV;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        double a = acc[k];
-        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
-        if (lane == 0) red[warp][k] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < NR) {
-        double a = 0.0;
-        for (int w = 0; w < kDotThreads / 32; ++w) a += red[w][threadIdx.x];
-        partial[(int64_t)blockIdx.x * 32 + threadIdx.x] = a;
+    if (NORM) {
+        double s = block_sum(a, red);
+        if (threadIdx.x == 0) partial[chunk * 32] = s;
     }
 }
 
@@ -177,26 +284,43 @@ __global__ void k_solve_y(GmresDev* g, int k)
     }
 }
 
+// x *= factor (an FP32 vector is scaled in FP32: it is rounded to FP32 anyway)
 template <class T>
 __global__ void k_scale(T* __restrict__ x, int64_t n, const double* __restrict__ factor)
 {
-    double f = *factor;
+    const T f = (T)*factor;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (T)((double)x[i] * f);
+        x[i] = x[i] * f;
 }
 
-// t = sum_{q<k} y_q V_q
+// t = sum_{q<k} y_q V_q (double-float for FP32 vectors)
 template <class T>
 __global__ void k_combine(const T* __restrict__ V, int64_t ldv, int k, const double* __restrict__ y,
                           T* __restrict__ t, int64_t n)
 {
     __shared__ double ys[kMaxRestart];
-    if (threadIdx.x < (unsigned)k) ys[threadIdx.x] = y[threadIdx.x];
+    __shared__ float yh[kMaxRestart], yl[kMaxRestart];
+    if (threadIdx.x < (unsigned)k) {
+        double c = y[threadIdx.x];
+        ys[threadIdx.x] = c;
+        yh[threadIdx.x] = (float)c;
+        yl[threadIdx.x] = (float)(c - (double)(float)c);
+    }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double a = 0.0;
-        for (int q = 0; q < k; ++q) a = fma(ys[q], (double)V[q * ldv + i], a);
-        t[i] = (T)a;
+        if constexpr (sizeof(T) == 4) {
+            DF a{0.f, 0.f};
+            for (int q = 0; q < k; ++q) {
+                float vi = V[q * ldv + i];
+                float h = yh[q] * vi;
+                df_add(a, h, fmaf(yl[q], vi, fmaf(yh[q], vi, -h)));
+            }
+            t[i] = a.hi + a.lo;
+        } else {
+            double a = 0.0;
+            for (int q = 0; q < k; ++q) a = fma(ys[q], (double)V[q * ldv + i], a);
+            t[i] = (T)a;
+        }
     }
 }
 
@@ -237,25 +361,29 @@ unsigned stream_blocks(int64_t n)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-template <int MODE, int NV, class T>
-rbf_status launch_mdot_nv(rbf_ctx* ctx, const T* V, int64_t ldv, int nv, T* x, int64_t n, const double* coef,
-                          double* out, cudaStream_t st)
-{
-    unsigned nb = dot_blocks(n);
-    RBF_LAUNCH(ctx, (k_mdot<MODE, NV, T>), nb, kDotThreads, 0, st, V, ldv, nv, x, n, coef, ctx->partial.p);
-    int nr = (MODE == 2) ? 1 : nv;
-    RBF_LAUNCH(ctx, k_reduce, 1, 32 * nr, 0, st, ctx->partial.p, (int)nb, nr, out);
-    return RBF_OK;
-}
+int64_t num_chunks(int64_t n) { return std::max<int64_t>(1, (n + kChunk - 1) / kChunk); }
 
+// MODE 0: out_k = V_k . x                      (one pass)
+// MODE 1: x -= V coef, then out_k = V_k . x    (two passes)
+// MODE 2: x -= V coef, out_0 = |x|^2           (one pass)
 template <int MODE, class T>
 rbf_status launch_mdot(rbf_ctx* ctx, const T* V, int64_t ldv, int nv, T* x, int64_t n, const double* coef,
                        double* out, cudaStream_t st)
 {
-    if (nv <= 4) return launch_mdot_nv<MODE, 4, T>(ctx, V, ldv, nv, x, n, coef, out, st);
-    if (nv <= 8) return launch_mdot_nv<MODE, 8, T>(ctx, V, ldv, nv, x, n, coef, out, st);
-    if (nv <= 16) return launch_mdot_nv<MODE, 16, T>(ctx, V, ldv, nv, x, n, coef, out, st);
-    return launch_mdot_nv<MODE, 32, T>(ctx, V, ldv, nv, x, n, coef, out, st);
+    const int64_t nc = num_chunks(n);
+    if (MODE == 2) {
+        RBF_LAUNCH(ctx, (k_update<T, true>), (unsigned)nc, kDotThreads, 0, st, V, ldv, nv, coef, x, n,
+                   ctx->partial.p);
+        RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nc, 1, out);
+        return RBF_OK;
+    }
+    if (MODE == 1)
+        RBF_LAUNCH(ctx, (k_update<T, false>), (unsigned)nc, kDotThreads, 0, st, V, ldv, nv, coef, x, n,
+                   ctx->partial.p);
+    RBF_LAUNCH(ctx, (k_dots<T>), (unsigned)(nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, n,
+               ctx->partial.p);
+    RBF_LAUNCH(ctx, k_reduce, 1, 32 * nv, 0, st, ctx->partial.p, (int)nc, nv, out);
+    return RBF_OK;
 }
 
 struct StepStatus {
@@ -361,7 +489,7 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
     const int max_iters = p->max_iters > 0 ? p->max_iters : 10000;
     const bool mixed = p->mixed != 0;
     RBF_CHECK(ensure(ctx, ctx->gm, 1));
-    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)kDotBlocksMax * 32));
+    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(kDotBlocksMax, num_chunks(n)) * 32));
     RBF_CHECK(ensure(ctx, ctx->vec_a, n));
     RBF_CHECK(ensure(ctx, ctx->vec_b, n));
     GmresDev* g = ctx->gm.p;

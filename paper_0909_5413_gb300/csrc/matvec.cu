@@ -161,38 +161,103 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
-// FP32 on cell-local scaled coordinates: loc[p] = (x_p - cell corner) * a with
-// a^2 = log2(e) / (2 sigma^2), so the kernel is exp2(-|dX|^2); the cell shift
-// between target and source cell is added as an integer multiple of c * a.
-__global__ void __launch_bounds__(128) k_matvec_f32(const float2* __restrict__ loc, const int32_t* __restrict__ cell_s,
-                                                    const int32_t* __restrict__ cell_start, int64_t n, int ncx, int ncy,
-                                                    int k, float ca, float rc2s, float knorm,
-                                                    const float* __restrict__ w, float* __restrict__ y)
+// Packed FP32 pairs (two lanes of work per instruction on sm_100-class SMs).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    float2 xi = loc[p];
-    int c = cell_s[p];
-    int cx = c % ncx, cy = c / ncx;
-    int y0 = max(cy - k, 0), y1 = min(cy + k, ncy - 1);
-    int x0 = max(cx - k, 0), x1 = min(cx + k, ncx - 1);
-    float acc = 0.0f;
-    for (int yy = y0; yy <= y1; ++yy) {
-        float ty = xi.y - (float)(yy - cy) * ca;
-        for (int xx = x0; xx <= x1; ++xx) {
-            float tx = xi.x - (float)(xx - cx) * ca;
-            int cc = yy * ncx + xx;
-            int b = cell_start[cc], e = cell_start[cc + 1];
-            for (int q = b; q < e; ++q) {
-                float2 xj = loc[q];
-                float dx = tx - xj.x, dy = ty - xj.y;
-                float r2 = fmaf(dy, dy, dx * dx);
-                float ev = ex2_approx(-r2);
-                acc = (r2 <= rc2s) ? fmaf(ev, w[q], acc) : acc;
-            }
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b),
+                          Cc = *reinterpret_cast<unsigned long long*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(A), "l"(B), "l"(Cc));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+constexpr int kMv32Stage = 3072;   // sources staged per pass (even; 36 KB of static shared memory)
+
+// FP32 matvec for the inner solves of the mixed form: block per (cell, 128
+// targets), sources staged in shared memory as FP32 offsets from the target
+// cell's corner (scaled so the kernel is exp2(-|dX|^2)), two sources per
+// packed f32x2 step. No cutoff mask: the entries beyond r_c that this adds
+// back are below 2^-53 relative to the diagonal, far under FP32 rounding, and
+// the outer FP64 residual uses the exact truncated matrix.
+__global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const float* __restrict__ w,
+                                                               float* __restrict__ y)
+{
+    __shared__ __align__(16) float SXs[kMv32Stage + 2], SYs[kMv32Stage + 2], SWs[kMv32Stage + 2];
+    __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
+    const int tid = threadIdx.x;
+    const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
+    const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
+    const int p = cb + first + tid;
+    const bool active = p < ce;
+    const int cx = cell % P.ncx, cy = cell / P.ncx;
+    const int y0 = max(cy - P.k, 0), y1 = min(cy + P.k, P.ncy - 1);
+    const int x0 = max(cx - P.k, 0), x1 = min(cx + P.k, P.ncx - 1);
+    const int nrow = y1 - y0 + 1;
+    if (tid == 0) {
+        int s = 0;
+        for (int r = 0; r < nrow; ++r) {
+            int yy = y0 + r;
+            int b = P.cell_start[yy * P.ncx + x0], e = P.cell_start[yy * P.ncx + x1 + 1];
+            row_beg[r] = b;
+            row_pre[r] = s;
+            s += e - b;
+        }
+        row_pre[nrow] = s;
+    }
+    float2 t2 = make_float2(0.f, 0.f), u2 = make_float2(0.f, 0.f);
+    if (active) {
+        float fx = P.loc[2 * p], fy = P.loc[2 * p + 1];
+        t2 = make_float2(fx, fx);
+        u2 = make_float2(fy, fy);
+    }
+    __syncthreads();
+    const int S = row_pre[nrow];
+    float2 acc2 = make_float2(0.f, 0.f);
+    for (int base = 0; base < S; base += kMv32Stage) {
+        const int ns = min(kMv32Stage, S - base);
+        if (base > 0) __syncthreads();
+        for (int idx = tid; idx < ns; idx += kMvThreads) {
+            int g = base + idx;
+            int r = 0;
+            while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
+            int q = row_beg[r] + (g - row_pre[r]);
+            int cq = P.cell_s[q];
+            SXs[idx] = P.loc[2 * q] + (float)(cq % P.ncx - cx) * P.ca;
+            SYs[idx] = P.loc[2 * q + 1] + (float)(cq / P.ncx - cy) * P.ca;
+            SWs[idx] = w[q];
+        }
+        if (tid == 0 && (ns & 1)) {   // pad to an even count with a far, zero-weight source
+            SXs[ns] = 1.0e4f;
+            SYs[ns] = 1.0e4f;
+            SWs[ns] = 0.0f;
+        }
+        __syncthreads();
+        const int ns2 = (ns + 1) >> 1;
+#pragma unroll 4
+        for (int s = 0; s < ns2; ++s) {
+            float2 sx = reinterpret_cast<const float2*>(SXs)[s];
+            float2 sy = reinterpret_cast<const float2*>(SYs)[s];
+            float2 sw = reinterpret_cast<const float2*>(SWs)[s];
+            float2 dx = f2_sub(t2, sx), dy = f2_sub(u2, sy);
+            float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
+            float2 e = make_float2(ex2_approx(-r2.x), ex2_approx(-r2.y));
+            acc2 = f2_fma(e, sw, acc2);
         }
     }
-    y[p] = acc * knorm;
+    if (active) y[p] = (acc2.x + acc2.y) * (float)P.knorm;
 }
 
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
@@ -261,13 +326,11 @@ rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t)
     return RBF_OK;
 }
 
-rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float* y, cudaStream_t st)
+rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y, cudaStream_t st)
 {
-    double a = local_scale(ctx);
     RBF_CHECK(prof_begin(ctx, RBF_PROF_MATVEC_F32, st));
-    RBF_LAUNCH(ctx, k_matvec_f32, blocks_for(ctx->n, 128), 128, 0, st, loc, ctx->cell_s.p, ctx->cell_start.p, ctx->n,
-               (int)ctx->ncx, (int)ctx->ncy, ctx->kst, (float)(ctx->cell * a), (float)(ctx->rc2 * a * a),
-               (float)ctx->knorm, w, y);
+    if (ctx->n_work > 0)
+        RBF_LAUNCH(ctx, k_matvec_f32v2, (unsigned)ctx->n_work, kMvThreads, 0, st, mv_params(ctx), w, y);
     return prof_end(ctx, RBF_PROF_MATVEC_F32, st);
 }
 

@@ -390,6 +390,17 @@ def test_solve_mixed_1m(rbf):
     assert oracle_relres(p, w) <= 1e-13
 
 
+@pytest.mark.slow
+def test_solve_mixed_51m_reaches_tolerance(rbf):
+    """The 7168 x 7168 lattice (N = 51,380,224) with FP32 inner solves: the true
+    relative residual, recomputed by the oracle's FP64 matvec on the host, is
+    <= 1e-13."""
+    p = W.config_51m()
+    st, info, w = solve_gpu(rbf, p, mixed=True, factor_precision=rbf.RBF_FP32)
+    assert st == 0, info.as_dict()
+    assert oracle_relres(p, w) <= 1e-13
+
+
 def test_solve_edge_single_point(rbf):
     p = W.lattice_problem(1, 0.8, seed=1)
     xy = np.array([[0.3, -0.2]])
