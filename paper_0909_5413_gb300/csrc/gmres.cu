@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(kDotThreads)
 // inner solve of the mixed form (inner = 1) the reference norm is |r| itself.
 __global__ void k_cycle_init(GmresDev* g, int m, int inner)
 {
-    if (inner) g->fnorm2 = g->beta2;
+    if (inner == 1) g->fnorm2 = g->beta2;
+    if (inner == 2) g->fnorm2 = 1.0;   // inner solve on a right-hand side of norm 1
     double beta = sqrt(g->beta2);
     double fn = sqrt(g->fnorm2);
     for (int q = 0; q <= m; ++q) g->g[q] = 0.0;
@@ -332,6 +333,36 @@ __global__ void k_axpy(double* __restrict__ w, const T* __restrict__ u, int64_t 
         w[i] += (double)u[i];
 }
 
+template <class T>
+__global__ void k_axpy_same(T* __restrict__ w, const T* __restrict__ u, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] += u[i];
+}
+
+// w += a * d (FP64 w, FP32 d): the refinement update of the mixed form.
+__global__ void k_axpy_scaled(double* __restrict__ w, const float* __restrict__ d, double a, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = fma(a, (double)d[i], w[i]);
+}
+
+// Inner residual of the mixed form: r = b - t (FP32); Dot2 partial sums of |r|^2.
+__global__ void __launch_bounds__(kDotThreads)
+    k_inner_residual(const float* __restrict__ b, const float* __restrict__ t, float* __restrict__ r, int64_t n,
+                     double* __restrict__ partial)
+{
+    __shared__ double red[kDotThreads / 32];
+    DF s{0.f, 0.f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = b[i] - t[i];
+        r[i] = v;
+        df_add_prod(s, v, v);
+    }
+    double tot = block_sum((double)s.hi + (double)s.lo, red);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 32] = tot;
+}
+
 // FP32 copy of an FP64 vector scaled by a device factor: out = in * (*factor)
 __global__ void k_to_f32_scaled(const double* __restrict__ in, int64_t n, const double* __restrict__ factor,
                                 float* __restrict__ out)
@@ -427,10 +458,12 @@ struct OpsF32 {
 
 // One GMRES cycle on vectors of type T starting from V_0 = r / |r| (V_0 holds
 // r on entry and beta2 is in g->beta2). Accumulates the correction
-// M^{-1} V y into w (FP64). Returns the number of Arnoldi steps.
+// M^{-1} V y into w (FP64) or, if wT is given, into wT. Returns the number of
+// Arnoldi steps.
 template <class T, class Ops>
 rbf_status gmres_cycle(rbf_ctx* ctx, T* V, int64_t ldv, int m, int max_steps, T* tmp_u, T* tmp_t, double* w,
-                       const float2* loc, bool scale_v0, cudaStream_t st, int* steps, double* est, int* applies)
+                       T* wT, const float2* loc, bool scale_v0, cudaStream_t st, int* steps, double* est,
+                       int* applies)
 {
     const int64_t n = ctx->n;
     GmresDev* g = ctx->gm.p;
@@ -458,7 +491,10 @@ rbf_status gmres_cycle(rbf_ctx* ctx, T* V, int64_t ldv, int m, int max_steps, T*
     RBF_LAUNCH(ctx, (k_combine<T>), stream_blocks(n), 256, 0, st, V, ldv, k, g->y, tmp_t, n);
     RBF_CHECK(Ops::minv(ctx, tmp_t, tmp_u, st));
     ++*applies;
-    RBF_LAUNCH(ctx, (k_axpy<T>), stream_blocks(n), 256, 0, st, w, tmp_u, n);
+    if (wT)
+        RBF_LAUNCH(ctx, (k_axpy_same<T>), stream_blocks(n), 256, 0, st, wT, tmp_u, n);
+    else
+        RBF_LAUNCH(ctx, (k_axpy<T>), stream_blocks(n), 256, 0, st, w, tmp_u, n);
     *steps = k;
     *est = ss.est;
     return RBF_OK;
@@ -526,7 +562,7 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
             RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 0);
             int steps = 0;
             RBF_CHECK((gmres_cycle<double, OpsF64>(ctx, V, n, m, max_iters - it, ctx->vec_b.p, ctx->vec_a.p, w,
-                                                   nullptr, true, st, &steps, &est, &applies)));
+                                                   (double*)nullptr, nullptr, true, st, &steps, &est, &applies)));
             it += steps;
             matvecs += steps;
             ++cycles;
@@ -542,28 +578,61 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
         }
         float2* loc = nullptr;
         RBF_CHECK(ensure_local_coords(ctx, &loc, st));
-        // FP32 Krylov basis plus two FP32 work vectors, in V's storage
+        // FP32 Krylov basis and four FP32 work vectors (u, t, b, d), in V's storage
         const int64_t ldv = ((n + 63) / 64) * 64;
-        RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 3) * ldv + 1) / 2 + 1));
+        RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 5) * ldv + 1) / 2 + 1));
         float* Vf = (float*)ctx->V.p;
         float* uf = Vf + (int64_t)(m + 1) * ldv;
         float* tf = uf + ldv;
+        float* bf = tf + ldv;   // inner right-hand side r / |r|
+        float* df = bf + ldv;   // inner solution
         double* r64 = ctx->vec_b.p;
+        const double inner_rtol = p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5;
+        // One inner cycle per refinement step: restarting the inner solve on the
+        // FP32 residual b - A d stalls near 1e-3, because A d is formed from
+        // entries much larger than the result (cancellation in FP32 once the
+        // correction d is large on an ill-conditioned system). Every restart
+        // therefore starts from the FP64 residual, which is the refinement step.
+        constexpr int kMaxInnerCycles = 1;
         for (;;) {
             RBF_CHECK(true_residual(ctx, f, w, ctx->vec_a.p, r64, st, fnorm, &relres));
             ++matvecs;
             if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
             if (relres <= p->rtol) { result = RBF_OK; break; }
             if (it >= max_iters || refine >= max_refine) break;
-            // inner solve from d = 0: V_0 = r / |r| in FP32 (beta2 already on the device)
-            RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 1);
-            RBF_LAUNCH(ctx, k_to_f32_scaled, stream_blocks(n), 256, 0, st, r64, n, &g->inv_beta, Vf);
-            int steps = 0;
-            RBF_CHECK((gmres_cycle<float, OpsF32>(ctx, Vf, ldv, m, max_iters - it, uf, tf, w, loc, false, st, &steps,
-                                                  &est, &applies)));
-            it += steps;
-            matvecs += steps;
-            ++cycles;
+            const double rnorm = relres * fnorm;
+            // inner solve of A d = b, b = r / |r| (norm 1), from d = 0, restarted on
+            // the FP32 inner residual b - A d until inner_rtol or kMaxInnerCycles
+            RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 1);   // inv_beta = 1 / |r|
+            RBF_LAUNCH(ctx, k_to_f32_scaled, stream_blocks(n), 256, 0, st, r64, n, &g->inv_beta, bf);
+            RBF_CUDA(ctx, cudaMemsetAsync(df, 0, sizeof(float) * n, st));
+            for (int ic = 0; ic < kMaxInnerCycles && it < max_iters; ++ic) {
+                if (ic == 0) {
+                    RBF_CUDA(ctx, cudaMemcpyAsync(Vf, bf, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+                } else {
+                    RBF_CHECK(OpsF32::amul(ctx, df, tf, st, loc));
+                    ++matvecs;
+                }
+                if (ic > 0) {
+                    unsigned nb = dot_blocks(n);
+                    RBF_LAUNCH(ctx, k_inner_residual, nb, kDotThreads, 0, st, bf, tf, Vf, n, ctx->partial.p);
+                    RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nb, 1, &g->beta2);
+                } else {
+                    RBF_CHECK((launch_mdot<0, float>(ctx, Vf, 0, 1, Vf, n, nullptr, &g->beta2, st)));
+                }
+                RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 2);
+                StepStatus s0{0.0, 0};
+                RBF_CHECK(read_status(ctx, st, &s0));
+                if (ic > 0 && s0.est <= inner_rtol) break;
+                int steps = 0;
+                RBF_CHECK((gmres_cycle<float, OpsF32>(ctx, Vf, ldv, m, max_iters - it, uf, tf, nullptr, df, loc, true,
+                                                      st, &steps, &est, &applies)));
+                it += steps;
+                matvecs += steps;
+                ++cycles;
+                if (est <= inner_rtol) break;
+            }
+            RBF_LAUNCH(ctx, k_axpy_scaled, stream_blocks(n), 256, 0, st, w, df, rnorm, n);
             ++refine;
         }
     }
