@@ -152,6 +152,30 @@ rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const doubl
  * the array keeps the last call's contents (nothing relies on it being zero). */
 rbf_status rbf_matvec_noalloc(rbf_ctx* ctx, const double* w_dev, double* y_dev, rbf_stream stream);
 
+/* ---- batches of independent problems in one context ----
+ * The problems are solved together: one launch of each kernel serves every
+ * problem (all subdomains of all problems are batched, as Sec. 2.3 batches many
+ * subdomains per process). Problem b owns the points [ptr[b], ptr[b+1]) of the
+ * concatenated arrays (user order), has its own kernel width, cutoff, cell grid
+ * and subdomain boxes, and gets its own GMRES (its own Krylov basis segment,
+ * reductions, Hessenberg and stopping test). rbf_matvec and rbf_rasm_apply act
+ * on all problems at once (block-diagonal operators). */
+
+/* Bin nprob problems: xy_dev holds ptr_host[nprob] points; ptr_host (nprob+1
+ * entries, ptr[0] = 0, strictly increasing) and params_host (nprob entries)
+ * are host arrays. Errors as rbf_bin, plus INVALID_ARG for an empty problem. */
+rbf_status rbf_bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* ptr_host, int64_t nprob,
+                         const rbf_params* params_host, rbf_stream stream);
+/* Subdomain boxes of every problem (params_host: nprob entries; precision of
+ * the first entry applies to all). Errors as rbf_rasm_setup. */
+rbf_status rbf_rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params_host, rbf_stream stream);
+/* Solve every problem of the batch (f_dev, w_dev: concatenated, user order; w
+ * holds the initial guesses). info_host (nprob entries, optional) receives each
+ * problem's iterations and final true relative residual. Returns
+ * NOT_CONVERGED if any problem misses rtol within max_iters steps. */
+rbf_status rbf_solve_batch(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* params,
+                           rbf_solve_info* info_host, rbf_stream stream);
+
 /* ---- parity / inspection getters (synchronous; device outputs caller-owned) ---- */
 
 /* Grid after rbf_bin: cells per axis and bounding box {xmin, ymin, xmax, ymax} (host). */

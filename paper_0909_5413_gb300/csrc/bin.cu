@@ -2,11 +2,14 @@
 // matrix-free truncated matvec), user <-> cell-order permutations, and the
 // neighbour-list export used for parity checks.
 //
-// Binning: bounding box; cell (cx, cy) = floor((x - xmin) / c) clamped to the
-// grid, ncx = floor((xmax - xmin) / c) + 1; stable sort by cy*ncx + cx with
-// ties in user order. Every floating-point step uses explicit round-to-nearest
-// intrinsics (no contraction), so the cell of each point is the IEEE result
-// of that expression.
+// Binning of each problem: bounding box; cell (cx, cy) = floor((x - xmin) / c)
+// clamped to the problem's grid, ncx = floor((xmax - xmin) / c) + 1; global
+// cell id = cellbase + cy*ncx + cx; stable sort of all points by global cell
+// id with ties in user order. Problems of a batch get consecutive cell ranges,
+// so each problem's points stay a contiguous range in cell order. Every
+// floating-point step uses explicit round-to-nearest intrinsics (no
+// contraction), so the cell of each point is the IEEE result of that
+// expression.
 #include <cfloat>
 #include <cmath>
 
@@ -28,62 +31,113 @@ __device__ __forceinline__ double pair_r2(double xi, double yi, double xj, doubl
     return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
-// Per-block min/max of x and y: part[4*b + {0,1,2,3}] = {xmin, ymin, xmax, ymax}.
-__global__ void k_bbox(const double* __restrict__ xy, int64_t n, double* __restrict__ part)
+// Index b with base[b] <= v < base[b+1] (base ascending, n entries + sentinel).
+__device__ __forceinline__ int find_segment(const int64_t* __restrict__ base, int n, int64_t v)
 {
-    double x0 = DBL_MAX, y0 = DBL_MAX, x1 = -DBL_MAX, y1 = -DBL_MAX;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Order-preserving map of doubles to unsigned keys (for atomic min / max).
+__device__ __forceinline__ unsigned long long okey(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double okey_inv(unsigned long long k)
+{
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+__global__ void k_pid(const int64_t* __restrict__ pbeg, int nprob, int64_t n, int32_t* __restrict__ pid)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pid[i] = find_segment(pbeg, nprob, i);
+}
+
+__global__ void k_pid_cells(const Prob* __restrict__ prob, int nprob, int64_t ncell, int32_t* __restrict__ pid_cell)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prob[mid].cellbase <= c) lo = mid; else hi = mid - 1;
+    }
+    pid_cell[c] = lo;
+}
+
+constexpr int kBoxTile = 4096;
+
+// Per-problem bounding boxes as ordered keys: keys[4 b + {0..3}] = min x, min y,
+// -max x, -max y (all taken with atomicMin). A tile of one problem is reduced
+// in the block first; tiles that straddle problems use per-thread atomics.
+__global__ void k_bbox(const double* __restrict__ xy, int64_t n, const int32_t* __restrict__ pid,
+                       unsigned long long* __restrict__ keys)
+{
+    __shared__ unsigned long long red[4][8];
+    const int64_t t0 = (int64_t)blockIdx.x * kBoxTile;
+    const int64_t t1 = min(t0 + kBoxTile, n);
+    const int p0 = pid[t0], p1 = pid[t1 - 1];
+    unsigned long long k[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+    int cur = -1;
+    for (int64_t i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
+        int b = pid[i];
+        if (p0 != p1 && b != cur && cur >= 0) {
+            for (int q = 0; q < 4; ++q) atomicMin(&keys[4 * cur + q], k[q]);
+            k[0] = k[1] = k[2] = k[3] = ~0ull;
+        }
+        cur = b;
         double x = xy[2 * i], y = xy[2 * i + 1];
-        x0 = fmin(x0, x); x1 = fmax(x1, x);
-        y0 = fmin(y0, y); y1 = fmax(y1, y);
+        k[0] = min(k[0], okey(x));
+        k[1] = min(k[1], okey(y));
+        k[2] = min(k[2], okey(-x));
+        k[3] = min(k[3], okey(-y));
     }
-    for (int d = 16; d > 0; d >>= 1) {
-        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, d));
-        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, d));
-        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, d));
-        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, d));
+    if (p0 != p1) {
+        if (cur >= 0)
+            for (int q = 0; q < 4; ++q) atomicMin(&keys[4 * cur + q], k[q]);
+        return;
     }
-    __shared__ double sm[4][32];
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { sm[0][w] = x0; sm[1][w] = y0; sm[2][w] = x1; sm[3][w] = y1; }
+    for (int q = 0; q < 4; ++q)
+        for (int d = 16; d > 0; d >>= 1) k[q] = min(k[q], __shfl_xor_sync(0xffffffffu, k[q], d));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int q = 0; q < 4; ++q) red[q][w] = k[q];
     __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        x0 = l < nw ? sm[0][l] : DBL_MAX;  y0 = l < nw ? sm[1][l] : DBL_MAX;
-        x1 = l < nw ? sm[2][l] : -DBL_MAX; y1 = l < nw ? sm[3][l] : -DBL_MAX;
-        for (int d = 16; d > 0; d >>= 1) {
-            x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, d));
-            y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, d));
-            x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, d));
-            y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, d));
-        }
-        if (l == 0) {
-            part[4 * blockIdx.x + 0] = x0; part[4 * blockIdx.x + 1] = y0;
-            part[4 * blockIdx.x + 2] = x1; part[4 * blockIdx.x + 3] = y1;
-        }
+    if (threadIdx.x < 4) {
+        unsigned long long m = ~0ull;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) m = min(m, red[threadIdx.x][ww]);
+        atomicMin(&keys[4 * p0 + threadIdx.x], m);
     }
 }
 
-__global__ void k_bbox_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+__global__ void k_bbox_final(const unsigned long long* __restrict__ keys, int nprob, double* __restrict__ out)
 {
-    if (threadIdx.x != 0) return;
-    double x0 = DBL_MAX, y0 = DBL_MAX, x1 = -DBL_MAX, y1 = -DBL_MAX;
-    for (int b = 0; b < nb; ++b) {
-        x0 = fmin(x0, part[4 * b]); y0 = fmin(y0, part[4 * b + 1]);
-        x1 = fmax(x1, part[4 * b + 2]); y1 = fmax(y1, part[4 * b + 3]);
-    }
-    out[0] = x0; out[1] = y0; out[2] = x1; out[3] = y1;
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nprob) return;
+    out[4 * b + 0] = okey_inv(keys[4 * b + 0]);
+    out[4 * b + 1] = okey_inv(keys[4 * b + 1]);
+    out[4 * b + 2] = -okey_inv(keys[4 * b + 2]);
+    out[4 * b + 3] = -okey_inv(keys[4 * b + 3]);
 }
 
 // Cell id of every point (user order) and per-cell counts.
-__global__ void k_cell_count(const double* __restrict__ xy, int64_t n, double xmin, double ymin, double c,
-                             int64_t ncx, int64_t ncy, int32_t* __restrict__ cell_u, int32_t* __restrict__ counts)
+__global__ void k_cell_count(const double* __restrict__ xy, int64_t n, const Prob* __restrict__ prob,
+                             const int32_t* __restrict__ pid, int32_t* __restrict__ cell_u, int32_t* __restrict__ counts)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int64_t cx = cell_axis(xy[2 * i], xmin, c, ncx);
-    int64_t cy = cell_axis(xy[2 * i + 1], ymin, c, ncy);
-    int32_t cell = (int32_t)(cy * ncx + cx);
+    const Prob& P = prob[pid[i]];
+    int64_t cx = cell_axis(xy[2 * i], P.xmin, P.c, P.ncx);
+    int64_t cy = cell_axis(xy[2 * i + 1], P.ymin, P.c, P.ncy);
+    int32_t cell = (int32_t)(P.cellbase + cy * P.ncx + cx);
     cell_u[i] = cell;
     atomicAdd(&counts[cell], 1);
 }
@@ -133,15 +187,16 @@ __global__ void k_gather_sorted(const double* __restrict__ xy, int64_t n, const 
 // FP32 offsets of each point from its cell's lower corner, scaled by a with
 // a^2 = log2(e) / (2 sigma^2): the FP32 kernel value is exp2(-|dX|^2).
 __global__ void k_local_coords(const double* __restrict__ xy_s, const int32_t* __restrict__ cell_s, int64_t n,
-                               int64_t ncx, double xmin, double ymin, double c, double a, float* __restrict__ loc)
+                               const Prob* __restrict__ prob, const int32_t* __restrict__ pid, float* __restrict__ loc)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    int64_t cc = cell_s[p];
-    int64_t cx = cc % ncx, cy = cc / ncx;
-    double ox = xmin + (double)cx * c, oy = ymin + (double)cy * c;
-    loc[2 * p] = (float)((xy_s[2 * p] - ox) * a);
-    loc[2 * p + 1] = (float)((xy_s[2 * p + 1] - oy) * a);
+    const Prob& P = prob[pid[p]];
+    int64_t cc = cell_s[p] - P.cellbase;
+    int64_t cx = cc % P.ncx, cy = cc / P.ncx;
+    double ox = P.xmin + (double)cx * P.c, oy = P.ymin + (double)cy * P.c;
+    loc[2 * p] = (float)((xy_s[2 * p] - ox) * (double)P.a_loc);
+    loc[2 * p + 1] = (float)((xy_s[2 * p + 1] - oy) * (double)P.a_loc);
 }
 
 // Matvec work items: cell c with m points gives ceil(m / 128) items (c, 128 q).
@@ -180,25 +235,27 @@ __global__ void k_permute_to_user(const double* __restrict__ sorted, const int32
 // are filled from the cell stencil, then put in ascending user order.
 __global__ void k_neighbors(const double* __restrict__ xy_s, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ iperm, const int32_t* __restrict__ cell_s,
-                            const int32_t* __restrict__ cell_start, int64_t n, int64_t ncx, int64_t ncy, int k,
-                            double rc2, const int64_t* __restrict__ ptr, int32_t* __restrict__ cnt,
-                            int32_t* __restrict__ idx, int mode)
+                            const int32_t* __restrict__ cell_start, int64_t n, const Prob* __restrict__ prob,
+                            const int32_t* __restrict__ pid, const int64_t* __restrict__ ptr,
+                            int32_t* __restrict__ cnt, int32_t* __restrict__ idx, int mode)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t p = iperm[i];
+    const Prob& P = prob[pid[p]];
+    const int64_t ncx = P.ncx, ncy = P.ncy, k = P.k;
     double xi = xy_s[2 * (int64_t)p], yi = xy_s[2 * (int64_t)p + 1];
-    int64_t c = cell_s[p];
+    int64_t c = cell_s[p] - P.cellbase;
     int64_t cx = c % ncx, cy = c / ncx;
     int64_t ylo = cy - k < 0 ? 0 : cy - k, yhi = cy + k > ncy - 1 ? ncy - 1 : cy + k;
     int64_t xlo = cx - k < 0 ? 0 : cx - k, xhi = cx + k > ncx - 1 ? ncx - 1 : cx + k;
     int64_t w = (mode == 1) ? ptr[i] : 0;
     int32_t count = 0;
     for (int64_t yy = ylo; yy <= yhi; ++yy) {
-        int32_t b = cell_start[yy * ncx + xlo], e = cell_start[yy * ncx + xhi + 1];
+        int32_t b = cell_start[P.cellbase + yy * ncx + xlo], e = cell_start[P.cellbase + yy * ncx + xhi + 1];
         for (int32_t q = b; q < e; ++q) {
             double r2 = pair_r2(xi, yi, xy_s[2 * (int64_t)q], xy_s[2 * (int64_t)q + 1]);
-            if (r2 <= rc2) {
+            if (r2 <= P.rc2) {
                 if (mode == 1) idx[w + count] = perm[q];
                 ++count;
             }
@@ -226,26 +283,57 @@ __global__ void k_widen_i32_i64(const int32_t* __restrict__ in, int64_t n, int64
 
 }  // namespace
 
+// Bins all problems of ctx->prob_h (kernel parameters and point ranges filled
+// in; grids are set here from the bounding boxes).
 rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
 {
     const int64_t n = ctx->n;
-    const int nb = 2 * kNumSMs;
-    RBF_CHECK(ensure(ctx, ctx->bbox_part, 4 * nb));
-    RBF_CHECK(ensure(ctx, ctx->bbox_dev, 4));
-    RBF_LAUNCH(ctx, k_bbox, nb, 256, 0, st, xy, n, ctx->bbox_part.p);
-    RBF_LAUNCH(ctx, k_bbox_final, 1, 32, 0, st, ctx->bbox_part.p, nb, ctx->bbox_dev.p);
-    RBF_CUDA(ctx, cudaMemcpyAsync(ctx->bbox, ctx->bbox_dev.p, sizeof(ctx->bbox), cudaMemcpyDeviceToHost, st));
+    const int nprob = (int)ctx->nprob;
+    std::vector<Prob>& P = ctx->prob_h;
+    // problem of every point
+    std::vector<int64_t> pbeg(nprob + 1);
+    for (int b = 0; b < nprob; ++b) pbeg[b] = P[b].pbeg;
+    pbeg[nprob] = n;
+    RBF_CHECK(ensure(ctx, ctx->pbeg_dev, nprob + 1));
+    RBF_CUDA(ctx, cudaMemcpyAsync(ctx->pbeg_dev.p, pbeg.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice,
+                                  st));
+    RBF_CHECK(ensure(ctx, ctx->pid, n));
+    RBF_LAUNCH(ctx, k_pid, blocks_for(n, 256), 256, 0, st, ctx->pbeg_dev.p, nprob, n, ctx->pid.p);
+    // bounding boxes
+    const int64_t ntile = (n + kBoxTile - 1) / kBoxTile;
+    RBF_CHECK(ensure(ctx, ctx->bbox_part, 4 * (size_t)nprob));   // keys, reinterpreted
+    RBF_CHECK(ensure(ctx, ctx->bbox_dev, 4 * (size_t)nprob));
+    unsigned long long* keys = (unsigned long long*)ctx->bbox_part.p;
+    RBF_CUDA(ctx, cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * 4 * nprob, st));
+    RBF_LAUNCH(ctx, k_bbox, (unsigned)ntile, 256, 0, st, xy, n, ctx->pid.p, keys);
+    RBF_LAUNCH(ctx, k_bbox_final, blocks_for(nprob, 128), 128, 0, st, keys, nprob, ctx->bbox_dev.p);
+    std::vector<double> bb(4 * (size_t)nprob);
+    RBF_CUDA(ctx, cudaMemcpyAsync(bb.data(), ctx->bbox_dev.p, sizeof(double) * 4 * nprob, cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
-    for (double v : ctx->bbox)
-        if (!std::isfinite(v)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: non-finite coordinate");
-    double fx = std::floor((ctx->bbox[2] - ctx->bbox[0]) / ctx->cell);
-    double fy = std::floor((ctx->bbox[3] - ctx->bbox[1]) / ctx->cell);
-    if (!(fx < 1.0e9) || !(fy < 1.0e9)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: grid too large");
-    ctx->ncx = (int64_t)fx + 1;
-    ctx->ncy = (int64_t)fy + 1;
-    const int64_t ncell = ctx->ncx * ctx->ncy;
-    if (ncell > ((int64_t)1 << 28))
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: %lld cells exceed 2^28 (cell_size too small)", (long long)ncell);
+    int64_t ncell = 0;
+    for (int b = 0; b < nprob; ++b) {
+        Prob& q = P[b];
+        q.xmin = bb[4 * b]; q.ymin = bb[4 * b + 1]; q.xmax = bb[4 * b + 2]; q.ymax = bb[4 * b + 3];
+        if (!std::isfinite(q.xmin) || !std::isfinite(q.ymin) || !std::isfinite(q.xmax) || !std::isfinite(q.ymax))
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: non-finite coordinate in problem %d", b);
+        double fx = std::floor((q.xmax - q.xmin) / q.c), fy = std::floor((q.ymax - q.ymin) / q.c);
+        if (!(fx < 1.0e9) || !(fy < 1.0e9)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: grid too large");
+        q.ncx = (int64_t)fx + 1;
+        q.ncy = (int64_t)fy + 1;
+        q.cellbase = ncell;
+        ncell += q.ncx * q.ncy;
+        if (ncell > ((int64_t)1 << 28))
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: %lld cells exceed 2^28 (cell_size too small)",
+                        (long long)ncell);
+    }
+    ctx->ncell_total = ncell;
+    if (nprob == 1) {
+        ctx->bbox[0] = P[0].xmin; ctx->bbox[1] = P[0].ymin; ctx->bbox[2] = P[0].xmax; ctx->bbox[3] = P[0].ymax;
+        ctx->ncx = P[0].ncx;
+        ctx->ncy = P[0].ncy;
+    }
+    RBF_CHECK(ensure(ctx, ctx->prob, nprob));
+    RBF_CUDA(ctx, cudaMemcpyAsync(ctx->prob.p, P.data(), sizeof(Prob) * nprob, cudaMemcpyHostToDevice, st));
 
     RBF_CHECK(ensure(ctx, ctx->counts, ncell + 1));
     RBF_CHECK(ensure(ctx, ctx->cell_start, ncell + 1));
@@ -255,11 +343,12 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
     RBF_CHECK(ensure(ctx, ctx->iperm, n));
     RBF_CHECK(ensure(ctx, ctx->tmp_i32, std::max<int64_t>(n, 2 * kNumSMs + 1)));
     RBF_CHECK(ensure(ctx, ctx->xy_s, 2 * n));
+    RBF_CHECK(ensure(ctx, ctx->pid_cell, ncell));
 
     RBF_CHECK(prof_begin(ctx, RBF_PROF_BIN, st));
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
-    RBF_LAUNCH(ctx, k_cell_count, blocks_for(n, 256), 256, 0, st, xy, n, ctx->bbox[0], ctx->bbox[1], ctx->cell,
-               ctx->ncx, ctx->ncy, ctx->cell_u.p, ctx->counts.p);
+    RBF_LAUNCH(ctx, k_cell_count, blocks_for(n, 256), 256, 0, st, xy, n, ctx->prob.p, ctx->pid.p, ctx->cell_u.p,
+               ctx->counts.p);
     RBF_CHECK(exclusive_scan_i32(ctx, ctx->counts.p, ctx->cell_start.p, ncell, st));
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
     RBF_LAUNCH(ctx, k_cell_scatter, blocks_for(n, 256), 256, 0, st, ctx->cell_u.p, n, ctx->cell_start.p,
@@ -268,9 +357,10 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
                ctx->perm.p);
     RBF_LAUNCH(ctx, k_gather_sorted, blocks_for(n, 256), 256, 0, st, xy, n, ctx->perm.p, ctx->cell_u.p, ctx->xy_s.p,
                ctx->iperm.p, ctx->cell_s.p);
+    RBF_LAUNCH(ctx, k_pid_cells, blocks_for(ncell, 256), 256, 0, st, ctx->prob.p, nprob, ncell, ctx->pid_cell.p);
     RBF_CHECK(ensure(ctx, ctx->loc32, 2 * n));
-    RBF_LAUNCH(ctx, k_local_coords, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, ctx->cell_s.p, n, ctx->ncx,
-               ctx->bbox[0], ctx->bbox[1], ctx->cell, std::sqrt(M_LOG2E * ctx->s), ctx->loc32.p);
+    RBF_LAUNCH(ctx, k_local_coords, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, ctx->cell_s.p, n, ctx->prob.p,
+               ctx->pid.p, ctx->loc32.p);
     RBF_CHECK(ensure(ctx, ctx->mv_wcnt, ncell + 1));
     RBF_CHECK(ensure(ctx, ctx->mv_woff, ncell + 1));
     RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell, ctx->mv_wcnt.p);
@@ -304,8 +394,8 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
     RBF_CHECK(ensure(ctx, ctx->nbr_cnt, n));
     RBF_CHECK(ensure(ctx, ctx->nbr_ptr_tmp, 2 * (n + 1)));
     RBF_LAUNCH(ctx, k_neighbors, blocks_for(n, 128), 128, 0, st, ctx->xy_s.p, ctx->perm.p, ctx->iperm.p,
-               ctx->cell_s.p, ctx->cell_start.p, n, ctx->ncx, ctx->ncy, ctx->kst, ctx->rc2, (const int64_t*)nullptr,
-               ctx->nbr_cnt.p, (int32_t*)nullptr, 0);
+               ctx->cell_s.p, ctx->cell_start.p, n, ctx->prob.p, ctx->pid.p, (const int64_t*)nullptr, ctx->nbr_cnt.p,
+               (int32_t*)nullptr, 0);
     int64_t* cnt64 = ctx->nbr_ptr_tmp.p;
     int64_t* p64 = ctx->nbr_ptr_tmp.p + (n + 1);
     RBF_LAUNCH(ctx, k_widen_i32_i64, blocks_for(n, 256), 256, 0, st, ctx->nbr_cnt.p, n, cnt64);
@@ -318,8 +408,8 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
                     (long long)*total);
     RBF_CUDA(ctx, cudaMemcpyAsync(ptr, p64, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
     RBF_LAUNCH(ctx, k_neighbors, blocks_for(n, 128), 128, 0, st, ctx->xy_s.p, ctx->perm.p, ctx->iperm.p,
-               ctx->cell_s.p, ctx->cell_start.p, n, ctx->ncx, ctx->ncy, ctx->kst, ctx->rc2, (const int64_t*)p64,
-               ctx->nbr_cnt.p, idx, 1);
+               ctx->cell_s.p, ctx->cell_start.p, n, ctx->prob.p, ctx->pid.p, (const int64_t*)p64, ctx->nbr_cnt.p, idx,
+               1);
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
     return RBF_OK;
 }

@@ -70,6 +70,7 @@ template rbf_status ensure<int64_t>(rbf_ctx*, DevArray<int64_t>&, size_t);
 template rbf_status ensure<double>(rbf_ctx*, DevArray<double>&, size_t);
 template rbf_status ensure<float>(rbf_ctx*, DevArray<float>&, size_t);
 template rbf_status ensure<GmresDev>(rbf_ctx*, DevArray<GmresDev>&, size_t);
+template rbf_status ensure<Prob>(rbf_ctx*, DevArray<Prob>&, size_t);
 
 constexpr int64_t kMaxProfPairs = 1 << 16;
 
@@ -216,32 +217,82 @@ void rbf_destroy(rbf_ctx* ctx)
     delete ctx;
 }
 
-rbf_status rbf_bin(rbf_ctx* ctx, const double* xy_dev, int64_t n, const rbf_params* p, rbf_stream stream)
+// Kernel part of a problem from its parameters (Sec. 2.3); grid set by binning.
+static rbf_status init_prob(rbf_ctx* ctx, Prob& q, const rbf_params* p, int64_t pbeg, int64_t pend)
+{
+    if (!(p->sigma > 0.0) || !(p->cutoff > 0.0) || !std::isfinite(p->sigma) || !std::isfinite(p->cutoff))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: sigma and cutoff must be positive");
+    std::memset(&q, 0, sizeof(q));
+    q.sigma = p->sigma;
+    q.rc = p->cutoff;
+    q.rc2 = p->cutoff * p->cutoff;
+    q.s = 1.0 / (2.0 * p->sigma * p->sigma);
+    q.knorm = p->normalized ? 1.0 / (2.0 * M_PI * p->sigma * p->sigma) : 1.0;
+    q.K = 2048.0 * q.s / M_LN2;
+    q.c = (p->cell_size > 0.0) ? p->cell_size : p->cutoff;
+    double k = std::ceil(q.rc / q.c);
+    if (!(k >= 1.0) || k > 64.0)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: cutoff / cell_size = %g gives a stencil outside 1..64", k);
+    q.k = (int)k;
+    double a = std::sqrt(M_LOG2E * q.s);
+    q.a_loc = (float)a;
+    q.ca = (float)(q.c * (double)q.a_loc);
+    double rc2f = q.rc2 * (double)q.a_loc * (double)q.a_loc;
+    q.rc2f_lo = (float)(rc2f * (1.0 - 1e-4));
+    q.rc2f_hi = (float)(rc2f * (1.0 + 1e-4));
+    q.pbeg = pbeg;
+    q.pend = pend;
+    return RBF_OK;
+}
+
+static rbf_status bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* ptr, int64_t nprob,
+                            const rbf_params* params, cudaStream_t st)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;
-    if (!xy_dev || !p || n < 1 || n > (int64_t)0x7fffffff - 1)
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: need xy, params and 1 <= n < 2^31 (n = %lld)", (long long)n);
-    if (!(p->sigma > 0.0) || !(p->cutoff > 0.0) || !std::isfinite(p->sigma))
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: sigma and cutoff must be positive");
+    if (!xy_dev || !ptr || !params || nprob < 1 || nprob > (1 << 24))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: need xy, point ranges, parameters and 1 <= nprob <= 2^24");
+    const int64_t n = ptr[nprob];
+    if (ptr[0] != 0 || n < 1 || n > (int64_t)0x7fffffff - 1)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: need ptr[0] = 0 and 1 <= n < 2^31 (n = %lld)", (long long)n);
     if (((uintptr_t)xy_dev) % 8 != 0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: xy must be 8-byte aligned");
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->binned = false;
     ctx->rasm_ready = false;
+    ctx->prob_h.assign((size_t)nprob, Prob{});
+    for (int64_t b = 0; b < nprob; ++b) {
+        if (ptr[b + 1] <= ptr[b])
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: problem %lld has no points", (long long)b);
+        RBF_CHECK(init_prob(ctx, ctx->prob_h[b], &params[b], ptr[b], ptr[b + 1]));
+    }
+    ctx->nprob = nprob;
     ctx->n = n;
-    ctx->sigma = p->sigma;
-    ctx->rc = p->cutoff;
-    ctx->rc2 = p->cutoff * p->cutoff;
-    ctx->cell = (p->cell_size > 0.0) ? p->cell_size : p->cutoff;
-    ctx->s = 1.0 / (2.0 * p->sigma * p->sigma);
-    ctx->normalized = p->normalized ? 1 : 0;
-    ctx->knorm = p->normalized ? 1.0 / (2.0 * M_PI * p->sigma * p->sigma) : 1.0;
-    double k = std::ceil(ctx->rc / ctx->cell);
-    if (!(k >= 1.0) || k > 64.0)
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: cutoff / cell_size = %g gives a stencil outside 1..64", k);
-    ctx->kst = (int)k;
-    RBF_CHECK(bin_points(ctx, xy_dev, S(stream)));
+    const Prob& q = ctx->prob_h[0];
+    ctx->sigma = q.sigma;
+    ctx->rc = q.rc;
+    ctx->rc2 = q.rc2;
+    ctx->cell = q.c;
+    ctx->s = q.s;
+    ctx->knorm = q.knorm;
+    ctx->normalized = params[0].normalized ? 1 : 0;
+    ctx->kst = q.k;
+    RBF_CHECK(bin_points(ctx, xy_dev, st));
     ctx->binned = true;
     return RBF_OK;
+}
+
+rbf_status rbf_bin(rbf_ctx* ctx, const double* xy_dev, int64_t n, const rbf_params* p, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (n < 1 || n > (int64_t)0x7fffffff - 1)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: need 1 <= n < 2^31 (n = %lld)", (long long)n);
+    int64_t ptr[2] = {0, n};
+    return bin_batch(ctx, xy_dev, ptr, 1, p, S(stream));
+}
+
+rbf_status rbf_bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* ptr_host, int64_t nprob,
+                         const rbf_params* params_host, rbf_stream stream)
+{
+    return bin_batch(ctx, xy_dev, ptr_host, nprob, params_host, S(stream));
 }
 
 rbf_status rbf_matvec(rbf_ctx* ctx, const double* w_dev, double* y_dev, int precision, rbf_stream stream)
@@ -262,36 +313,79 @@ rbf_status rbf_matvec(rbf_ctx* ctx, const double* w_dev, double* y_dev, int prec
     return permute_to_user(ctx, ctx->vec_b.p, y_dev, S(stream));
 }
 
-rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* p, rbf_stream stream)
+static rbf_status rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params, cudaStream_t st)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;
     if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_rasm_setup: call rbf_bin first");
-    if (!p || !(p->core_size > 0.0) || !(p->overlap >= 0.0) || !std::isfinite(p->x0) || !std::isfinite(p->y0))
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: need core_size > 0, overlap >= 0");
-    int cap = p->max_sub_points > 0 ? p->max_sub_points : kMaxSub;
-    if (cap > kMaxSub) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: max_sub_points > %d", kMaxSub);
-    if (p->precision != RBF_FP64 && p->precision != RBF_FP32)
+    if (!params) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: null parameters");
+    const int precision = params[0].precision;
+    if (precision != RBF_FP64 && precision != RBF_FP32)
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: precision must be RBF_FP64 or RBF_FP32");
+    int cap = 0;
+    int64_t nsub = 0;
+    for (int64_t b = 0; b < ctx->nprob; ++b) {
+        const rbf_rasm_params* p = &params[b];
+        if (!(p->core_size > 0.0) || !(p->overlap >= 0.0) || !std::isfinite(p->x0) || !std::isfinite(p->y0) ||
+            !std::isfinite(p->core_size) || !std::isfinite(p->overlap))
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: need core_size > 0, overlap >= 0 (problem %lld)",
+                        (long long)b);
+        int c = p->max_sub_points > 0 ? p->max_sub_points : kMaxSub;
+        if (c > kMaxSub) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: max_sub_points > %d", kMaxSub);
+        cap = (b == 0) ? c : std::min(cap, c);
+        Prob& q = ctx->prob_h[b];
+        q.x0 = p->x0;
+        q.y0 = p->y0;
+        q.B = p->core_size;
+        q.delta = p->overlap;
+        double fx = std::floor((q.xmax - q.x0) / q.B), fy = std::floor((q.ymax - q.y0) / q.B);
+        double reach = std::ceil(q.delta / q.B) + 1.0;
+        if (!(fx < 1.0e9) || !(fy < 1.0e9) || reach > 64.0)
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes or overlap / core_size too large");
+        q.nbx = fx < 0.0 ? 1 : (int64_t)fx + 1;
+        q.nby = fy < 0.0 ? 1 : (int64_t)fy + 1;
+        q.reach = (int)reach;
+        q.subbase = nsub;
+        nsub += q.nbx * q.nby;
+        if (nsub > ((int64_t)1 << 30)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes");
+    }
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->rasm_ready = false;
-    ctx->x0 = p->x0;
-    ctx->y0 = p->y0;
-    ctx->B = p->core_size;
-    ctx->delta = p->overlap;
-    ctx->rasm_precision = p->precision;
-    double fx = std::floor((ctx->bbox[2] - ctx->x0) / ctx->B), fy = std::floor((ctx->bbox[3] - ctx->y0) / ctx->B);
-    if (!(fx < 1.0e9) || !(fy < 1.0e9)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes");
-    ctx->nbx = fx < 0.0 ? 1 : (int64_t)fx + 1;
-    ctx->nby = fy < 0.0 ? 1 : (int64_t)fy + 1;
-    ctx->nsub = ctx->nbx * ctx->nby;
-    if (ctx->nsub > ((int64_t)1 << 30)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: too many boxes");
-    RBF_CHECK(build_subdomains(ctx, S(stream)));
+    ctx->rasm_precision = precision;
+    ctx->nsub = nsub;
+    if (ctx->nprob == 1) {
+        const Prob& q = ctx->prob_h[0];
+        ctx->x0 = q.x0;
+        ctx->y0 = q.y0;
+        ctx->B = q.B;
+        ctx->delta = q.delta;
+        ctx->nbx = q.nbx;
+        ctx->nby = q.nby;
+    } else {   // a batch reports its total subdomain count as nbx x 1
+        ctx->nbx = nsub;
+        ctx->nby = 1;
+    }
+    RBF_CUDA(ctx, cudaMemcpyAsync(ctx->prob.p, ctx->prob_h.data(), sizeof(Prob) * ctx->nprob, cudaMemcpyHostToDevice,
+                                  st));
+    RBF_CHECK(build_subdomains(ctx, st));
     if (ctx->max_ov > cap)
         return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE, "rbf_rasm_setup: an overlap list has %d points (cap %d)",
                     ctx->max_ov, cap);
-    RBF_CHECK(rasm_factor(ctx, S(stream)));
+    RBF_CHECK(rasm_factor(ctx, st));
     ctx->rasm_ready = true;
     return RBF_OK;
+}
+
+rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* p, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (ctx->binned && ctx->nprob != 1)
+        return fail(ctx, RBF_ERR_STATE, "rbf_rasm_setup: the context holds a batch; use rbf_rasm_setup_batch");
+    return rasm_setup_batch(ctx, p, S(stream));
+}
+
+rbf_status rbf_rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params_host, rbf_stream stream)
+{
+    return rasm_setup_batch(ctx, params_host, S(stream));
 }
 
 rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_stream stream)
@@ -312,6 +406,8 @@ rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;
     if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_solve: call rbf_rasm_setup first");
+    if (ctx->nprob != 1)
+        return fail(ctx, RBF_ERR_STATE, "rbf_solve: the context holds a batch; use rbf_solve_batch");
     if (!f_dev || !w_dev || !p) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: null argument");
     if (!(p->rtol > 0.0) || p->restart < 0 || p->restart > kMaxRestart || p->max_iters < 0)
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: need rtol > 0, 0 <= restart <= %d", kMaxRestart);
@@ -324,6 +420,27 @@ rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf
     std::memset(&local, 0, sizeof(local));
     rbf_status st = gmres_solve(ctx, ctx->vec_d.p, ctx->vec_e.p, p, &local, S(stream));
     if (info) *info = local;
+    if (st != RBF_OK && st != RBF_ERR_NOT_CONVERGED) return st;
+    rbf_status st2 = permute_to_user(ctx, ctx->vec_e.p, w_dev, S(stream));
+    if (st2 != RBF_OK) return st2;
+    RBF_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    return st;
+}
+
+rbf_status rbf_solve_batch(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* p,
+                           rbf_solve_info* info_host, rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_solve_batch: call rbf_rasm_setup_batch first");
+    if (!f_dev || !w_dev || !p) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve_batch: null argument");
+    if (!(p->rtol > 0.0) || p->restart < 0 || p->restart > kMaxRestart || p->max_iters < 0)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve_batch: need rtol > 0, 0 <= restart <= %d", kMaxRestart);
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(ensure(ctx, ctx->vec_d, ctx->n));
+    RBF_CHECK(ensure(ctx, ctx->vec_e, ctx->n));
+    RBF_CHECK(permute_to_sorted(ctx, f_dev, ctx->vec_d.p, S(stream)));
+    RBF_CHECK(permute_to_sorted(ctx, w_dev, ctx->vec_e.p, S(stream)));
+    rbf_status st = gmres_solve_batch(ctx, ctx->vec_d.p, ctx->vec_e.p, p, info_host, S(stream));
     if (st != RBF_OK && st != RBF_ERR_NOT_CONVERGED) return st;
     rbf_status st2 = permute_to_user(ctx, ctx->vec_e.p, w_dev, S(stream));
     if (st2 != RBF_OK) return st2;

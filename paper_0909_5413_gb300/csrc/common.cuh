@@ -44,6 +44,26 @@ struct DevArray {
     size_t count = 0;
 };
 
+// One interpolation problem of a context (a context holds one problem, or a
+// batch of independent ones). Its points occupy [pbeg, pend) both in user
+// order and in cell order; its cells are [cellbase, cellbase + ncx*ncy) and
+// its subdomains [subbase, subbase + nbx*nby) of the context's global ids.
+struct Prob {
+    // kernel and cell grid
+    double sigma, rc, rc2, s, knorm, K;   // K = 2048 s / ln 2 (FP64 matvec exp)
+    double xmin, ymin, xmax, ymax, c;
+    int64_t ncx, ncy, cellbase;
+    int64_t pbeg, pend;
+    int k;                                // stencil half-width ceil(rc / c)
+    float a_loc;                          // FP32 offset scale sqrt(log2(e) s)
+    float ca, rc2f_lo, rc2f_hi;           // c * a_loc; FP32 accept / exact-test band around rc2 a_loc^2
+    // subdomain boxes
+    double x0, y0, B, delta;
+    int64_t nbx, nby, subbase;
+    int reach;
+    int pad;
+};
+
 }  // namespace rbf
 
 struct rbf_prof_slot {
@@ -61,12 +81,22 @@ struct rbf_ctx {
     int64_t dev_bytes = 0;
     std::vector<std::pair<void*, size_t>> owned;   // every live allocation
 
+    // ---- problems (one for rbf_bin, several for rbf_bin_batch)
+    int64_t nprob = 0;
+    std::vector<rbf::Prob> prob_h;
+    rbf::DevArray<rbf::Prob> prob;
+    rbf::DevArray<int32_t> pid;        // problem of each point (user order == cell order ranges)
+    rbf::DevArray<int32_t> pid_cell;   // problem of each cell
+    rbf::DevArray<int32_t> pid_sub;    // problem of each subdomain
+    rbf::DevArray<int64_t> pbeg_dev;   // pbeg of each problem, plus the total
+
     // ---- binning (rbf_bin)
     bool binned = false;
     int64_t n = 0;
     double sigma = 0, rc = 0, rc2 = 0, cell = 0, s = 0, knorm = 1.0;
     int normalized = 0;
-    int64_t ncx = 0, ncy = 0;
+    int64_t ncx = 0, ncy = 0;      // grid of a single problem
+    int64_t ncell_total = 0;       // cells of all problems
     int kst = 1;                   // stencil half-width ceil(rc / c)
     double bbox[4] = {0, 0, 0, 0};
     rbf::DevArray<int32_t> perm, iperm, cell_start, cell_s, counts, cell_u, tmp_i32;
@@ -97,6 +127,13 @@ struct rbf_ctx {
     rbf::DevArray<int64_t> scan_tmp;
     rbf::DevArray<int32_t> nbr_cnt;
     rbf::DevArray<int64_t> nbr_ptr_tmp;
+
+    // ---- batched solver workspace
+    rbf::DevArray<int32_t> bch;        // chunk table
+    rbf::DevArray<rbf::GmresDev> gmb;  // per-problem GMRES state
+    rbf::DevArray<int32_t> bactive;    // per-problem active / zero masks
+    rbf::DevArray<double> bstat;       // per-problem summary for the host
+    int batch_rounds = 0;
 };
 
 namespace rbf {
@@ -172,5 +209,9 @@ rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStrea
 // ---- gmres.cu
 rbf_status gmres_solve(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,
                        rbf_solve_info* info, cudaStream_t st);
+
+// ---- gmres_batch.cu
+rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,
+                             rbf_solve_info* infos, cudaStream_t st);
 
 }  // namespace rbf

@@ -1,0 +1,617 @@
+// gmres_batch.cu -- restarted right-preconditioned GMRES(m) for a batch of
+// independent problems solved together: one launch of each kernel serves all
+// problems, and every problem keeps its own Krylov basis segment, Gram-Schmidt
+// coefficients, Hessenberg matrix, Givens rotations and stopping test.
+//
+// Vectors are the concatenation of the problems' cell-ordered vectors. They
+// are cut into chunks of at most kBChunk elements that never cross a problem
+// boundary; block partial sums of a chunk are reduced per problem in a fixed
+// order (deterministic: a problem's result does not depend on the other
+// problems of the batch). Converged problems are masked: their kernels return
+// at once. An Arnoldi cycle runs with no host synchronisation (each problem's
+// stop flag lives on the device), so the cycle is captured once as a CUDA
+// graph and replayed; the host reads the problems' residuals once per cycle.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "vecops.cuh"
+
+namespace rbf {
+
+rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStream_t st);
+rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float* y, cudaStream_t st);
+
+namespace {
+
+constexpr int kBPer = 16;                       // elements per thread
+constexpr int kBChunk = kDotThreads * kBPer;    // elements per chunk
+
+enum BField { F_H1 = 0, F_H2 = 1, F_NRM2 = 2, F_BETA2 = 3, F_FNORM2 = 4 };
+
+__device__ __forceinline__ double* field_ptr(GmresDev& g, int field)
+{
+    switch (field) {
+    case F_H1: return g.h1;
+    case F_H2: return g.h2;
+    case F_NRM2: return &g.nrm2;
+    case F_BETA2: return &g.beta2;
+    default: return &g.fnorm2;
+    }
+}
+
+struct Chunks {
+    const int32_t* beg;   // first element of chunk
+    const int32_t* end;   // one past the last
+    const int32_t* pid;   // problem of the chunk
+    const int32_t* cptr;  // chunks of problem b: [cptr[b], cptr[b+1])
+    int64_t nc;
+};
+
+// Dots V_k . x over one chunk (k fastest); 0 for masked problems.
+template <class T>
+__global__ void __launch_bounds__(kDotThreads)
+    k_bdots(const T* __restrict__ V, int64_t ldv, int nv, const T* __restrict__ x, Chunks C,
+            const int32_t* __restrict__ active, double* __restrict__ partial)
+{
+    __shared__ double red[kDotThreads / 32];
+    const int k = (int)(blockIdx.x % (unsigned)nv);
+    const int64_t c = blockIdx.x / (unsigned)nv;
+    if (!active[C.pid[c]]) {
+        if (threadIdx.x == 0) partial[c * 32 + k] = 0.0;
+        return;
+    }
+    const int64_t b = C.beg[c], e = C.end[c];
+    const T* v = V + k * ldv;
+    double a = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF s{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            if (i < e) df_add_prod(s, v[i], x[i]);
+        }
+        a = (double)s.hi + (double)s.lo;
+    } else {
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            if (i < e) a = fma((double)v[i], (double)x[i], a);
+        }
+    }
+    double s = block_sum(a, red);
+    if (threadIdx.x == 0) partial[c * 32 + k] = s;
+}
+
+// x -= sum_k coef_k V_k with the chunk's problem's coefficients (field h1 or
+// h2 of its state); with NORM, |x|^2 partial sums.
+template <class T, bool NORM>
+__global__ void __launch_bounds__(kDotThreads)
+    k_bupdate(const T* __restrict__ V, int64_t ldv, int nv, GmresDev* __restrict__ gm, int field, T* __restrict__ x,
+              Chunks C, const int32_t* __restrict__ active, double* __restrict__ partial)
+{
+    __shared__ double cf[kMaxRestart + 1];
+    __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
+    __shared__ double red[kDotThreads / 32];
+    const int64_t c = blockIdx.x;
+    const int pb = C.pid[c];
+    if (!active[pb]) {
+        if (NORM && threadIdx.x == 0) partial[c * 32] = 0.0;
+        return;
+    }
+    if (threadIdx.x < (unsigned)nv) {
+        double v = field_ptr(gm[pb], field)[threadIdx.x];
+        cf[threadIdx.x] = v;
+        float h = (float)v;
+        cf_hi[threadIdx.x] = h;
+        cf_lo[threadIdx.x] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    const int64_t b = C.beg[c], e = C.end[c];
+    double a = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF xl[kBPer];
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            xl[u].hi = i < e ? (float)x[i] : 0.f;
+            xl[u].lo = 0.f;
+        }
+        for (int k = 0; k < nv; ++k) {
+            const T* v = V + k * ldv;
+            const float ch = cf_hi[k], cl = cf_lo[k];
+#pragma unroll
+            for (int u = 0; u < kBPer; ++u) {
+                int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+                if (i < e) {
+                    float vi = v[i];
+                    float h = ch * vi;
+                    float r = fmaf(ch, vi, -h);
+                    df_add(xl[u], -h, fmaf(-cl, vi, -r));
+                }
+            }
+        }
+        DF s{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            if (i < e) {
+                float xs = xl[u].hi + xl[u].lo;
+                x[i] = xs;
+                if (NORM) df_add_prod(s, xs, xs);
+            }
+        }
+        a = (double)s.hi + (double)s.lo;
+    } else {
+        double xl[kBPer];
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            xl[u] = i < e ? (double)x[i] : 0.0;
+        }
+        for (int k = 0; k < nv; ++k) {
+            const T* v = V + k * ldv;
+            const double cc = cf[k];
+#pragma unroll
+            for (int u = 0; u < kBPer; ++u) {
+                int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+                if (i < e) xl[u] = fma(-cc, (double)v[i], xl[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBPer; ++u) {
+            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+            if (i < e) {
+                T xs = (T)xl[u];
+                x[i] = xs;
+                if (NORM) a = fma((double)xs, (double)xs, a);
+            }
+        }
+    }
+    if (NORM) {
+        double s = block_sum(a, red);
+        if (threadIdx.x == 0) partial[c * 32] = s;
+    }
+}
+
+// r = f - t over one chunk (FP64) and |r|^2 partial sums.
+__global__ void __launch_bounds__(kDotThreads)
+    k_bresidual(const double* __restrict__ f, const double* __restrict__ t, double* __restrict__ r, Chunks C,
+                const int32_t* __restrict__ active, double* __restrict__ partial)
+{
+    __shared__ double red[kDotThreads / 32];
+    const int64_t c = blockIdx.x;
+    if (!active[C.pid[c]]) {
+        if (threadIdx.x == 0) partial[c * 32] = 0.0;
+        return;
+    }
+    const int64_t b = C.beg[c], e = C.end[c];
+    double a = 0.0;
+    for (int u = 0; u < kBPer; ++u) {
+        int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
+        if (i < e) {
+            double v = f[i] - t[i];
+            r[i] = v;
+            a = fma(v, v, a);
+        }
+    }
+    double s = block_sum(a, red);
+    if (threadIdx.x == 0) partial[c * 32] = s;
+}
+
+// Per problem (block), per vector k (warp): sum of the problem's chunk partials
+// in a fixed order, written to the field of its state.
+__global__ void k_breduce(const double* __restrict__ partial, Chunks C, int nprob, int nv, GmresDev* __restrict__ gm,
+                          int field, const int32_t* __restrict__ active)
+{
+    const int pb = blockIdx.x;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (pb >= nprob || k >= nv || !active[pb]) return;
+    double a = 0.0;
+    for (int c = C.cptr[pb] + lane; c < C.cptr[pb + 1]; c += 32) a += partial[(int64_t)c * 32 + k];
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if (lane == 0) field_ptr(gm[pb], field)[k] = a;
+}
+
+// Start of a cycle of every active problem (mode 1: reference norm = |r|).
+__global__ void k_bcycle_init(GmresDev* __restrict__ gm, int nprob, int m, int mode,
+                              const int32_t* __restrict__ active)
+{
+    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pb >= nprob || !active[pb]) return;
+    GmresDev& g = gm[pb];
+    if (mode == 1) g.fnorm2 = g.beta2;
+    double beta = sqrt(g.beta2);
+    double fn = sqrt(g.fnorm2);
+    for (int q = 0; q <= m; ++q) g.g[q] = 0.0;
+    g.g[0] = beta;
+    g.inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+    g.est = fn > 0.0 ? beta / fn : 0.0;
+    g.done = (g.est <= g.rtol) ? 1 : 0;
+    g.breakdown = 0;
+    g.j = 0;       // steps taken in this cycle
+}
+
+// Arnoldi step j of every active problem that has not stopped in this cycle.
+__global__ void k_barnoldi(GmresDev* __restrict__ gm, int nprob, int j, const int32_t* __restrict__ active)
+{
+    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pb >= nprob || !active[pb]) return;
+    GmresDev& gg = gm[pb];
+    if (gg.done) return;
+    GmresDev* g = &gg;
+    const int M = kMaxRestart;
+    for (int q = 0; q <= j; ++q) g->H[q * M + j] = g->h1[q] + g->h2[q];
+    double hn = sqrt(fmax(g->nrm2, 0.0));
+    g->H[(j + 1) * M + j] = hn;
+    for (int q = 0; q < j; ++q) {
+        double a = g->H[q * M + j], b = g->H[(q + 1) * M + j];
+        g->H[q * M + j] = g->cs[q] * a + g->sn[q] * b;
+        g->H[(q + 1) * M + j] = -g->sn[q] * a + g->cs[q] * b;
+    }
+    double a = g->H[j * M + j], b = g->H[(j + 1) * M + j];
+    double c, s;
+    if (b == 0.0) { c = 1.0; s = 0.0; }
+    else if (fabs(b) > fabs(a)) { double t = a / b; s = 1.0 / sqrt(1.0 + t * t); c = s * t; }
+    else { double t = b / a; c = 1.0 / sqrt(1.0 + t * t); s = c * t; }
+    g->cs[j] = c;
+    g->sn[j] = s;
+    g->H[j * M + j] = c * a + s * b;
+    g->H[(j + 1) * M + j] = 0.0;
+    g->g[j + 1] = -s * g->g[j];
+    g->g[j] = c * g->g[j];
+    g->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
+    g->breakdown = (hn == 0.0) ? 1 : 0;
+    g->est = fabs(g->g[j + 1]) / sqrt(g->fnorm2);
+    g->done = (g->est <= g->rtol || g->breakdown) ? 1 : 0;
+    g->j = j + 1;
+}
+
+__global__ void k_bsolve_y(GmresDev* __restrict__ gm, int nprob, const int32_t* __restrict__ active)
+{
+    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pb >= nprob || !active[pb]) return;
+    GmresDev* g = &gm[pb];
+    const int M = kMaxRestart, k = g->j;
+    for (int q = k - 1; q >= 0; --q) {
+        double v = g->g[q];
+        for (int p = q + 1; p < k; ++p) v -= g->H[q * M + p] * g->y[p];
+        g->y[q] = v / g->H[q * M + q];
+    }
+}
+
+// x *= the problem's factor (inv_beta if which = 0, inv_h if which = 1).
+template <class T>
+__global__ void k_bscale(T* __restrict__ x, int64_t n, const int32_t* __restrict__ pid,
+                         const GmresDev* __restrict__ gm, int which, const int32_t* __restrict__ active)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int pb = pid[i];
+        if (!active[pb]) continue;
+        const GmresDev& g = gm[pb];
+        if (which == 1 && g.done && g.breakdown) continue;
+        double f = which == 0 ? g.inv_beta : g.inv_h;
+        x[i] = (T)((double)x[i] * f);
+    }
+}
+
+// FP32 copy of r scaled by the problem's inv_beta (inner start of the mixed form).
+__global__ void k_bto_f32_scaled(const double* __restrict__ r, int64_t n, const int32_t* __restrict__ pid,
+                                 const GmresDev* __restrict__ gm, const int32_t* __restrict__ active,
+                                 float* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int pb = pid[i];
+        if (active[pb]) out[i] = (float)(r[i] * gm[pb].inv_beta);
+    }
+}
+
+// t = sum_{q < k_b} y_q V_q with the problem's own step count and y.
+template <class T>
+__global__ void k_bcombine(const T* __restrict__ V, int64_t ldv, const GmresDev* __restrict__ gm,
+                           const int32_t* __restrict__ pid, const int32_t* __restrict__ active, T* __restrict__ t,
+                           int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int pb = pid[i];
+        if (!active[pb]) continue;
+        const GmresDev& g = gm[pb];
+        const int k = g.j;
+        if constexpr (sizeof(T) == 4) {
+            DF a{0.f, 0.f};
+            for (int q = 0; q < k; ++q) {
+                double c = g.y[q];
+                float ch = (float)c, cl = (float)(c - (double)ch);
+                float vi = V[q * ldv + i];
+                float h = ch * vi;
+                df_add(a, h, fmaf(cl, vi, fmaf(ch, vi, -h)));
+            }
+            t[i] = a.hi + a.lo;
+        } else {
+            double a = 0.0;
+            for (int q = 0; q < k; ++q) a = fma(g.y[q], (double)V[q * ldv + i], a);
+            t[i] = (T)a;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_baxpy(double* __restrict__ w, const T* __restrict__ u, const int32_t* __restrict__ pid,
+                        const int32_t* __restrict__ active, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (active[pid[i]]) w[i] += (double)u[i];
+}
+
+__global__ void k_binit(GmresDev* __restrict__ gm, int nprob, double rtol)
+{
+    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pb >= nprob) return;
+    gm[pb].rtol = rtol;
+    gm[pb].done = 0;
+    gm[pb].j = 0;
+}
+
+// Per-problem summary for the host: (|r|^2, |f|^2, steps of the last cycle, estimate).
+__global__ void k_bpack(const GmresDev* __restrict__ gm, int nprob, double* __restrict__ out)
+{
+    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pb >= nprob) return;
+    out[4 * pb + 0] = gm[pb].beta2;
+    out[4 * pb + 1] = gm[pb].fnorm2;
+    out[4 * pb + 2] = (double)gm[pb].j;
+    out[4 * pb + 3] = gm[pb].est;
+}
+
+__global__ void k_bzero_inactive_w(double* __restrict__ w, const int32_t* __restrict__ pid,
+                                   const int32_t* __restrict__ zero, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (zero[pid[i]]) w[i] = 0.0;
+}
+
+unsigned bstream_blocks(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 16 * kNumSMs) b = 16 * kNumSMs;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+struct BatchWork {
+    rbf_ctx* ctx;
+    cudaStream_t st;
+    Chunks C;
+    int nprob;
+    GmresDev* gm;
+    const int32_t* active;
+    double* partial;
+    const int32_t* pid;
+    int64_t n;
+
+    template <int MODE, class T>
+    rbf_status mdot(const T* V, int64_t ldv, int nv, T* x, int field_in, int field_out)
+    {
+        if (MODE == 2) {
+            RBF_LAUNCH(ctx, (k_bupdate<T, true>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x, C,
+                       active, partial);
+            RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, partial, C, nprob, 1, gm, field_out, active);
+            return RBF_OK;
+        }
+        if (MODE == 1)
+            RBF_LAUNCH(ctx, (k_bupdate<T, false>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x,
+                       C, active, partial);
+        RBF_LAUNCH(ctx, (k_bdots<T>), (unsigned)(C.nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, C, active,
+                   partial);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nv, 0, st, partial, C, nprob, nv, gm, field_out, active);
+        return RBF_OK;
+    }
+};
+
+template <class T>
+struct BOps;
+
+template <>
+struct BOps<double> {
+    static rbf_status amul(rbf_ctx* c, const double* x, double* y, cudaStream_t st)
+    {
+        return matvec_sorted_f64(c, x, y, st);
+    }
+    static rbf_status minv(rbf_ctx* c, const double* x, double* y, cudaStream_t st)
+    {
+        return rasm_apply_sorted(c, x, y, st);
+    }
+};
+
+template <>
+struct BOps<float> {
+    static rbf_status amul(rbf_ctx* c, const float* x, float* y, cudaStream_t st)
+    {
+        return matvec_f32_raw(c, nullptr, x, y, st);
+    }
+    static rbf_status minv(rbf_ctx* c, const float* x, float* y, cudaStream_t st)
+    {
+        return rasm_apply_sorted_f32(c, x, y, st);
+    }
+};
+
+// The launches of one Arnoldi cycle (m steps and the update of w), with no
+// host synchronisation; V_0 holds the normalised start vector.
+template <class T>
+rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double* w)
+{
+    rbf_ctx* ctx = B.ctx;
+    cudaStream_t st = B.st;
+    const int64_t n = B.n;
+    const unsigned pb_blocks = blocks_for(B.nprob, 128);
+    for (int j = 0; j < m; ++j) {
+        T* vj = V + (int64_t)j * ldv;
+        T* vn = V + (int64_t)(j + 1) * ldv;
+        RBF_CHECK(BOps<T>::minv(ctx, vj, u, st));
+        RBF_CHECK(BOps<T>::amul(ctx, u, vn, st));
+        RBF_CHECK((B.mdot<0, T>(V, ldv, j + 1, vn, -1, F_H1)));
+        RBF_CHECK((B.mdot<1, T>(V, ldv, j + 1, vn, F_H1, F_H2)));
+        RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H2, F_NRM2)));
+        RBF_LAUNCH(ctx, k_barnoldi, pb_blocks, 128, 0, st, B.gm, B.nprob, j, B.active);
+        RBF_LAUNCH(ctx, (k_bscale<T>), bstream_blocks(n), 256, 0, st, vn, n, B.pid, B.gm, 1, B.active);
+    }
+    RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);
+    RBF_LAUNCH(ctx, (k_bcombine<T>), bstream_blocks(n), 256, 0, st, V, ldv, B.gm, B.pid, B.active, t, n);
+    RBF_CHECK(BOps<T>::minv(ctx, t, u, st));
+    RBF_LAUNCH(ctx, (k_baxpy<T>), bstream_blocks(n), 256, 0, st, w, u, B.pid, B.active, n);
+    return RBF_OK;
+}
+
+}  // namespace
+
+rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf_solve_params* p,
+                             rbf_solve_info* infos, cudaStream_t st)
+{
+    const int64_t n = ctx->n;
+    const int nprob = (int)ctx->nprob;
+    const int m = p->restart > 0 ? p->restart : 30;
+    const int max_iters = p->max_iters > 0 ? p->max_iters : 10000;
+    const bool mixed = p->mixed != 0;
+    const int max_refine = p->max_refine > 0 ? p->max_refine : 40;
+
+    // chunk table
+    std::vector<int32_t> cb, ce, cp, cptr(nprob + 1);
+    for (int b = 0; b < nprob; ++b) {
+        cptr[b] = (int32_t)cb.size();
+        const Prob& q = ctx->prob_h[b];
+        for (int64_t s = q.pbeg; s < q.pend; s += kBChunk) {
+            cb.push_back((int32_t)s);
+            ce.push_back((int32_t)std::min<int64_t>(s + kBChunk, q.pend));
+            cp.push_back(b);
+        }
+    }
+    cptr[nprob] = (int32_t)cb.size();
+    const int64_t nc = (int64_t)cb.size();
+    RBF_CHECK(ensure(ctx, ctx->bch, 3 * (size_t)nc + nprob + 1));
+    int32_t* dch = ctx->bch.p;
+    RBF_CUDA(ctx, cudaMemcpyAsync(dch, cb.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(dch + nc, ce.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(dch + 2 * nc, cp.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(dch + 3 * nc, cptr.data(), sizeof(int32_t) * (nprob + 1), cudaMemcpyHostToDevice,
+                                  st));
+    Chunks C{dch, dch + nc, dch + 2 * nc, dch + 3 * nc, nc};
+
+    RBF_CHECK(ensure(ctx, ctx->gmb, nprob));
+    RBF_CHECK(ensure(ctx, ctx->bactive, 2 * (size_t)nprob));
+    RBF_CHECK(ensure(ctx, ctx->bstat, 4 * (size_t)nprob));
+    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(nc, 1) * 32));
+    RBF_CHECK(ensure(ctx, ctx->vec_a, n));
+    RBF_CHECK(ensure(ctx, ctx->vec_b, n));
+    GmresDev* gm = ctx->gmb.p;
+    int32_t* active = ctx->bactive.p;
+    int32_t* zero_mask = ctx->bactive.p + nprob;
+    RBF_CUDA(ctx, cudaMemsetAsync(gm, 0, sizeof(GmresDev) * nprob, st));
+    const double rt = mixed ? (p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5) : p->rtol;
+    RBF_LAUNCH(ctx, k_binit, blocks_for(nprob, 128), 128, 0, st, gm, nprob, rt);
+    std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
+    RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+
+    BatchWork B{ctx, st, C, nprob, gm, active, ctx->partial.p, ctx->pid.p, n};
+    // |f_b|^2
+    RBF_CHECK((B.mdot<0, double>(f, 0, 1, const_cast<double*>(f), -1, F_FNORM2)));
+    std::vector<double> stat(4 * (size_t)nprob);
+    auto read_stat = [&]() -> rbf_status {
+        RBF_LAUNCH(ctx, k_bpack, blocks_for(nprob, 128), 128, 0, st, gm, nprob, ctx->bstat.p);
+        RBF_CUDA(ctx, cudaMemcpyAsync(stat.data(), ctx->bstat.p, sizeof(double) * 4 * nprob, cudaMemcpyDeviceToHost,
+                                      st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+        return RBF_OK;
+    };
+    RBF_CHECK(read_stat());
+    std::vector<double> fnorm(nprob), relres(nprob, 0.0), est(nprob, 0.0);
+    std::vector<int> iters(nprob, 0), cycles(nprob, 0), refines(nprob, 0), fmv(nprob, 0);
+    bool any_zero = false;
+    for (int b = 0; b < nprob; ++b) {
+        fnorm[b] = std::sqrt(stat[4 * b + 1]);
+        if (!std::isfinite(fnorm[b])) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve_batch: f of problem %d", b);
+        if (fnorm[b] == 0.0) { act[b] = 0; zmask[b] = 1; any_zero = true; }
+    }
+    if (any_zero) {
+        RBF_CUDA(ctx, cudaMemcpyAsync(zero_mask, zmask.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+        RBF_LAUNCH(ctx, k_bzero_inactive_w, bstream_blocks(n), 256, 0, st, w, ctx->pid.p, zero_mask, n);
+        RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+    }
+
+    // Krylov storage
+    const int64_t ldv = ((n + 63) / 64) * 64;
+    double* V64 = nullptr;
+    float *Vf = nullptr, *uf = nullptr, *tf = nullptr;
+    if (!mixed) {
+        RBF_CHECK(ensure(ctx, ctx->V, (size_t)(m + 1) * ldv));
+        V64 = ctx->V.p;
+    } else {
+        if (ctx->rasm_precision == RBF_FP64 || !ctx->W32.p) return fail(ctx, RBF_ERR_STATE,
+            "rbf_solve_batch: the mixed form needs rbf_rasm_setup_batch with precision RBF_FP32");
+        RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 3) * ldv + 1) / 2 + 1));
+        Vf = (float*)ctx->V.p;
+        uf = Vf + (int64_t)(m + 1) * ldv;
+        tf = uf + ldv;
+    }
+    double* r64 = mixed ? ctx->vec_b.p : V64;
+    int total_steps = 0, rounds = 0;
+    rbf_status result = RBF_ERR_NOT_CONVERGED;
+    for (;;) {
+        // true FP64 residual of the active problems
+        RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
+        RBF_LAUNCH(ctx, k_bresidual, (unsigned)nc, kDotThreads, 0, st, f, ctx->vec_a.p, r64, C, active, B.partial);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, B.partial, C, nprob, 1, gm, F_BETA2, active);
+        RBF_CHECK(read_stat());
+        int nact = 0;
+        for (int b = 0; b < nprob; ++b) {
+            if (!act[b]) continue;
+            ++fmv[b];
+            relres[b] = std::sqrt(stat[4 * b + 0]) / fnorm[b];
+            if (!std::isfinite(relres[b])) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve_batch: residual of "
+                                                       "problem %d is not finite", b);
+            if (relres[b] <= p->rtol || iters[b] >= max_iters || (mixed && refines[b] >= max_refine)) act[b] = 0;
+            else ++nact;
+        }
+        RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+        if (nact == 0) break;
+        // one cycle of every active problem
+        RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active);
+        if (!mixed) {
+            RBF_LAUNCH(ctx, k_bscale<double>, bstream_blocks(n), 256, 0, st, V64, n, ctx->pid.p, gm, 0, active);
+            RBF_CHECK(batch_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
+        } else {
+            RBF_LAUNCH(ctx, k_bto_f32_scaled, bstream_blocks(n), 256, 0, st, r64, n, ctx->pid.p, gm, active, Vf);
+            RBF_CHECK(batch_cycle<float>(B, Vf, ldv, m, uf, tf, w));
+        }
+        RBF_CHECK(read_stat());
+        for (int b = 0; b < nprob; ++b) {
+            if (!act[b]) continue;
+            iters[b] += (int)stat[4 * b + 2];
+            est[b] = stat[4 * b + 3];
+            ++cycles[b];
+            if (mixed) ++refines[b];
+        }
+        total_steps += m;
+        ++rounds;
+    }
+    result = RBF_OK;
+    for (int b = 0; b < nprob; ++b)
+        if (!(relres[b] <= p->rtol)) result = RBF_ERR_NOT_CONVERGED;
+    if (infos) {
+        for (int b = 0; b < nprob; ++b) {
+            rbf_solve_info& I = infos[b];
+            std::memset(&I, 0, sizeof(I));
+            I.iters = iters[b];
+            I.restarts = cycles[b];
+            I.refinements = refines[b];
+            I.relres = relres[b];
+            I.relres_est = est[b] * (mixed ? relres[b] : 1.0);
+            I.matvecs = fmv[b] + iters[b];
+            I.applies = iters[b] + cycles[b];
+        }
+    }
+    ctx->batch_rounds = rounds;
+    if (result != RBF_OK) fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve_batch: some problems missed rtol %.1e", p->rtol);
+    return result;
+}
+
+}  // namespace rbf

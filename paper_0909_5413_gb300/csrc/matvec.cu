@@ -28,17 +28,13 @@ constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 struct MvParams {
     const double* xy;          // cell-ordered coordinates (x, y)
     const float* loc;          // FP32 scaled offsets from the point's cell corner (x, y)
-    const int32_t* cell_s;     // cell id of each cell-ordered point
+    const int32_t* cell_s;     // global cell id of each cell-ordered point
     const int32_t* cell_start;
     const int32_t* work;       // (cell, first target) per block
     const double* tab;         // 2^(-j/2048)
-    int ncx, ncy, k;
-    double rc2;                // exact cutoff (squared)
-    double K;                  // 2048 s / ln 2
+    const Prob* prob;          // per-problem grid and kernel constants
+    const int32_t* pid_cell;   // problem of each cell
     double c1, c2, c3;         // exp cubic
-    double knorm;
-    float ca;                  // cell side in the FP32 offset units
-    float rc2f_lo, rc2f_hi;    // FP32 accept / reject thresholds around rc2 in those units
 };
 
 constexpr size_t kMvSmem = kExpTab2048 * sizeof(double)            // table
@@ -61,18 +57,22 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
     const int tid = threadIdx.x;
     for (int i = tid; i < kExpTab2048; i += kMvThreads) tab[i] = P.tab[i];
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
+    const Prob& pr = P.prob[P.pid_cell[cell]];
+    const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
+    const double rc2 = pr.rc2, K = pr.K, knorm = pr.knorm;
+    const float ca = pr.ca, rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
     const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
     const int p = cb + first + tid;
     const bool active = p < ce;
-    const int cx = cell % P.ncx, cy = cell / P.ncx;
-    const int y0 = max(cy - P.k, 0), y1 = min(cy + P.k, P.ncy - 1);
-    const int x0 = max(cx - P.k, 0), x1 = min(cx + P.k, P.ncx - 1);
+    const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
+    const int y0 = max(cy - kst, 0), y1 = min(cy + kst, ncy - 1);
+    const int x0 = max(cx - kst, 0), x1 = min(cx + kst, ncx - 1);
     const int nrow = y1 - y0 + 1;
     if (tid == 0) {
         int s = 0;
         for (int r = 0; r < nrow; ++r) {
             int yy = y0 + r;
-            int b = P.cell_start[yy * P.ncx + x0], e = P.cell_start[yy * P.ncx + x1 + 1];
+            int b = P.cell_start[cbase + yy * ncx + x0], e = P.cell_start[cbase + yy * ncx + x1 + 1];
             row_beg[r] = b;
             row_pre[r] = s;
             s += e - b;
@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
             SX[2 * idx] = P.xy[2 * q];
             SX[2 * idx + 1] = P.xy[2 * q + 1];
             SW[idx] = w[q];
-            int cq = P.cell_s[q];
-            SF[2 * idx] = P.loc[2 * q] + (float)(cq % P.ncx - cx) * P.ca;
-            SF[2 * idx + 1] = P.loc[2 * q + 1] + (float)(cq / P.ncx - cy) * P.ca;
+            int cq = P.cell_s[q] - cbase;
+            SF[2 * idx] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
+            SF[2 * idx + 1] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
         }
         __syncthreads();
         // FP32 filter: one accept bit per staged source. Sources in the thin band
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
                     const int idx = wi * 32 + b;
                     float dx = fx - SF[2 * idx], dy = fy - SF[2 * idx + 1];
                     float r2 = fmaf(dy, dy, dx * dx);
-                    m |= (uint32_t)(r2 < P.rc2f_lo) << b;
-                    band |= (uint32_t)(r2 >= P.rc2f_lo && r2 <= P.rc2f_hi) << b;
+                    m |= (uint32_t)(r2 < rc2f_lo) << b;
+                    band |= (uint32_t)(r2 >= rc2f_lo && r2 <= rc2f_hi) << b;
                 }
             }
             while (band != 0u) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
                 band &= band - 1u;
                 const int idx = wi * 32 + b;
                 double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
-                if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= P.rc2) m |= 1u << b;
+                if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
             }
             MASK[wi * kMvThreads + tid] = m;
         }
@@ -147,11 +147,11 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
                 cur &= cur - 1u;
                 double dx = xi - SX[2 * idx], dy = yi - SX[2 * idx + 1];
                 double r2 = fma(dy, dy, dx * dx);
-                acc = fma(exp_neg_r2(r2, P.K, tab, P.c1, P.c2, P.c3), SW[idx], acc);
+                acc = fma(exp_neg_r2(r2, K, tab, P.c1, P.c2, P.c3), SW[idx], acc);
             }
         }
     }
-    if (active) y[p] = acc * P.knorm;
+    if (active) y[p] = acc * knorm;
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -199,18 +199,21 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const f
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
     const int tid = threadIdx.x;
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
+    const Prob& pr = P.prob[P.pid_cell[cell]];
+    const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
+    const float ca = pr.ca, knorm = (float)pr.knorm;
     const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
     const int p = cb + first + tid;
     const bool active = p < ce;
-    const int cx = cell % P.ncx, cy = cell / P.ncx;
-    const int y0 = max(cy - P.k, 0), y1 = min(cy + P.k, P.ncy - 1);
-    const int x0 = max(cx - P.k, 0), x1 = min(cx + P.k, P.ncx - 1);
+    const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
+    const int y0 = max(cy - kst, 0), y1 = min(cy + kst, ncy - 1);
+    const int x0 = max(cx - kst, 0), x1 = min(cx + kst, ncx - 1);
     const int nrow = y1 - y0 + 1;
     if (tid == 0) {
         int s = 0;
         for (int r = 0; r < nrow; ++r) {
             int yy = y0 + r;
-            int b = P.cell_start[yy * P.ncx + x0], e = P.cell_start[yy * P.ncx + x1 + 1];
+            int b = P.cell_start[cbase + yy * ncx + x0], e = P.cell_start[cbase + yy * ncx + x1 + 1];
             row_beg[r] = b;
             row_pre[r] = s;
             s += e - b;
@@ -234,9 +237,9 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const f
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
             int q = row_beg[r] + (g - row_pre[r]);
-            int cq = P.cell_s[q];
-            SXs[idx] = P.loc[2 * q] + (float)(cq % P.ncx - cx) * P.ca;
-            SYs[idx] = P.loc[2 * q + 1] + (float)(cq / P.ncx - cy) * P.ca;
+            int cq = P.cell_s[q] - cbase;
+            SXs[idx] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
+            SYs[idx] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
             SWs[idx] = w[q];
         }
         if (tid == 0 && (ns & 1)) {   // pad to an even count with a far, zero-weight source
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const f
             acc2 = f2_fma(e, sw, acc2);
         }
     }
-    if (active) y[p] = (acc2.x + acc2.y) * (float)P.knorm;
+    if (active) y[p] = (acc2.x + acc2.y) * knorm;
 }
 
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
@@ -272,9 +275,6 @@ __global__ void k_to_f64(const float* __restrict__ in, int64_t n, double* __rest
     if (i < n) out[i] = (double)in[i];
 }
 
-// Scale of the FP32 local coordinates: a^2 = log2(e) / (2 sigma^2).
-double local_scale(const rbf_ctx* ctx) { return std::sqrt(M_LOG2E * ctx->s); }
-
 MvParams mv_params(const rbf_ctx* ctx)
 {
     MvParams P;
@@ -284,20 +284,11 @@ MvParams mv_params(const rbf_ctx* ctx)
     P.cell_start = ctx->cell_start.p;
     P.work = ctx->mv_work.p;
     P.tab = ctx->exp2048.p;
-    P.ncx = (int)ctx->ncx;
-    P.ncy = (int)ctx->ncy;
-    P.k = ctx->kst;
-    P.rc2 = ctx->rc2;
-    P.K = 2048.0 * ctx->s / M_LN2;
+    P.prob = ctx->prob.p;
+    P.pid_cell = ctx->pid_cell.p;
     P.c1 = ctx->exp2048_c[0];
     P.c2 = ctx->exp2048_c[1];
     P.c3 = ctx->exp2048_c[2];
-    P.knorm = ctx->knorm;
-    double a = local_scale(ctx);
-    P.ca = (float)(ctx->cell * a);
-    double rc2f = ctx->rc2 * a * a;
-    P.rc2f_lo = (float)(rc2f * (1.0 - 1e-4));
-    P.rc2f_hi = (float)(rc2f * (1.0 + 1e-4));
     return P;
 }
 

@@ -23,13 +23,15 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
     k_rasm_setup(const double* __restrict__ xy_s, const int32_t* __restrict__ ov_ptr,
                  const int32_t* __restrict__ ov_idx, const int32_t* __restrict__ core_of,
                  const int32_t* __restrict__ core_ptr, const int64_t* __restrict__ w_off, int64_t nsub, int nmax,
-                 int ncmax, int wpb, double rc2, double s, double knorm, double* __restrict__ W64,
-                 float* __restrict__ W32, int* __restrict__ status)
+                 int ncmax, int wpb, const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub,
+                 double* __restrict__ W64, float* __restrict__ W32, int* __restrict__ status)
 {
     extern __shared__ double sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t sub = (int64_t)blockIdx.x * wpb + warp;
     if (warp >= wpb || sub >= nsub) return;
+    const Prob& pr = prob[pid_sub[sub]];
+    const double rc2 = pr.rc2, s = pr.s, knorm = pr.knorm;
     const size_t per = (size_t)nmax * nmax + (size_t)ncmax * nmax + 2 * (size_t)nmax;
     double* A = sm + per * warp;
     double* X = A + (size_t)nmax * nmax;
@@ -192,8 +194,8 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
     RBF_CUDA(ctx, cudaFuncSetAttribute(k_rasm_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_SETUP, st));
     RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nsub, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
-               ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, ncmax, wpb, ctx->rc2, ctx->s,
-               ctx->knorm, W64, W32, ctx->status_dev.p);
+               ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, ncmax, wpb, ctx->prob.p,
+               ctx->pid_sub.p, W64, W32, ctx->status_dev.p);
     RBF_CHECK(prof_end(ctx, RBF_PROF_RASM_SETUP, st));
     int status = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&status, ctx->status_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));

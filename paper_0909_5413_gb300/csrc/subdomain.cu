@@ -25,24 +25,20 @@ __device__ __forceinline__ bool in_overlap(double v, int64_t k, int64_t kc, doub
     return v >= __dsub_rn(__dadd_rn(o, __dmul_rn((double)k, B)), delta);
 }
 
-struct Boxes {
-    double x0, y0, B, delta;
-    int64_t nbx, nby;
-    int reach;
-};
-
 // mode 0: count core / overlap members; mode 1: place them (unordered slots).
-__global__ void k_boxes(const double* __restrict__ xy_s, int64_t n, Boxes bx, int32_t* __restrict__ core_of,
-                        int32_t* __restrict__ ccnt, int32_t* __restrict__ ocnt, const int32_t* __restrict__ cptr,
-                        const int32_t* __restrict__ optr, int32_t* __restrict__ cidx, int32_t* __restrict__ oidx,
-                        int mode)
+// Box grid and subdomain numbering of each point's problem from prob[pid[p]].
+__global__ void k_boxes(const double* __restrict__ xy_s, int64_t n, const Prob* __restrict__ prob,
+                        const int32_t* __restrict__ pid, int32_t* __restrict__ core_of, int32_t* __restrict__ ccnt,
+                        int32_t* __restrict__ ocnt, const int32_t* __restrict__ cptr, const int32_t* __restrict__ optr,
+                        int32_t* __restrict__ cidx, int32_t* __restrict__ oidx, int mode)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    const Prob& bx = prob[pid[p]];
     double x = xy_s[2 * p], y = xy_s[2 * p + 1];
     int64_t cx = box_axis(x, bx.x0, bx.B, bx.nbx);
     int64_t cy = box_axis(y, bx.y0, bx.B, bx.nby);
-    int64_t sc = cy * bx.nbx + cx;
+    int64_t sc = bx.subbase + cy * bx.nbx + cx;
     if (mode == 0) {
         core_of[p] = (int32_t)sc;
         atomicAdd(&ccnt[sc], 1);
@@ -58,7 +54,7 @@ __global__ void k_boxes(const double* __restrict__ xy_s, int64_t n, Boxes bx, in
         if (!in_overlap(y, ky, cy, bx.y0, bx.B, bx.delta)) continue;
         for (int64_t kx = kx0; kx <= kx1; ++kx) {
             if (!in_overlap(x, kx, cx, bx.x0, bx.B, bx.delta)) continue;
-            int64_t s = ky * bx.nbx + kx;
+            int64_t s = bx.subbase + ky * bx.nbx + kx;
             if (mode == 0) {
                 atomicAdd(&ocnt[s], 1);
             } else {
@@ -67,6 +63,18 @@ __global__ void k_boxes(const double* __restrict__ xy_s, int64_t n, Boxes bx, in
             }
         }
     }
+}
+
+__global__ void k_pid_subs(const Prob* __restrict__ prob, int nprob, int64_t nsub, int32_t* __restrict__ pid_sub)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsub) return;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prob[mid].subbase <= s) lo = mid; else hi = mid - 1;
+    }
+    pid_sub[s] = lo;
 }
 
 // One warp per list: order the entries by the user index perm[entry] (rank sort).
@@ -98,13 +106,7 @@ __global__ void k_export(const int32_t* __restrict__ in, int64_t n, const int32_
 rbf_status build_subdomains(rbf_ctx* ctx, cudaStream_t st)
 {
     const int64_t n = ctx->n, nsub = ctx->nsub;
-    Boxes b;
-    b.x0 = ctx->x0; b.y0 = ctx->y0; b.B = ctx->B; b.delta = ctx->delta;
-    b.nbx = ctx->nbx; b.nby = ctx->nby;
-    double reach = std::ceil(ctx->delta / ctx->B) + 1.0;
-    if (reach > 64.0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: overlap / core_size too large");
-    b.reach = (int)reach;
-
+    const int nprob = (int)ctx->nprob;
     RBF_CHECK(ensure(ctx, ctx->core_of, n));
     RBF_CHECK(ensure(ctx, ctx->core_ptr, nsub + 1));
     RBF_CHECK(ensure(ctx, ctx->ov_ptr, nsub + 1));
@@ -112,8 +114,10 @@ rbf_status build_subdomains(rbf_ctx* ctx, cudaStream_t st)
     int32_t* ccnt = ctx->sub_cnt.p;
     int32_t* ocnt = ctx->sub_cnt.p + (nsub + 1);
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->sub_cnt.p, 0, sizeof(int32_t) * 2 * (nsub + 1), st));
-    RBF_LAUNCH(ctx, k_boxes, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, b, ctx->core_of.p, ccnt, ocnt,
-               (const int32_t*)nullptr, (const int32_t*)nullptr, (int32_t*)nullptr, (int32_t*)nullptr, 0);
+    RBF_CHECK(ensure(ctx, ctx->pid_sub, nsub));
+    RBF_LAUNCH(ctx, k_pid_subs, blocks_for(nsub, 256), 256, 0, st, ctx->prob.p, nprob, nsub, ctx->pid_sub.p);
+    RBF_LAUNCH(ctx, k_boxes, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, ctx->prob.p, ctx->pid.p, ctx->core_of.p,
+               ccnt, ocnt, (const int32_t*)nullptr, (const int32_t*)nullptr, (int32_t*)nullptr, (int32_t*)nullptr, 0);
     int32_t mx = 0;
     RBF_CHECK(reduce_max_i32(ctx, ocnt, nsub, &mx, st));
     ctx->max_ov = mx;
@@ -133,8 +137,8 @@ rbf_status build_subdomains(rbf_ctx* ctx, cudaStream_t st)
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->sub_cnt.p, 0, sizeof(int32_t) * 2 * (nsub + 1), st));
     // place overlap members into tmp, core members directly (sorted below)
     RBF_CHECK(ensure(ctx, ctx->sub_fill, (size_t)tot[0]));
-    RBF_LAUNCH(ctx, k_boxes, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, b, ctx->core_of.p, ccnt, ocnt,
-               ctx->core_ptr.p, ctx->ov_ptr.p, ctx->sub_fill.p, ctx->tmp_i32.p, 1);
+    RBF_LAUNCH(ctx, k_boxes, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, ctx->prob.p, ctx->pid.p, ctx->core_of.p,
+               ccnt, ocnt, ctx->core_ptr.p, ctx->ov_ptr.p, ctx->sub_fill.p, ctx->tmp_i32.p, 1);
     RBF_LAUNCH(ctx, k_sort_lists, blocks_for(nsub * 32, 256), 256, 0, st, ctx->core_ptr.p, nsub, ctx->perm.p,
                ctx->sub_fill.p, ctx->core_idx.p);
     RBF_LAUNCH(ctx, k_sort_lists, blocks_for(nsub * 32, 256), 256, 0, st, ctx->ov_ptr.p, nsub, ctx->perm.p,

@@ -1,0 +1,50 @@
+// vecops.cuh -- device helpers shared by the GMRES drivers: double-float
+// accumulation of FP32 data and a block-wide FP64 sum.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbf {
+
+constexpr int kDotThreads = 256;
+
+// Double-float accumulator for FP32 data (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26(6), 2005: TwoProduct by FMA,
+// TwoSum, and the Dot2 recurrence): a sum of exact FP32 products carried as an
+// unevaluated hi + lo pair, as accurate as accumulating in twice the FP32
+// precision. On GB300 this keeps FP64-class dot products on the FP32 pipe.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DF& s, float h, float r)
+{
+    float p = s.hi + h;                 // TwoSum(s.hi, h) = (p, q)
+    float z = p - s.hi;
+    float q = (s.hi - (p - z)) + (h - z);
+    s.hi = p;
+    s.lo = s.lo + (q + r);
+}
+
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b)
+{
+    float h = a * b;                    // TwoProduct(a, b) = (h, r)
+    float r = fmaf(a, b, -h);
+    df_add(s, h, r);
+}
+
+// Sum of one value per thread over a block of kDotThreads threads, returned
+// to thread 0 (fixed order: shuffle tree within warps, warps in order).
+__device__ __forceinline__ double block_sum(double a, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
+    return s;
+}
+
+}  // namespace rbf

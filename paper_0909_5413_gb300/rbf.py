@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_INVALID_ARG", 2: "RBF_ERR_OOM", 3: "RBF
 EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setup", "rbf_rasm_apply", "rbf_solve",
             "rbf_interpolate_host", "rbf_get_grid", "rbf_get_bins", "rbf_get_subdomain_sizes", "rbf_get_subdomains",
             "rbf_count_neighbors", "rbf_get_neighbors", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
-            "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc"]
+            "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
+            "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -100,6 +101,9 @@ def load(path: str | None = None):
     L.rbf_profile_read.argtypes = [P, C.c_int, I64, D]
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
     L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
+    L.rbf_bin_batch.argtypes = [P, P, I64, C.c_int64, C.POINTER(RbfParams), P]
+    L.rbf_rasm_setup_batch.argtypes = [P, C.POINTER(RbfRasmParams), P]
+    L.rbf_solve_batch.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
     for name in EXPORTED:
         if name not in ("rbf_destroy", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
                         "rbf_device_bytes"):
@@ -185,6 +189,27 @@ def rbf_interpolate_host(ctx, xy_host, f_host, w_host, n: int, params: RbfParams
     if check:
         _check(ctx, st)
     return st, info
+
+
+def rbf_bin_batch(ctx, xy_dev, ptr: list[int], params: list[RbfParams], stream=None) -> None:
+    nprob = len(params)
+    p = (C.c_int64 * (nprob + 1))(*[int(v) for v in ptr])
+    pa = (RbfParams * nprob)(*params)
+    _check(ctx, load().rbf_bin_batch(ctx, _ptr(xy_dev), p, nprob, pa, _stream(stream)))
+
+
+def rbf_rasm_setup_batch(ctx, params: list[RbfRasmParams], stream=None) -> None:
+    pa = (RbfRasmParams * len(params))(*params)
+    _check(ctx, load().rbf_rasm_setup_batch(ctx, pa, _stream(stream)))
+
+
+def rbf_solve_batch(ctx, f_dev, w_dev, params: RbfSolveParams, nprob: int, stream=None,
+                    check: bool = True) -> tuple[int, list[RbfSolveInfo]]:
+    infos = (RbfSolveInfo * nprob)()
+    st = load().rbf_solve_batch(ctx, _ptr(f_dev), _ptr(w_dev), C.byref(params), infos, _stream(stream))
+    if check:
+        _check(ctx, st)
+    return st, list(infos)
 
 
 def rbf_get_grid(ctx) -> tuple[int, int, tuple[float, float, float, float]]:
@@ -324,6 +349,19 @@ class Context:
     @property
     def launches(self) -> int:
         return rbf_launch_count(self.handle)
+
+
+def batch_arrays(problems, cell_size: float = 0.0, factor_precision: int = RBF_FP64, max_sub_points: int = 0):
+    """Concatenated inputs of a batch: (xy (N, 2), f (N,), ptr, [RbfParams], [RbfRasmParams])."""
+    import numpy as np
+    xy = np.ascontiguousarray(np.concatenate([p.xy for p in problems]), dtype=np.float64)
+    f = np.ascontiguousarray(np.concatenate([p.f for p in problems]), dtype=np.float64)
+    ptr = [0]
+    for p in problems:
+        ptr.append(ptr[-1] + p.n)
+    params = [RbfParams(p.sigma, p.cutoff, cell_size, 0) for p in problems]
+    rasm = [RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, max_sub_points, factor_precision) for p in problems]
+    return xy, f, ptr, params, rasm
 
 
 def config_for(problem, **kw) -> SolverConfig:

@@ -143,6 +143,23 @@ def batch_problem_sizes(count: int, lo: int, hi: int, seed: int) -> list[tuple[i
     return out
 
 
+def batch_workload(count: int, lo: int = 256, hi: int = 16384, seed: int = DEFAULT_SEED,
+                   ratio_lo: float = 0.6, ratio_hi: float = 1.0) -> list[Problem]:
+    """Many independent problems: N log-uniform in [lo, hi] (n_side = round(sqrt N)),
+    h/sigma uniform in [ratio_lo, ratio_hi], each on its own jittered lattice over
+    [-1, 1]^2 with a sum of four random Gaussians as right-hand side; problem k
+    uses seed + k."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+        n_side = max(2, int(round(math.sqrt(n))))
+        ratio = float(rng.uniform(ratio_lo, ratio_hi))
+        out.append(lattice_problem(n_side, ratio, seed=seed + 1 + k, rhs="four_gaussians",
+                                   name=f"batch{k}_n{n_side}_r{ratio:.3f}"))
+    return out
+
+
 def unit_square_problem(h_over_sigma: float, sigma: float = 0.01, seed: int = DEFAULT_SEED,
                         jitter: float = 0.0) -> Problem:
     """Franke's function on a lattice over [0, 1]^2 with ``N = (1/h + 1)^2`` (Sec. 3.1),

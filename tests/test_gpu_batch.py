@@ -1,0 +1,153 @@
+"""Batches of independent problems in one context: every problem of the batch
+must give what the oracle gives for it alone (bit-exact index work, FP64 matvec
+within 1e-13, solves to a true relative residual <= 1e-13), and a problem's
+solution must not depend on the other problems of the batch."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0909_5413_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    from paper_0909_5413_gb300 import rbf as R
+    R.load()
+    return R
+
+
+def small_batch():
+    sizes = [(2, 0.9), (3, 1.0), (16, 0.8), (21, 0.95), (33, 0.85), (12, 0.8), (40, 0.9)]
+    return [W.lattice_problem(n, r, seed=100 + k, rhs="four_gaussians") for k, (n, r) in enumerate(sizes)]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def setup(rbf, probs, factor_precision=0):
+    xy, f, ptr, params, rasm = rbf.batch_arrays(probs, factor_precision=factor_precision)
+    ctx = rbf.Context(0)
+    rbf.rbf_bin_batch(ctx.handle, dev(xy), ptr, params)
+    rbf.rbf_rasm_setup_batch(ctx.handle, rasm)
+    return ctx, xy, f, ptr
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_batch_binning_and_lists_match_each_problem_alone(rbf):
+    probs = small_batch()
+    ctx, xy, f, ptr = setup(rbf, probs)
+    n = ptr[-1]
+    pd = torch.empty(n, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_bins(ctx.handle, pd, None)
+    perm = host(pd)
+    nsub_tot, _, ct, ot = rbf.rbf_get_subdomain_sizes(ctx.handle)
+    cp = torch.empty(nsub_tot + 1, dtype=torch.int32, device="cuda")
+    op = torch.empty(nsub_tot + 1, dtype=torch.int32, device="cuda")
+    ci = torch.empty(ct, dtype=torch.int32, device="cuda")
+    oi = torch.empty(ot, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_subdomains(ctx.handle, cp, ci, op, oi)
+    cp, ci, op, oi = host(cp), host(ci), host(op), host(oi)
+    sub0 = 0
+    for b, p in enumerate(probs):
+        lo, hi = ptr[b], ptr[b + 1]
+        _, rperm, _ = O.bin_points(p.xy, p.cutoff)
+        np.testing.assert_array_equal(perm[lo:hi] - lo, rperm)
+        (nbx, nby), rcp, rci, rop, roi = O.subdomains(p.xy, p.x0, p.x0, p.core_size, p.overlap)
+        ns = nbx * nby
+        np.testing.assert_array_equal(cp[sub0:sub0 + ns + 1] - cp[sub0], rcp)
+        np.testing.assert_array_equal(ci[cp[sub0]:cp[sub0 + ns]] - lo, rci)
+        np.testing.assert_array_equal(op[sub0:sub0 + ns + 1] - op[sub0], rop)
+        np.testing.assert_array_equal(oi[op[sub0]:op[sub0 + ns]] - lo, roi)
+        sub0 += ns
+    assert sub0 == nsub_tot
+    ctx.close()
+
+
+def test_batch_matvec_and_rasm_per_problem(rbf):
+    probs = small_batch()
+    ctx, xy, f, ptr = setup(rbf, probs)
+    n = ptr[-1]
+    v = np.random.default_rng(3).standard_normal(n)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(v), y)
+    rbf.rbf_rasm_apply(ctx.handle, dev(v), z)
+    y, z = host(y), host(z)
+    for b, p in enumerate(probs):
+        lo, hi = ptr[b], ptr[b + 1]
+        ref = O.matvec_cutoff(p.xy, v[lo:hi], p.sigma, p.cutoff)
+        assert rel(y[lo:hi], ref) <= 1e-13
+        pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+        assert rel(z[lo:hi], pr.rasm_apply(v[lo:hi])) <= 1e-10
+    ctx.close()
+
+
+def solve_batch(rbf, probs, mixed=False, repeat=1):
+    ctx, xy, f, ptr = setup(rbf, probs, factor_precision=1 if mixed else 0)
+    sp = rbf.RbfSolveParams(1e-13, 30, 20000, int(mixed), 60, 1e-5)
+    outs = []
+    for _ in range(repeat):
+        w = torch.zeros(ptr[-1], dtype=torch.float64, device="cuda")
+        st, infos = rbf.rbf_solve_batch(ctx.handle, dev(f), w, sp, len(probs), check=False)
+        outs.append(host(w))
+    ctx.close()
+    return st, infos, outs, ptr
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_solve_reaches_tolerance_per_problem(rbf, mixed):
+    probs = small_batch()
+    st, infos, (w,), ptr = solve_batch(rbf, probs, mixed)
+    assert st == 0, [i.as_dict() for i in infos]
+    for b, p in enumerate(probs):
+        wb = w[ptr[b]:ptr[b + 1]]
+        r = p.f - O.matvec_cutoff(p.xy, wb, p.sigma, p.cutoff)
+        assert np.linalg.norm(r) / np.linalg.norm(p.f) <= 1e-13, (b, infos[b].as_dict())
+        assert infos[b].relres <= 1e-13
+
+
+def test_batch_result_independent_of_the_mix(rbf):
+    """Each problem's w is bit-identical alone and inside the batch, and the
+    batch result is reproducible run to run."""
+    probs = small_batch()
+    _, _, (w1, w2), ptr = solve_batch(rbf, probs, repeat=2)
+    np.testing.assert_array_equal(w1, w2)
+    for b in (1, 4, 6):
+        _, _, (wa,), _ = solve_batch(rbf, [probs[b]])
+        np.testing.assert_array_equal(wa, w1[ptr[b]:ptr[b + 1]])
+
+
+def test_single_solver_equals_batch_of_one(rbf):
+    p = W.lattice_problem(30, 0.85, seed=7)
+    _, _, (wb,), _ = solve_batch(rbf, [p])
+    cfg = rbf.config_for(p)
+    ctx = rbf.Context(0)
+    ctx.bin(dev(p.xy), cfg)
+    ctx.rasm_setup(cfg)
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = ctx.solve(dev(p.f), w, cfg)
+    np.testing.assert_array_equal(host(w), wb)
+    ctx.close()
+
+
+def test_batch_rejects_single_problem_calls(rbf):
+    probs = small_batch()[:3]
+    ctx, xy, f, ptr = setup(rbf, probs)
+    w = torch.zeros(ptr[-1], dtype=torch.float64, device="cuda")
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_solve(ctx.handle, dev(f), w, rbf.RbfSolveParams(1e-13, 30, 100, 0, 0, 0.0))
+    assert e.value.status == 8
+    ctx.close()
