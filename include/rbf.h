@@ -88,6 +88,8 @@ typedef struct {
     double relres_est;    /* last GMRES residual estimate |g_{j+1}| / ||f|| */
     int matvecs;          /* FP64 matvecs + FP32 matvecs */
     int applies;          /* preconditioner applications */
+    int status;           /* rbf_status of this solve / problem */
+    int stagnated;        /* 1: stopped because the true residual stopped decreasing */
 } rbf_solve_info;
 
 /* Create a context on CUDA device `device` (makes it current). */
@@ -125,7 +127,9 @@ rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_
  * Sec. 3.1). w_dev holds the initial guess on entry (zeros for none) and the
  * solution on return, so a later call continues from it. info (host,
  * optional) is filled. Synchronises `stream`. Returns NOT_CONVERGED (with the
- * best w) if rtol is not met within max_iters. Needs rbf_rasm_setup. */
+ * best w) if rtol is not met within max_iters, or as soon as the true
+ * residual stagnates: less than 10 % reduction over three consecutive restart
+ * cycles (info.stagnated = 1). Needs rbf_rasm_setup. */
 rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* params,
                      rbf_solve_info* info, rbf_stream stream);
 

@@ -372,6 +372,7 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
     RBF_CHECK(ensure(ctx, ctx->mv_work, 2 * (size_t)std::max<int32_t>(nwork, 1)));
     RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell,
                ctx->mv_work.p);
+    RBF_CHECK(matvec_prepare(ctx));
     return prof_end(ctx, RBF_PROF_BIN, st);
 }
 

@@ -209,6 +209,9 @@ void rbf_destroy(rbf_ctx* ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    batch_graph_reset(ctx);
+    if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
+    if (ctx->bevent) cudaEventDestroy(ctx->bevent);
     for (auto& a : ctx->owned) cudaFree(a.first);
     ctx->owned.clear();
     for (auto& s : ctx->prof_slots)

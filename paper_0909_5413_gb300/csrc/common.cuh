@@ -134,6 +134,11 @@ struct rbf_ctx {
     rbf::DevArray<int32_t> bactive;    // per-problem active / zero masks
     rbf::DevArray<double> bstat;       // per-problem summary for the host
     int batch_rounds = 0;
+    const int32_t* active_mask = nullptr;   // problems the matvec / apply skip when 0 (null: none)
+    cudaStream_t bstream = nullptr;         // capturable stream of the batched solver
+    cudaEvent_t bevent = nullptr;
+    cudaGraphExec_t bgraph = nullptr;       // captured Arnoldi cycle of the batched solver
+    uint64_t bgraph_launches = 0;           // kernels in that graph
 };
 
 namespace rbf {
@@ -201,6 +206,10 @@ rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStrea
 rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 // The FP64 matvec launch alone (no profiler events), for the allocation-free entry point.
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+// Function attributes of the matvec kernels (called once per binning, outside any capture).
+rbf_status matvec_prepare(rbf_ctx* ctx);
+// Drop the captured batched cycle (its kernels hold pointers into the context).
+void batch_graph_reset(rbf_ctx* ctx);
 
 // ---- rasm.cu  (vectors in cell order)
 rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st);

@@ -510,6 +510,8 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
     }
 
     int it = 0, cycles = 0, refine = 0, matvecs = 0, applies = 0;
+    std::vector<double> hist;   // true relative residual at each restart
+    bool stagnated = false;
     double relres = 0.0, est = 0.0;
     rbf_status result = RBF_ERR_NOT_CONVERGED;
 
@@ -522,6 +524,7 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
             if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
             if (relres <= p->rtol) { result = RBF_OK; break; }
             if (it >= max_iters) break;
+            if (stagnating(hist, relres)) { stagnated = true; break; }
             RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 0);
             int steps = 0;
             RBF_CHECK((gmres_cycle<double, OpsF64>(ctx, V, n, m, max_iters - it, ctx->vec_b.p, ctx->vec_a.p, w,
@@ -563,6 +566,7 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
             if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
             if (relres <= p->rtol) { result = RBF_OK; break; }
             if (it >= max_iters || refine >= max_refine) break;
+            if (stagnating(hist, relres)) { stagnated = true; break; }
             const double rnorm = relres * fnorm;
             // inner solve of A d = b, b = r / |r| (norm 1), from d = 0, restarted on
             // the FP32 inner residual b - A d until inner_rtol or kMaxInnerCycles
@@ -606,6 +610,8 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
     info->relres_est = est;
     info->matvecs = matvecs;
     info->applies = applies;
+    info->status = result;
+    info->stagnated = stagnated ? 1 : 0;
     if (result != RBF_OK)
         fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: relative residual %.3e after %d steps (rtol %.1e)", relres, it,
              p->rtol);

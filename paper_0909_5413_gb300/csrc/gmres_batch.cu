@@ -462,11 +462,68 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
     return RBF_OK;
 }
 
+// One cycle: captured into a CUDA graph on its first use in a solve and
+// replayed afterwards (the kernel arguments of a cycle do not change within a
+// solve; the per-problem masks and states they read live in device memory).
+template <class T>
+rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double* w)
+{
+    rbf_ctx* ctx = B.ctx;
+    if (!ctx->bgraph) {
+        const bool prof = ctx->prof;
+        const uint64_t l0 = ctx->launches;
+        ctx->prof = false;   // no event records inside the graph
+        RBF_CUDA(ctx, cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
+        rbf_status s = batch_cycle<T>(B, V, ldv, m, u, t, w);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(B.st, &g);
+        ctx->prof = prof;
+        if (s != RBF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (s != RBF_OK) return s;
+            return cuda_fail(ctx, e, "rbf_solve_batch: graph capture");
+        }
+        e = cudaGraphInstantiate(&ctx->bgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->bgraph = nullptr;
+            return cuda_fail(ctx, e, "rbf_solve_batch: graph instantiation");
+        }
+        ctx->bgraph_launches = ctx->launches - l0;
+        ctx->launches = l0;
+    }
+    RBF_CUDA(ctx, cudaGraphLaunch(ctx->bgraph, B.st));
+    ctx->launches += ctx->bgraph_launches;
+    return RBF_OK;
+}
+
+// Clears the matvec / apply mask when the batched solve returns.
+struct MaskGuard {
+    rbf_ctx* ctx;
+    ~MaskGuard() { ctx->active_mask = nullptr; }
+};
+
 }  // namespace
 
-rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf_solve_params* p,
-                             rbf_solve_info* infos, cudaStream_t st)
+void batch_graph_reset(rbf_ctx* ctx)
 {
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    ctx->bgraph_launches = 0;
+}
+
+rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf_solve_params* p,
+                             rbf_solve_info* infos, cudaStream_t user_st)
+{
+    // the solve runs on a stream of its own (capturable), ordered after user_st
+    if (!ctx->bstream) {
+        RBF_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+        RBF_CUDA(ctx, cudaEventCreateWithFlags(&ctx->bevent, cudaEventDisableTiming));
+    }
+    RBF_CUDA(ctx, cudaEventRecord(ctx->bevent, user_st));
+    RBF_CUDA(ctx, cudaStreamWaitEvent(ctx->bstream, ctx->bevent, 0));
+    cudaStream_t st = ctx->bstream;
+    MaskGuard guard{ctx};
     const int64_t n = ctx->n;
     const int nprob = (int)ctx->nprob;
     const int m = p->restart > 0 ? p->restart : 30;
@@ -555,6 +612,10 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     double* r64 = mixed ? ctx->vec_b.p : V64;
     int total_steps = 0, rounds = 0;
     rbf_status result = RBF_ERR_NOT_CONVERGED;
+    std::vector<std::vector<double>> hist(nprob);
+    std::vector<int> stagnated(nprob, 0);
+    ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
+    batch_graph_reset(ctx);      // buffers may have moved since the last solve
     for (;;) {
         // true FP64 residual of the active problems
         RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
@@ -568,8 +629,14 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             relres[b] = std::sqrt(stat[4 * b + 0]) / fnorm[b];
             if (!std::isfinite(relres[b])) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve_batch: residual of "
                                                        "problem %d is not finite", b);
-            if (relres[b] <= p->rtol || iters[b] >= max_iters || (mixed && refines[b] >= max_refine)) act[b] = 0;
-            else ++nact;
+            if (relres[b] <= p->rtol || iters[b] >= max_iters || (mixed && refines[b] >= max_refine)) {
+                act[b] = 0;
+            } else if (stagnating(hist[b], relres[b])) {
+                act[b] = 0;
+                stagnated[b] = 1;
+            } else {
+                ++nact;
+            }
         }
         RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         if (nact == 0) break;
@@ -577,10 +644,10 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active);
         if (!mixed) {
             RBF_LAUNCH(ctx, k_bscale<double>, bstream_blocks(n), 256, 0, st, V64, n, ctx->pid.p, gm, 0, active);
-            RBF_CHECK(batch_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
+            RBF_CHECK(run_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
         } else {
             RBF_LAUNCH(ctx, k_bto_f32_scaled, bstream_blocks(n), 256, 0, st, r64, n, ctx->pid.p, gm, active, Vf);
-            RBF_CHECK(batch_cycle<float>(B, Vf, ldv, m, uf, tf, w));
+            RBF_CHECK(run_cycle<float>(B, Vf, ldv, m, uf, tf, w));
         }
         RBF_CHECK(read_stat());
         for (int b = 0; b < nprob; ++b) {
@@ -607,6 +674,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             I.relres_est = est[b] * (mixed ? relres[b] : 1.0);
             I.matvecs = fmv[b] + iters[b];
             I.applies = iters[b] + cycles[b];
+            I.status = relres[b] <= p->rtol ? RBF_OK : RBF_ERR_NOT_CONVERGED;
+            I.stagnated = stagnated[b];
         }
     }
     ctx->batch_rounds = rounds;

@@ -34,6 +34,7 @@ struct MvParams {
     const double* tab;         // 2^(-j/2048)
     const Prob* prob;          // per-problem grid and kernel constants
     const int32_t* pid_cell;   // problem of each cell
+    const int32_t* active;     // per-problem mask (null: every problem)
     double c1, c2, c3;         // exp cubic
 };
 
@@ -57,7 +58,9 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
     const int tid = threadIdx.x;
     for (int i = tid; i < kExpTab2048; i += kMvThreads) tab[i] = P.tab[i];
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
-    const Prob& pr = P.prob[P.pid_cell[cell]];
+    const int pcell = P.pid_cell[cell];
+    if (P.active && !P.active[pcell]) return;   // masked problem (the whole block belongs to it)
+    const Prob& pr = P.prob[pcell];
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
     const double rc2 = pr.rc2, K = pr.K, knorm = pr.knorm;
     const float ca = pr.ca, rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
@@ -199,7 +202,9 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const f
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
     const int tid = threadIdx.x;
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
-    const Prob& pr = P.prob[P.pid_cell[cell]];
+    const int pcell = P.pid_cell[cell];
+    if (P.active && !P.active[pcell]) return;   // masked problem (the whole block belongs to it)
+    const Prob& pr = P.prob[pcell];
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
     const float ca = pr.ca, knorm = (float)pr.knorm;
     const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
@@ -286,6 +291,7 @@ MvParams mv_params(const rbf_ctx* ctx)
     P.tab = ctx->exp2048.p;
     P.prob = ctx->prob.p;
     P.pid_cell = ctx->pid_cell.p;
+    P.active = ctx->active_mask;
     P.c1 = ctx->exp2048_c[0];
     P.c2 = ctx->exp2048_c[1];
     P.c3 = ctx->exp2048_c[2];
@@ -294,11 +300,16 @@ MvParams mv_params(const rbf_ctx* ctx)
 
 }  // namespace
 
-rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+rbf_status matvec_prepare(rbf_ctx* ctx)
 {
     RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMvSmem));
     RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared));
+    return RBF_OK;
+}
+
+rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+{
     if (ctx->n_work == 0) return RBF_OK;
     RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMvThreads, kMvSmem, st, mv_params(ctx), w, y);
     return RBF_OK;

@@ -122,12 +122,14 @@ __global__ void __launch_bounds__(256)
     k_rasm_apply(const int32_t* __restrict__ ov_ptr, const int32_t* __restrict__ ov_idx,
                  const int32_t* __restrict__ core_ptr, const int32_t* __restrict__ core_idx,
                  const int64_t* __restrict__ w_off, const TW* __restrict__ W, int64_t nsub,
-                 const TV* __restrict__ r, TV* __restrict__ z)
+                 const int32_t* __restrict__ pid_sub, const int32_t* __restrict__ active, const TV* __restrict__ r,
+                 TV* __restrict__ z)
 {
     __shared__ TV rg_all[8][kMaxSub];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t sub = (int64_t)blockIdx.x * 8 + warp;
     if (sub >= nsub) return;
+    if (active && !active[pid_sub[sub]]) return;   // masked problem (warp-uniform)
     TV* rg = rg_all[warp];
     const int b = ov_ptr[sub];
     const int n = ov_ptr[sub + 1] - b;
@@ -210,10 +212,12 @@ rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStrea
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
     if (ctx->rasm_precision == RBF_FP64)
         RBF_LAUNCH(ctx, (k_rasm_apply<double, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W64.p, ctx->nsub, r, z);
+                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W64.p, ctx->nsub,
+                   ctx->pid_sub.p, ctx->active_mask, r, z);
     else
         RBF_LAUNCH(ctx, (k_rasm_apply<float, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub, r, z);
+                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub,
+                   ctx->pid_sub.p, ctx->active_mask, r, z);
     return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
 }
 
@@ -221,7 +225,8 @@ rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStr
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
     RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p, ctx->ov_idx.p,
-               ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub, r, z);
+               ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub, ctx->pid_sub.p,
+               ctx->active_mask, r, z);
     return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
 }
 

@@ -2,9 +2,20 @@
 // accumulation of FP32 data and a block-wide FP64 sum.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace rbf {
+
+// Records the true relative residual of a restart; true when it is above 90 %
+// of the value three restarts earlier (stagnation of restarted GMRES).
+inline bool stagnating(std::vector<double>& hist, double relres)
+{
+    hist.push_back(relres);
+    const size_t k = hist.size();
+    return k >= 4 && relres > 0.9 * hist[k - 4];
+}
 
 constexpr int kDotThreads = 256;
 

@@ -48,7 +48,8 @@ class RbfSolveParams(C.Structure):
 
 class RbfSolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("refinements", C.c_int), ("relres", C.c_double),
-                ("relres_est", C.c_double), ("matvecs", C.c_int), ("applies", C.c_int)]
+                ("relres_est", C.c_double), ("matvecs", C.c_int), ("applies", C.c_int), ("status", C.c_int),
+                ("stagnated", C.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -151,3 +151,36 @@ def test_batch_rejects_single_problem_calls(rbf):
         rbf.rbf_solve(ctx.handle, dev(f), w, rbf.RbfSolveParams(1e-13, 30, 100, 0, 0, 0.0))
     assert e.value.status == 8
     ctx.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_stagnating_problem_stops_alone(rbf, mixed):
+    """h/sigma = 0.6 with 4x4-point subdomains stalls near a relative residual
+    of 0.44 (the oracle's GMRES on the same problem stays above 0.43 for 3000
+    steps): it is stopped on its own with status NOT_CONVERGED and the flag
+    set, while the other problems converge exactly as they do alone."""
+    probs = small_batch()[2:5]
+    hard = W.lattice_problem(24, 0.6, seed=5, rhs="four_gaussians")
+    mix = probs[:1] + [hard] + probs[1:]
+    st, infos, (w,), ptr = solve_batch(rbf, mix, mixed)
+    assert st == 6
+    hi = infos[1]
+    assert hi.stagnated == 1 and hi.status == 6, hi.as_dict()
+    assert 0.3 < hi.relres < 1.0 and hi.iters < 400
+    for b in (0, 2, 3):
+        assert infos[b].status == 0 and infos[b].stagnated == 0, infos[b].as_dict()
+        _, _, (wa,), _ = solve_batch(rbf, [mix[b]], mixed)
+        np.testing.assert_array_equal(wa, w[ptr[b]:ptr[b + 1]])
+
+
+def test_single_solver_stops_on_stagnation(rbf):
+    p = W.lattice_problem(24, 0.6, seed=5, rhs="four_gaussians")
+    cfg = rbf.config_for(p)
+    ctx = rbf.Context(0)
+    ctx.bin(dev(p.xy), cfg)
+    ctx.rasm_setup(cfg)
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+    assert st == 6 and info.status == 6 and info.stagnated == 1, info.as_dict()
+    assert info.iters < 400
+    ctx.close()
