@@ -57,6 +57,8 @@ WORKLOADS = {
     "lattice64": (W.config_small, "64x64 jittered lattice on [-1,1]^2 (N=4,096)"),
     "lattice1024": (W.config_1m, "1024x1024 jittered lattice on [-1,1]^2 (N=1,048,576)"),
     "lattice7168": (W.config_51m, "7168x7168 jittered lattice on [-1,1]^2 (N=51,380,224)"),
+    "batch4096": (None, "independent jittered lattices on [-1,1]^2, N log-uniform in [256, 16384], "
+                        "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians, one seed per problem"),
 }
 
 
@@ -67,7 +69,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lattice1024", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--mode", default=None, choices=["f64", "mixed"],
+                    help="precision (default: f64 for one problem, mixed for the batch)")
+    ap.add_argument("--batch-count", type=int, default=4096, help="problems of the batch workload")
+    ap.add_argument("--max-iters", type=int, default=3000, help="GMRES step cap per problem (batch)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
@@ -219,7 +224,7 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     name = args.workload
     p = WORKLOADS[name][0]()
-    mode = args.mode
+    mode = args.mode or "f64"
     cfg = rbf.config_for(p, mixed=(mode == "mixed"), factor_precision=rbf.RBF_FP32 if mode == "mixed" else rbf.RBF_FP64)
     xy = torch.from_numpy(p.xy).cuda()
     f = torch.from_numpy(p.f).cuda()
@@ -361,13 +366,277 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- many-problem batch
+
+BATCH_METRIC = "RBF batch solve time at 1e-13 rel. residual (4096 independent problems, GMRES+RASM)"
+RATIO_BINS = ((0.6, 0.7), (0.7, 0.8), (0.8, 0.9), (0.9, 1.0001))
+
+
+def batch_problems(args):
+    return W.batch_workload(args.batch_count)
+
+
+def batch_config(args, probs, mode: str) -> dict:
+    ns = np.array([p.n for p in probs])
+    return {"workload": "batch4096" if args.batch_count == 4096 else f"batch{args.batch_count}",
+            "description": WORKLOADS["batch4096"][1], "problems": len(probs), "n_points_total": int(ns.sum()),
+            "n_min": int(ns.min()), "n_max": int(ns.max()), "cutoff_sigmas": 8.6,
+            "rasm": "4x4 lattice-point cores + 1-point ring", "gmres_restart": 30, "rtol": 1e-13,
+            "max_iters_per_problem": args.max_iters, "precision": mode,
+            "l2": "flushed (256 MB write) before each timed step", "parallelism": "replicas"}
+
+
+def batch_summary(probs, infos, stats_w=None) -> dict:
+    st = np.array([i.status for i in infos])
+    stg = np.array([i.stagnated for i in infos])
+    it = np.array([i.iters for i in infos])
+    rr = np.array([i.relres for i in infos])
+    ratio = np.array([p.h / p.sigma for p in probs])
+    conv = st == 0
+    bins = {}
+    for lo, hi in RATIO_BINS:
+        sel = (ratio >= lo) & (ratio < hi)
+        bins[f"{lo:.1f}-{min(hi, 1.0):.1f}"] = {"problems": int(sel.sum()), "converged": int((conv & sel).sum()),
+                                               "median_iters": float(np.median(it[sel & conv])) if (sel & conv).any()
+                                               else None}
+    return {"converged": int(conv.sum()), "stagnated": int(stg.sum()), "not_converged": int((~conv).sum()),
+            "iters_median": float(np.median(it)), "iters_p90": float(np.percentile(it, 90)), "iters_max": int(it.max()),
+            "relres_max_converged": float(rr[conv].max()) if conv.any() else None, "by_h_over_sigma": bins}
+
+
+def oracle_batch_sample(probs, budget_s: float, seed: int, w_gpu=None, ptr=None, iters=None) -> dict:
+    """The CPU oracle on a seeded sample of the batch's problems, each solved on
+    its own (setup and GMRES); problems are taken in a seeded random order until
+    the budget is spent. With the GPU's per-problem step counts, each sampled
+    solve runs that many steps and the time is projected to the whole batch by
+    N x (steps + 1); otherwise each solve runs to 1e-13 (at most 3000 steps)
+    and the projection is by N. With the GPU result, the sample also gives the
+    relative error of w against the oracle's."""
+    from oracle import oracle as O
+
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    order = np.random.default_rng(seed).permutation(len(probs))
+    t_all, used, errs = 0.0, [], []
+    for k in order:
+        p = probs[k]
+        mi = int(iters[k]) if iters is not None else 3000
+        t0 = time.perf_counter()
+        pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+        wo, inf = pr.solve(p.f, max_iters=max(mi, 1))
+        t_all += time.perf_counter() - t0
+        used.append(int(k))
+        if w_gpu is not None and inf.relres <= 1e-13:
+            wg = w_gpu[ptr[k]:ptr[k + 1]]
+            errs.append(float(np.linalg.norm(wg - wo) / np.linalg.norm(wo)))
+        if t_all >= budget_s:
+            break
+    ns = np.array([p.n for p in probs], dtype=np.float64)
+    wts = ns * (np.asarray(iters, dtype=np.float64) + 1.0) if iters is not None else ns
+    proj = t_all * wts.sum() / wts[used].sum()
+    out = {"value": proj * 1e3, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"{len(used)} of {len(probs)} problems (seeded random order) solved one by one by the oracle "
+                      f"in {t_all:.2f} s; projected to the batch by " +
+                      ("N x (GPU steps + 1)" if iters is not None else "N")),
+           "measured_s": round(t_all, 3)}
+    if errs:
+        out["w_rel_error_vs_oracle_max"] = max(errs)
+        out["w_rel_error_vs_oracle_problems"] = len(errs)
+    return out
+
+
+def run_reference_batch(args, ws, rank):
+    if rank != 0:
+        return
+    probs = batch_problems(args)
+    times, cb = [], None
+    for step in range(args.warmup + args.steps):
+        cb = oracle_batch_sample(probs, budget_s=8.0, seed=step)
+        if step >= args.warmup:
+            times.append(cb["value"])
+    v = statistics.mean(times)
+    cb["value"] = v
+    out = {"impl": "reference", "metric": BATCH_METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": batch_config(args, probs, "f64"), "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args, ws, rank, local):
+    import torch
+
+    from paper_0909_5413_gb300 import rbf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mode = args.mode or "mixed"
+    probs = batch_problems(args)
+    xy_np, f_np, ptr, params, rasm64 = rbf.batch_arrays(probs, factor_precision=rbf.RBF_FP64)
+    _, _, _, _, rasm32 = rbf.batch_arrays(probs, factor_precision=rbf.RBF_FP32)
+    ptr_c, params_c, rasm64_c = rbf.batch_ctypes(ptr, params, rasm64)
+    rasm32_c = rbf.batch_ctypes(ptr, params, rasm32)[2]
+    nprob, ntot = len(probs), ptr[-1]
+    xy = torch.from_numpy(xy_np).cuda()
+    f = torch.from_numpy(f_np).cuda()
+    w = torch.zeros(ntot, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ctx = rbf.Context(local)
+    h = ctx.handle
+
+    def sparams(md):
+        return rbf.RbfSolveParams(1e-13, 30, args.max_iters, int(md == "mixed"), args.max_iters, 1e-5)
+
+    def step(md, xy_t=xy, f_t=f, w_t=w):
+        w_t.zero_()
+        rbf.rbf_bin_batch(h, xy_t, ptr_c, params_c)
+        rbf.rbf_rasm_setup_batch(h, rasm32_c if md == "mixed" else rasm64_c)
+        return rbf.rbf_solve_batch(h, f_t, w_t, sparams(md), nprob, check=False)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        ts, last = [], None
+        for _ in range(reps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            last = fn()
+            e1.record()
+            barrier()
+            ts.append(e0.elapsed_time(e1))
+        return ts, last
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(mode)
+    torch.cuda.synchronize()
+    launches0 = ctx.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, (st, infos) = timed(lambda: step(mode), args.steps)
+    clk = clocks.stop()
+    launches = ctx.launches - launches0
+    ms = statistics.mean(times)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    summ = batch_summary(probs, infos)
+    w_host = w.cpu().numpy()
+    iters = [i.iters for i in infos]
+
+    # FP64 matvec over the whole batch (every problem active), kernel time from the profiler
+    rbf.rbf_profile_enable(h, True)
+    for k in range(6):
+        rbf.rbf_profile_read(h, k)
+    y = torch.empty_like(w)
+    for _ in range(5):
+        flush.zero_()
+        rbf.rbf_matvec(h, w, y)
+    torch.cuda.synchronize()
+    n_mv, t_mv = rbf.rbf_profile_read(h, rbf.RBF_PROF_MATVEC_F64)
+    rbf.rbf_profile_enable(h, False)
+    pairs = rbf.rbf_count_neighbors(h)
+    avg_s = t_mv / max(n_mv, 1) / 1e3
+    achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
+    roofline = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
+                "peak_measured": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
+                "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
+                "launches": n_mv, "note": "all problems of the batch in one launch"}
+
+    # the other precision, batched
+    extra = None
+    if not args.no_extra:
+        other = "f64" if mode == "mixed" else "mixed"
+        step(other)
+        ts, (st2, inf2) = timed(lambda: step(other), max(1, min(args.steps, 2)))
+        extra = {"precision": other, "ms_per_step": statistics.mean(ts), "status": st2,
+                 **batch_summary(probs, inf2)}
+
+    # the plain single-problem FP64 path, one problem at a time, on a seeded sample
+    seq = None
+    if not args.no_extra:
+        sample = np.random.default_rng(7).choice(nprob, size=min(64, nprob), replace=False)
+        sctx = rbf.Context(local)
+        tot, sts = 0.0, []
+        for k in sample:
+            p = probs[k]
+            cfg = rbf.config_for(p, max_iters=args.max_iters)
+            xs = torch.from_numpy(p.xy).cuda()
+            fs = torch.from_numpy(p.f).cuda()
+            ws_ = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+
+            def one():
+                sctx.bin(xs, cfg)
+                sctx.rasm_setup(cfg)
+                return sctx.solve(fs, ws_, cfg, check=False)
+            ts, (s1, _) = timed(one, 1)
+            tot += ts[0]
+            sts.append(s1)
+        sctx.close()
+        ns = np.array([p.n for p in probs], dtype=np.float64)
+        seq = {"precision": "f64", "sample_problems": len(sample), "sample_ms": tot,
+               "projected_ms": tot * nprob / len(sample), "sample_converged": int(sum(1 for s in sts if s == 0)),
+               "note": "single-problem solver (rbf_bin / rbf_rasm_setup / rbf_solve) per problem, "
+                       "projected to the batch by problem count"}
+
+    # end to end: pinned host inputs copied in, the three batch calls, w copied out
+    e2e = None
+    if not args.no_e2e:
+        xy_h = torch.from_numpy(xy_np.copy()).pin_memory()
+        f_h = torch.from_numpy(f_np.copy()).pin_memory()
+        w_h = torch.zeros(ntot, dtype=torch.float64).pin_memory()
+        xy_d, f_d, w_d = torch.empty_like(xy), torch.empty_like(f), torch.empty_like(w)
+
+        def e2e_step():
+            xy_d.copy_(xy_h, non_blocking=True)
+            f_d.copy_(f_h, non_blocking=True)
+            r = step(mode, xy_d, f_d, w_d)
+            w_h.copy_(w_d, non_blocking=True)
+            return r
+        e2e_step()
+        te, _ = timed(e2e_step, max(1, min(args.steps, 2)))
+        e2e = {"value": statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": (xy_h.numel() + f_h.numel()) * 8,
+               "d2h_bytes_per_step": w_h.numel() * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_batch_sample(probs, budget_s=15.0, seed=0, w_gpu=w_host, ptr=ptr, iters=iters)
+
+    if rank == 0:
+        out = {"metric": BATCH_METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64" if mode == "f64" else "f32-inner/f64-outer", "data": "synthetic",
+               "config": batch_config(args, probs, mode), "status": st, "solve": summ,
+               "problems_per_s": nprob / (ms / 1e3), "points_per_s": ntot / (ms / 1e3),
+               "step_ms": [round(t, 3) for t in times], "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clk, "other_precision": extra,
+               "one_problem_at_a_time": seq}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
+    batch = args.workload.startswith("batch")
     if args.impl == "reference":
-        run_reference(args, ws, rank)
+        (run_reference_batch if batch else run_reference)(args, ws, rank)
         return
-    run_ours(args, ws, rank, local)
+    (run_batch if batch else run_ours)(args, ws, rank, local)
 
 
 if __name__ == "__main__":

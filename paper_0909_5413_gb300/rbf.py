@@ -192,15 +192,17 @@ def rbf_interpolate_host(ctx, xy_host, f_host, w_host, n: int, params: RbfParams
     return st, info
 
 
-def rbf_bin_batch(ctx, xy_dev, ptr: list[int], params: list[RbfParams], stream=None) -> None:
+def rbf_bin_batch(ctx, xy_dev, ptr, params, stream=None) -> None:
+    """``ptr`` (nprob + 1 offsets) and ``params`` may be lists or ctypes arrays
+    (``batch_ctypes``); arrays are passed without copying."""
     nprob = len(params)
-    p = (C.c_int64 * (nprob + 1))(*[int(v) for v in ptr])
-    pa = (RbfParams * nprob)(*params)
+    p = ptr if isinstance(ptr, C.Array) else (C.c_int64 * (nprob + 1))(*[int(v) for v in ptr])
+    pa = params if isinstance(params, C.Array) else (RbfParams * nprob)(*params)
     _check(ctx, load().rbf_bin_batch(ctx, _ptr(xy_dev), p, nprob, pa, _stream(stream)))
 
 
-def rbf_rasm_setup_batch(ctx, params: list[RbfRasmParams], stream=None) -> None:
-    pa = (RbfRasmParams * len(params))(*params)
+def rbf_rasm_setup_batch(ctx, params, stream=None) -> None:
+    pa = params if isinstance(params, C.Array) else (RbfRasmParams * len(params))(*params)
     _check(ctx, load().rbf_rasm_setup_batch(ctx, pa, _stream(stream)))
 
 
@@ -363,6 +365,12 @@ def batch_arrays(problems, cell_size: float = 0.0, factor_precision: int = RBF_F
     params = [RbfParams(p.sigma, p.cutoff, cell_size, 0) for p in problems]
     rasm = [RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, max_sub_points, factor_precision) for p in problems]
     return xy, f, ptr, params, rasm
+
+
+def batch_ctypes(ptr, params, rasm):
+    """The per-problem tables of ``batch_arrays`` as ctypes arrays, built once."""
+    n = len(params)
+    return ((C.c_int64 * (n + 1))(*[int(v) for v in ptr]), (RbfParams * n)(*params), (RbfRasmParams * n)(*rasm))
 
 
 def config_for(problem, **kw) -> SolverConfig:
