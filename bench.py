@@ -59,6 +59,8 @@ WORKLOADS = {
     "lattice7168": (W.config_51m, "7168x7168 jittered lattice on [-1,1]^2 (N=51,380,224)"),
     "batch4096": (None, "independent jittered lattices on [-1,1]^2, N log-uniform in [256, 16384], "
                         "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians, one seed per problem"),
+    "serve": (None, "requests with Poisson arrivals, N log-uniform in [1e3, 4e6] (jittered lattices on [-1,1]^2), "
+                    "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians"),
 }
 
 
@@ -72,7 +74,10 @@ def parse():
     ap.add_argument("--mode", default=None, choices=["f64", "mixed"],
                     help="precision (default: f64 for one problem, mixed for the batch)")
     ap.add_argument("--batch-count", type=int, default=4096, help="problems of the batch workload")
-    ap.add_argument("--max-iters", type=int, default=3000, help="GMRES step cap per problem (batch)")
+    ap.add_argument("--max-iters", type=int, default=3000, help="GMRES step cap per problem (batch, serve)")
+    ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
+    ap.add_argument("--slots", type=int, default=8, help="server slots (serve)")
+    ap.add_argument("--rates", default="0.5,0.9", help="arrival rates swept, as fractions of the saturated rate")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
@@ -404,14 +409,16 @@ def batch_summary(probs, infos, stats_w=None) -> dict:
             "relres_max_converged": float(rr[conv].max()) if conv.any() else None, "by_h_over_sigma": bins}
 
 
-def oracle_batch_sample(probs, budget_s: float, seed: int, w_gpu=None, ptr=None, iters=None) -> dict:
+def oracle_batch_sample(probs, budget_s: float, seed: int, w_gpu=None, ptr=None, iters=None,
+                        max_n: int | None = None) -> dict:
     """The CPU oracle on a seeded sample of the batch's problems, each solved on
     its own (setup and GMRES); problems are taken in a seeded random order until
     the budget is spent. With the GPU's per-problem step counts, each sampled
     solve runs that many steps and the time is projected to the whole batch by
     N x (steps + 1); otherwise each solve runs to 1e-13 (at most 3000 steps)
     and the projection is by N. With the GPU result, the sample also gives the
-    relative error of w against the oracle's."""
+    relative error of w against the oracle's. Problems above max_n points are
+    left out of the sample (the projection still covers them)."""
     from oracle import oracle as O
 
     threads = os.cpu_count() or 1
@@ -420,6 +427,8 @@ def oracle_batch_sample(probs, budget_s: float, seed: int, w_gpu=None, ptr=None,
     t_all, used, errs = 0.0, [], []
     for k in order:
         p = probs[k]
+        if max_n is not None and p.n > max_n:
+            continue
         mi = int(iters[k]) if iters is not None else 3000
         t0 = time.perf_counter()
         pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
@@ -436,7 +445,8 @@ def oracle_batch_sample(probs, budget_s: float, seed: int, w_gpu=None, ptr=None,
     proj = t_all * wts.sum() / wts[used].sum()
     out = {"value": proj * 1e3, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": (f"{len(used)} of {len(probs)} problems (seeded random order) solved one by one by the oracle "
-                      f"in {t_all:.2f} s; projected to the batch by " +
+                      f"in {t_all:.2f} s" + (f" (problems of N <= {max_n} only)" if max_n else "") +
+                      "; projected to all problems by " +
                       ("N x (GPU steps + 1)" if iters is not None else "N")),
            "measured_s": round(t_all, 3)}
     if errs:
@@ -629,14 +639,189 @@ def run_batch(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ serving
+
+SERVE_METRIC = "RBF serve latency p50 at 1e-13 rel. residual (Poisson arrivals, mixed precision)"
+
+
+def serve_problems(args):
+    return W.batch_workload(args.requests, lo=1000, hi=4_000_000, seed=W.DEFAULT_SEED + 5000)
+
+
+def serve_config(args, probs) -> dict:
+    ns = np.array([p.n for p in probs])
+    return {"workload": "serve", "description": WORKLOADS["serve"][1], "requests": len(probs),
+            "n_points_total": int(ns.sum()), "n_min": int(ns.min()), "n_max": int(ns.max()),
+            "cutoff_sigmas": 8.6, "rasm": "4x4 lattice-point cores + 1-point ring (FP32 inverses)",
+            "gmres_restart": 30, "rtol": 1e-13, "max_iters_per_request": args.max_iters,
+            "precision": "mixed", "slots": args.slots, "rates": args.rates,
+            "l2": "inputs (2.4-96 MB per request, 1.5 GB per sweep) far above L2", "parallelism": "replicas"}
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_reference_serve(args, ws, rank):
+    if rank != 0:
+        return
+    probs = serve_problems(args)
+    times, cb = [], None
+    for step in range(args.warmup + args.steps):
+        cb = oracle_batch_sample(probs, budget_s=8.0, seed=step, max_n=300_000)
+        if step >= args.warmup:
+            times.append(cb["value"] / len(probs))
+    v = statistics.mean(times)
+    cb["value"] = v
+    cb["sample"] += "; value is the projected oracle time per request (one request at a time)"
+    out = {"impl": "reference", "metric": SERVE_METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": serve_config(args, probs), "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args, ws, rank, local):
+    import torch
+
+    from paper_0909_5413_gb300 import rbf
+
+    torch.cuda.set_device(local)
+    probs = serve_problems(args)
+    R = len(probs)
+    # pinned host buffers, as a serving front end would hold them
+    host = []
+    for p in probs:
+        xy = torch.from_numpy(p.xy.copy()).pin_memory().numpy()
+        f = torch.from_numpy(p.f.copy()).pin_memory().numpy()
+        w = torch.zeros(p.n, dtype=torch.float64).pin_memory().numpy()
+        cfg = rbf.config_for(p, mixed=True, factor_precision=rbf.RBF_FP32, max_iters=args.max_iters,
+                             max_refine=args.max_iters)
+        host.append((xy, f, w, cfg))
+    srv = rbf.Server(local, slots=args.slots)
+
+    def submit(k):
+        xy, f, w, cfg = host[k]
+        return srv.submit(xy, f, cfg, w=w)
+
+    def collect(tickets):
+        out = {}
+        for k, t in tickets.items():
+            st, r, _ = srv.wait(t)
+            out[k] = r
+        return out
+
+    # warm-up: every slot grows its resident buffers on the largest request
+    big = int(np.argmax([p.n for p in probs]))
+    for _ in range(max(1, args.warmup)):
+        collect({j: submit(big) for j in range(args.slots)})
+
+    # saturated: everything submitted at once
+    clocks = ClockSampler(local)
+    clocks.start()
+    s0 = srv.stats()
+    t0 = srv.clock()
+    res = collect({k: submit(k) for k in range(R)})
+    t1 = max(r.t_done for r in res.values())
+    sat = {"rate_per_s": None, "makespan_s": t1 - t0, "throughput_per_s": R / (t1 - t0),
+           "p50_ms": pct([(r.t_done - r.t_submit) * 1e3 for r in res.values()], 50),
+           "p99_ms": pct([(r.t_done - r.t_submit) * 1e3 for r in res.values()], 99)}
+    thr = sat["throughput_per_s"]
+    rows = []
+    rng = np.random.default_rng(11)
+    for frac in [float(x) for x in args.rates.split(",") if x.strip()]:
+        lam = frac * thr
+        gaps = rng.exponential(1.0 / lam, size=R)
+        order = rng.permutation(R)
+        tickets = {}
+        start = srv.clock()
+        at = start
+        for k, g in zip(order, gaps):
+            at += g
+            while srv.clock() < at:
+                time.sleep(min(0.002, max(0.0, at - srv.clock())))
+            tickets[int(k)] = submit(int(k))
+        rr = collect(tickets)
+        lat = [(r.t_done - r.t_submit) * 1e3 for r in rr.values()]
+        qd = [(r.t_admit - r.t_submit) * 1e3 for r in rr.values()]
+        end = max(r.t_done for r in rr.values())
+        rows.append({"rate_frac": frac, "rate_per_s": lam, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                     "mean_ms": float(np.mean(lat)), "queue_p50_ms": pct(qd, 50), "queue_p99_ms": pct(qd, 99),
+                     "throughput_per_s": R / (end - start),
+                     "converged": int(sum(1 for r in rr.values() if r.status == 0))})
+    clk = clocks.stop()
+    s1 = srv.stats()
+    launches = s1["launches"] - s0["launches"]
+    conv = [r for r in res.values() if r.status == 0]
+    summ = {"converged": len(conv), "stagnated": int(sum(1 for r in res.values() if r.info.stagnated)),
+            "not_converged": R - len(conv),
+            "relres_max_converged": max((r.info.relres for r in conv), default=None),
+            "iters_median": pct([r.info.iters for r in res.values()], 50),
+            "peak_resident_gb": s1["peak_resident_bytes"] / 1e9, "mem_budget_gb": s1["mem_budget"] / 1e9,
+            "trims": s1["trims"]}
+    iters = [res[k].info.iters for k in range(R)]
+    w_all = np.concatenate([host[k][2] for k in range(R)])
+    ptr = np.concatenate([[0], np.cumsum([p.n for p in probs])])
+    srv.close()
+
+    # FP64 matvec roofline on the largest request (whole problem in one launch)
+    roofline = matvec_roofline(rbf, probs[big], local)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = oracle_batch_sample(probs, budget_s=15.0, seed=0, w_gpu=w_all, ptr=ptr, iters=iters, max_n=300_000)
+        cpu["value"] /= R
+        cpu["sample"] += "; value is the projected oracle time per request (one request at a time)"
+    main = rows[0] if rows else sat
+    h2d = float(np.mean([p.n * 24 for p in probs]))
+    out = {"metric": SERVE_METRIC, "value": main["p50_ms"], "unit": UNIT, "n_gpus": ws, "steps": R,
+           "warmup": args.warmup, "ms_per_step": main["mean_ms"] if rows else None, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-outer", "data": "synthetic",
+           "config": serve_config(args, probs), "p99_ms": main["p99_ms"], "rates": rows, "saturated": sat,
+           "solve": summ, "roofline": roofline, "cpu_baseline": cpu,
+           "e2e": {"value": main["p50_ms"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d / 3,
+                   "note": "the serving path is host to host: pinned inputs in, w out, per request"},
+           "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def matvec_roofline(rbf, p, local) -> dict:
+    import torch
+    ctx = rbf.Context(local)
+    cfg = rbf.config_for(p)
+    ctx.bin(torch.from_numpy(p.xy).cuda(), cfg)
+    w = torch.from_numpy(p.f).cuda()
+    y = torch.empty_like(w)
+    h = ctx.handle
+    rbf.rbf_matvec(h, w, y)
+    torch.cuda.synchronize()
+    rbf.rbf_profile_enable(h, True)
+    for _ in range(5):
+        rbf.rbf_matvec(h, w, y)
+    torch.cuda.synchronize()
+    n_mv, t_mv = rbf.rbf_profile_read(h, rbf.RBF_PROF_MATVEC_F64)
+    pairs = rbf.rbf_count_neighbors(h)
+    ctx.close()
+    avg_s = t_mv / max(n_mv, 1) / 1e3
+    achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
+    return {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
+            "peak_measured": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
+            "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
+            "launches": n_mv, "note": f"largest request, N={p.n}"}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
-    batch = args.workload.startswith("batch")
+    kind = "batch" if args.workload.startswith("batch") else ("serve" if args.workload == "serve" else "one")
     if args.impl == "reference":
-        (run_reference_batch if batch else run_reference)(args, ws, rank)
+        {"batch": run_reference_batch, "serve": run_reference_serve, "one": run_reference}[kind](args, ws, rank)
         return
-    (run_batch if batch else run_ours)(args, ws, rank, local)
+    {"batch": run_batch, "serve": run_serve, "one": run_ours}[kind](args, ws, rank, local)
 
 
 if __name__ == "__main__":

@@ -175,10 +175,84 @@ rbf_status rbf_bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* ptr_
 rbf_status rbf_rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params_host, rbf_stream stream);
 /* Solve every problem of the batch (f_dev, w_dev: concatenated, user order; w
  * holds the initial guesses). info_host (nprob entries, optional) receives each
- * problem's iterations and final true relative residual. Returns
- * NOT_CONVERGED if any problem misses rtol within max_iters steps. */
+ * problem's iterations, final true relative residual and status. A problem
+ * stops on its own when it meets rtol, reaches max_iters, or stagnates (as in
+ * rbf_solve); the others go on. Returns NOT_CONVERGED if any problem misses
+ * rtol. The Arnoldi cycle is replayed as a CUDA graph on an internal stream
+ * that is ordered after `stream` on entry; the call returns when the solve is
+ * complete. */
 rbf_status rbf_solve_batch(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* params,
                            rbf_solve_info* info_host, rbf_stream stream);
+
+/* ---- serving: independent requests admitted while others run ----
+ *
+ * No counterpart in the paper (its runs solve one problem per job); this is the
+ * serving form of the same solve. A server owns `slots` contexts, each with its
+ * own non-blocking stream and resident device buffers (points, lists, factors,
+ * Krylov basis) that are reused from request to request. A submitted request
+ * waits in a FIFO queue until a slot is free and its estimated device
+ * footprint fits in the memory budget together with what the other slots hold;
+ * a later, smaller request may go ahead of a head that does not fit (at most
+ * `slots` times in a row). Admitted requests run concurrently, each on its own
+ * stream: bin, RASM setup and GMRES solve, exactly as rbf_interpolate_host, so
+ * a request's result does not depend on the others in flight. */
+typedef struct rbf_server rbf_server;
+
+typedef struct {
+    int device;
+    int slots;            /* requests in flight at once, 1..64 */
+    int64_t mem_budget;   /* device bytes all slots may hold together; 0 = 90% of the free memory */
+} rbf_server_params;
+
+typedef struct {
+    const double* xy;     /* host, n x 2 interleaved (x, y), user order; read until the request completes */
+    const double* f;      /* host, n */
+    double* w;            /* host, n; written when the request completes */
+    int64_t n;
+    rbf_params kernel;
+    rbf_rasm_params rasm;
+    rbf_solve_params solve;
+} rbf_request;
+
+typedef struct {
+    rbf_solve_info info;
+    int status;           /* rbf_status of the request (NOT_CONVERGED keeps the last iterate in w) */
+    int slot;             /* slot that ran it */
+    double t_submit;      /* seconds on the server's clock (rbf_server_clock) */
+    double t_admit;
+    double t_done;
+    int64_t footprint;    /* estimated device bytes charged at admission */
+} rbf_request_result;
+
+typedef struct {
+    int64_t submitted, completed, queued, running;
+    int64_t resident_bytes;   /* device bytes the slots hold now */
+    int64_t mem_budget;
+    int64_t peak_resident_bytes;
+    int64_t trims;            /* idle slots that released their buffers to admit a request */
+    int64_t launches;         /* kernels launched by completed requests */
+} rbf_server_stats;
+
+/* Create a server (contexts are created lazily, on first use of a slot).
+ * INVALID_ARG for slots outside 1..64 or a negative budget. */
+rbf_status rbf_server_create(rbf_server** out, const rbf_server_params* params);
+/* Finish the admitted requests, fail the queued ones (status STATE), free everything. */
+void rbf_server_destroy(rbf_server* server);
+/* Queue a request (host call, returns at once) and give its ticket. The caller
+ * keeps req->xy, f and w alive until rbf_server_wait returns for it. OOM when
+ * the request alone exceeds the budget; INVALID_ARG for null buffers or n < 1. */
+rbf_status rbf_server_submit(rbf_server* server, const rbf_request* req, int64_t* ticket);
+/* Wait up to timeout_s seconds (< 0: no limit) for a ticket; TIMEOUT if it has
+ * not completed, INVALID_ARG for an unknown ticket. On success the result is
+ * copied out and the ticket is forgotten. */
+rbf_status rbf_server_wait(rbf_server* server, int64_t ticket, double timeout_s, rbf_request_result* result);
+rbf_status rbf_server_get_stats(rbf_server* server, rbf_server_stats* stats);
+/* Seconds since the server was created (steady clock). */
+double rbf_server_clock(rbf_server* server);
+/* Estimated device bytes of a request (host only, no GPU): staging, sorted
+ * points, lists, RASM factors of the requested precision and the Krylov basis
+ * (FP64, or FP32 for the mixed form); reads req->xy for the bounding box. */
+int64_t rbf_request_footprint(const rbf_request* req);
 
 /* ---- parity / inspection getters (synchronous; device outputs caller-owned) ---- */
 

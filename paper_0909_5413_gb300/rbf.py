@@ -26,7 +26,9 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_interpolate_host", "rbf_get_grid", "rbf_get_bins", "rbf_get_subdomain_sizes", "rbf_get_subdomains",
             "rbf_count_neighbors", "rbf_get_neighbors", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
             "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
-            "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch"]
+            "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
+            "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
+            "rbf_request_footprint"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -50,6 +52,29 @@ class RbfSolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("refinements", C.c_int), ("relres", C.c_double),
                 ("relres_est", C.c_double), ("matvecs", C.c_int), ("applies", C.c_int), ("status", C.c_int),
                 ("stagnated", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RbfServerParams(C.Structure):
+    _fields_ = [("device", C.c_int), ("slots", C.c_int), ("mem_budget", C.c_int64)]
+
+
+class RbfRequest(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("f", C.c_void_p), ("w", C.c_void_p), ("n", C.c_int64),
+                ("kernel", RbfParams), ("rasm", RbfRasmParams), ("solve", RbfSolveParams)]
+
+
+class RbfRequestResult(C.Structure):
+    _fields_ = [("info", RbfSolveInfo), ("status", C.c_int), ("slot", C.c_int), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("footprint", C.c_int64)]
+
+
+class RbfServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("resident_bytes", C.c_int64), ("mem_budget", C.c_int64), ("peak_resident_bytes", C.c_int64),
+                ("trims", C.c_int64), ("launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -105,9 +130,19 @@ def load(path: str | None = None):
     L.rbf_bin_batch.argtypes = [P, P, I64, C.c_int64, C.POINTER(RbfParams), P]
     L.rbf_rasm_setup_batch.argtypes = [P, C.POINTER(RbfRasmParams), P]
     L.rbf_solve_batch.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
+    L.rbf_server_create.argtypes = [C.POINTER(P), C.POINTER(RbfServerParams)]
+    L.rbf_server_destroy.argtypes = [P]
+    L.rbf_server_destroy.restype = None
+    L.rbf_server_submit.argtypes = [P, C.POINTER(RbfRequest), I64]
+    L.rbf_server_wait.argtypes = [P, C.c_int64, C.c_double, C.POINTER(RbfRequestResult)]
+    L.rbf_server_get_stats.argtypes = [P, C.POINTER(RbfServerStats)]
+    L.rbf_server_clock.argtypes = [P]
+    L.rbf_server_clock.restype = C.c_double
+    L.rbf_request_footprint.argtypes = [C.POINTER(RbfRequest)]
+    L.rbf_request_footprint.restype = C.c_int64
     for name in EXPORTED:
         if name not in ("rbf_destroy", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
-                        "rbf_device_bytes"):
+                        "rbf_device_bytes", "rbf_server_destroy", "rbf_server_clock", "rbf_request_footprint"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -377,3 +412,100 @@ def config_for(problem, **kw) -> SolverConfig:
     """SolverConfig from a ``workloads.Problem``."""
     return SolverConfig(sigma=problem.sigma, cutoff=problem.cutoff, x0=problem.x0, y0=problem.x0,
                         core_size=problem.core_size, overlap=problem.overlap, **kw)
+
+
+# ---------------------------------------------------------------- serving
+
+def rbf_server_create(device: int = 0, slots: int = 4, mem_budget: int = 0):
+    h = C.c_void_p()
+    p = RbfServerParams(device, slots, mem_budget)
+    st = load().rbf_server_create(C.byref(h), C.byref(p))
+    if st != 0:
+        raise RbfError(st, "rbf_server_create")
+    return h
+
+
+def rbf_server_destroy(server) -> None:
+    load().rbf_server_destroy(server)
+
+
+def rbf_server_submit(server, req: RbfRequest) -> int:
+    t = C.c_int64()
+    st = load().rbf_server_submit(server, C.byref(req), C.byref(t))
+    if st != 0:
+        raise RbfError(st, "rbf_server_submit")
+    return t.value
+
+
+def rbf_server_wait(server, ticket: int, timeout_s: float = -1.0) -> tuple[int, RbfRequestResult]:
+    r = RbfRequestResult()
+    st = load().rbf_server_wait(server, int(ticket), float(timeout_s), C.byref(r))
+    return st, r
+
+
+def rbf_server_get_stats(server) -> RbfServerStats:
+    s = RbfServerStats()
+    st = load().rbf_server_get_stats(server, C.byref(s))
+    if st != 0:
+        raise RbfError(st, "rbf_server_get_stats")
+    return s
+
+
+def rbf_server_clock(server) -> float:
+    return float(load().rbf_server_clock(server))
+
+
+def rbf_request_footprint(req: RbfRequest) -> int:
+    return int(load().rbf_request_footprint(C.byref(req)))
+
+
+def make_request(xy, f, w, cfg: SolverConfig) -> RbfRequest:
+    """Request over host arrays (C-contiguous float64 numpy arrays; xy (n, 2))."""
+    n = int(f.shape[0])
+    return RbfRequest(_ptr(xy), _ptr(f), _ptr(w), n, cfg.params(), cfg.rasm(), cfg.solve())
+
+
+class Server:
+    """Owns one ``rbf_server``; keeps each request's host arrays alive until
+    its result has been collected."""
+
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0):
+        self.handle = rbf_server_create(device, slots, mem_budget)
+        self._live: dict[int, tuple] = {}
+
+    def submit(self, xy, f, cfg: SolverConfig, w=None) -> int:
+        import numpy as np
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if w is None:
+            w = np.zeros(f.shape[0], dtype=np.float64)
+        req = make_request(xy, f, w, cfg)
+        t = rbf_server_submit(self.handle, req)
+        self._live[t] = (xy, f, w)
+        return t
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """(status of the wait, RbfRequestResult, w) -- w is None on a timeout."""
+        st, r = rbf_server_wait(self.handle, ticket, timeout_s)
+        if st != 0:
+            return st, r, None
+        _, _, w = self._live.pop(ticket)
+        return st, r, w
+
+    def stats(self) -> dict:
+        return rbf_server_get_stats(self.handle).as_dict()
+
+    def clock(self) -> float:
+        return rbf_server_clock(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            rbf_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -53,3 +53,41 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert lib.rbf_bin(None, None, 10, C.byref(p), None) == 1
     assert lib.rbf_launch_count(None) == 0
     assert lib.rbf_last_error(None) == b"null context"
+
+
+def test_server_rejects_bad_parameters_without_gpu(lib):
+    from paper_0909_5413_gb300 import rbf
+    h = C.c_void_p()
+    for slots in (0, 65):
+        p = rbf.RbfServerParams(0, slots, 0)
+        assert lib.rbf_server_create(C.byref(h), C.byref(p)) == 1
+    p = rbf.RbfServerParams(0, 2, -5)
+    assert lib.rbf_server_create(C.byref(h), C.byref(p)) == 1
+    assert lib.rbf_server_submit(None, None, None) == 1
+    assert lib.rbf_server_clock(None) == 0.0
+
+
+def test_request_footprint_estimate(lib):
+    """The admission estimate (host only): grows in proportion to N, and the
+    mixed form with FP32 inverses needs about half the bytes of the FP64 form."""
+    import numpy as np
+    from paper_0909_5413_gb300 import rbf
+    from paper_0909_5413_gb300 import workloads as W
+
+    def fp(n_side, mixed):
+        p = W.lattice_problem(n_side, 0.8, seed=1)
+        cfg = rbf.config_for(p, mixed=mixed, factor_precision=rbf.RBF_FP32 if mixed else rbf.RBF_FP64)
+        w = np.zeros(p.n)
+        return rbf.rbf_request_footprint(rbf.make_request(p.xy, p.f, w, cfg)), p.n
+
+    f64_small, n_small = fp(64, False)
+    f64_big, n_big = fp(256, False)
+    mix_big, _ = fp(256, True)
+    fixed = 16 << 20
+    per_small = (f64_small - fixed) / n_small
+    per_big = (f64_big - fixed) / n_big
+    assert abs(per_small - per_big) / per_big < 0.05
+    # FP64: staging, lists, 31 Krylov vectors (248 B) and 36 FP64 inverse entries per point (288 B)
+    assert 600 < per_big < 800
+    assert 0.4 < (mix_big - fixed) / (f64_big - fixed) < 0.65
+    assert rbf.rbf_request_footprint(rbf.RbfRequest()) == 0
