@@ -295,6 +295,13 @@ rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable);
  * the number of recorded launches and their summed device time; clears that
  * class's record. */
 rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double* total_ms);
+/* Kernel values exp(-|x_i - x_j|^2 / (2 sigma^2)) of n point pairs, pairs_dev
+ * holding (x_i, y_i, x_j, y_j) per pair (device, FP64), computed by the FP64
+ * matvec's fixed-point evaluation with the constants of the binned problem
+ * (problem 0 of a batch); 0 for pairs beyond the cutoff (Sec. 2.3 kernel,
+ * without the normalisation factor). STATE before rbf_bin. */
+rbf_status rbf_debug_kernel_pairs(rbf_ctx* ctx, const double* pairs_dev, double* out_dev, int64_t n,
+                                  rbf_stream stream);
 /* out[i] = exp(-t[i]) for n FP64 values on the device: variant 0 is the
  * library's table-driven exp with 64 entries (subdomain setup), variant 2 the
  * 2048-entry one of the FP64 matvec, variant 1 CUDA's exp(); for accuracy

@@ -10,6 +10,7 @@
 // floating-point step uses explicit round-to-nearest intrinsics (no
 // contraction), so the cell of each point is the IEEE result of that
 // expression.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -321,6 +322,12 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
         q.ncx = (int64_t)fx + 1;
         q.ncy = (int64_t)fy + 1;
         q.cellbase = ncell;
+        const double amax = std::max(std::max(std::fabs(q.xmin), std::fabs(q.xmax)),
+                                     std::max(std::fabs(q.ymin), std::fabs(q.ymax)));
+        if (!make_fx_constants(amax, q.rc, q.s, &q.fx_scale, &q.fx_sh, &q.fx_F, &q.fx_M))
+            return fail(ctx, RBF_ERR_INVALID_ARG,
+                        "rbf_bin: cutoff %g out of range for the coordinates (max |x| %g) or for sigma (problem %d)",
+                        q.rc, amax, b);
         ncell += q.ncx * q.ncy;
         if (ncell > ((int64_t)1 << 28))
             return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: %lld cells exceed 2^28 (cell_size too small)",

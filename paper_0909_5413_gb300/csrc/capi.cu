@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" entry points declared in include/rbf.h, plus the
 // context's allocation and error bookkeeping.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -71,6 +72,7 @@ template rbf_status ensure<double>(rbf_ctx*, DevArray<double>&, size_t);
 template rbf_status ensure<float>(rbf_ctx*, DevArray<float>&, size_t);
 template rbf_status ensure<GmresDev>(rbf_ctx*, DevArray<GmresDev>&, size_t);
 template rbf_status ensure<Prob>(rbf_ctx*, DevArray<Prob>&, size_t);
+template rbf_status ensure<unsigned long long>(rbf_ctx*, DevArray<unsigned long long>&, size_t);
 
 constexpr int64_t kMaxProfPairs = 1 << 16;
 
@@ -124,7 +126,58 @@ void make_exp2048(double* tab, double* c)
     c[2] = (double)(c1 * c1 * c1 / 6.0L);
 }
 
+void make_fx_tables(unsigned long long* t1, unsigned long long* t2)
+{
+    for (int i = 0; i < kFxTab; ++i) {
+        t1[i] = (unsigned long long)(exp2l(-(long double)i / 1024.0L) * 0x1p63L + 0.5L);
+        t2[i] = (unsigned long long)(exp2l(-(long double)i / 1048576.0L) * 0x1p63L + 0.5L);
+    }
+}
+
+bool make_fx_constants(double amax, double rc, double s, double* scale, int* sh, int* F, unsigned long long* M)
+{
+    const double a = std::max(amax, rc);
+    if (!(a > 0.0) || !std::isfinite(a) || !(s > 0.0) || !std::isfinite(s)) return false;
+    int e = 0;
+    std::frexp(a, &e);                       // a < 2^e
+    const int S = 62 - e;                    // |x| 2^S < 2^62
+    if (S < -1000 || S > 1000) return false;
+    int eR = 0;
+    std::frexp(std::ldexp(rc, S), &eR);      // R = r_c 2^S < 2^eR
+    if (eR < 31 || eR > 62) return false;    // r_c below 2^-32 max|x|: too few bits for the offsets
+    const int shift = 63 - eR;               // |dx| 2^sh < 2^63 (1 + 2^-50) for r2 <= r_c^2
+    const long double g = (long double)s * 1.442695040888963407359924681001892137L;   // s log2(e)
+    int ge = 0;
+    const long double gm = std::frexp(g, &ge);                  // g = gm 2^ge, gm in [0.5, 1)
+    const int f = 2 * S + 2 * shift - 64 - ge;                  // makes M = gm 2^64 in [2^63, 2^64); z < 2^62
+    if (f < 21 || f > 63) return false;
+    *scale = std::ldexp(1.0, S);
+    *sh = shift;
+    *F = f;
+    *M = (unsigned long long)std::ldexp(gm, 64);
+    return true;
+}
+
 namespace {
+
+// Kernel values of point pairs (x_i, y_i, x_j, y_j) by the matvec's fixed-point
+// evaluation with problem 0's constants; 0 beyond the cutoff.
+__global__ void k_debug_kernel_pairs(const double* __restrict__ pr4, double* __restrict__ out, int64_t n,
+                                     const Prob* __restrict__ prob, const unsigned long long* __restrict__ tab)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Prob& q = prob[0];
+    const double xi = pr4[4 * i], yi = pr4[4 * i + 1], xj = pr4[4 * i + 2], yj = pr4[4 * i + 3];
+    const double ex = __dsub_rn(xi, xj), ey = __dsub_rn(yi, yj);
+    if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) > q.rc2) {
+        out[i] = 0.0;
+        return;
+    }
+    const long long dx = __double2ll_rn(xi * q.fx_scale) - __double2ll_rn(xj * q.fx_scale);
+    const long long dy = __double2ll_rn(yi * q.fx_scale) - __double2ll_rn(yj * q.fx_scale);
+    out[i] = kernel_fx(dx, dy, q.fx_sh, q.fx_F, q.fx_M, tab, tab + kFxTab);
+}
 
 __global__ void k_debug_exp(const double* __restrict__ t, double* __restrict__ out, int64_t n, int variant,
                             ExpConsts ec, const double* __restrict__ tab2048, double c1, double c2, double c3)
@@ -198,6 +251,14 @@ rbf_status rbf_create(rbf_ctx** out, int device)
     make_exp2048(tab.data(), ctx->exp2048_c);
     if (ensure(ctx, ctx->exp2048, kExpTab2048) != RBF_OK ||
         cudaMemcpy(ctx->exp2048.p, tab.data(), sizeof(double) * kExpTab2048, cudaMemcpyHostToDevice) != cudaSuccess) {
+        rbf_destroy(ctx);
+        return RBF_ERR_OOM;
+    }
+    std::vector<unsigned long long> fx(2 * kFxTab);
+    make_fx_tables(fx.data(), fx.data() + kFxTab);
+    if (ensure(ctx, ctx->fxtab, 2 * kFxTab) != RBF_OK ||
+        cudaMemcpy(ctx->fxtab.p, fx.data(), sizeof(unsigned long long) * 2 * kFxTab, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
         rbf_destroy(ctx);
         return RBF_ERR_OOM;
     }
@@ -573,6 +634,20 @@ rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double*
     if (launches) *launches = s.used;
     if (total_ms) *total_ms = tot;
     s.used = 0;
+    return RBF_OK;
+}
+
+rbf_status rbf_debug_kernel_pairs(rbf_ctx* ctx, const double* pairs_dev, double* out_dev, int64_t n,
+                                  rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_debug_kernel_pairs: call rbf_bin first");
+    if (n < 0 || (n > 0 && (!pairs_dev || !out_dev)))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_debug_kernel_pairs: bad buffers");
+    if (n == 0) return RBF_OK;
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_LAUNCH(ctx, k_debug_kernel_pairs, blocks_for(n, 256), 256, 0, S(stream), pairs_dev, out_dev, n,
+               ctx->prob.p, ctx->fxtab.p);
     return RBF_OK;
 }
 

@@ -10,6 +10,7 @@
 
 #include "../../include/rbf.h"
 #include "exp64.cuh"
+#include "fixexp.cuh"
 
 namespace rbf {
 
@@ -57,6 +58,10 @@ struct Prob {
     int k;                                // stencil half-width ceil(rc / c)
     float a_loc;                          // FP32 offset scale sqrt(log2(e) s)
     float ca, rc2f_lo, rc2f_hi;           // c * a_loc; FP32 accept / exact-test band around rc2 a_loc^2
+    // fixed-point kernel evaluation (fixexp.cuh)
+    double fx_scale;                      // 2^S: coordinate -> int64
+    unsigned long long fx_M;
+    int fx_sh, fx_F;
     // subdomain boxes
     double x0, y0, B, delta;
     int64_t nbx, nby, subbase;
@@ -106,6 +111,7 @@ struct rbf_ctx {
     rbf::DevArray<int32_t> mv_work, mv_wcnt, mv_woff;   // matvec work items (cell, first target) and their scan
     int64_t n_work = 0;
     rbf::DevArray<double> exp2048; // 2^(-j/2048), j < 2048
+    rbf::DevArray<unsigned long long> fxtab;   // T1 (1024) then T2 (1024), Q1.63
     double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)

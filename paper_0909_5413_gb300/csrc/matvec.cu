@@ -4,15 +4,18 @@
 // exp(-r2_ij / (2 sigma^2)) w_j. Each stencil row is one contiguous range of
 // cell-ordered sources, read straight from HBM/L2 (no ghost exchange on one GPU).
 //
-// FP64 kernel (GB300 runs FP64 at 1/73 of the FP32 rate, so FP64 issue slots
-// are the resource to save): one block per (cell, 128 targets); the stencil's
-// sources are staged in shared memory; each target first tests every candidate
-// in FP32 on scaled cell-local offsets (a thin band around the cutoff is
-// re-tested exactly in FP64, with the same IEEE operations as the index-list
-// definition) and keeps a bitmask of accepted sources; then the warp walks the
-// accepted sources of each lane in lockstep, so FP64 instructions are issued
-// only for accepted pairs: 2 SUB + MUL + FMA for r2 and 7 for the exp, plus
-// the accumulate FMA (12 per pair).
+// FP64 kernel. GB300 issues FP64 at 1/73 of the FP32 rate, so the pair's
+// kernel value is computed on the integer pipes (fixexp.cuh: exact
+// fixed-point offsets, table-driven exp in 64-bit fixed point, FP64 bits
+// assembled at the end) and the FP64 pipe only does the accumulate FMA. One
+// block per (cell, 128 targets) with four warps per target set: the stencil's
+// sources are staged in shared memory and split by 32-source word among the
+// four quarters (word w goes to quarter w mod 4); each target tests its
+// candidates in FP32 on scaled cell-local offsets (a thin band around the
+// cutoff is re-tested exactly in FP64 with the same IEEE operations as the
+// index-list definition) and keeps a bitmask of accepted sources; each warp
+// then walks its lanes' accepted sources in lockstep. The four partial sums of
+// a target are added in quarter order (deterministic).
 #include <cmath>
 
 #include "common.cuh"
@@ -20,9 +23,11 @@
 namespace rbf {
 namespace {
 
-constexpr int kMvThreads = 128;
+constexpr int kMvThreads = 128;                // targets per block (FP32 kernel: threads per block)
+constexpr int kMvQ = 4;                        // source quarters of the FP64 kernel
+constexpr int kMv64Threads = kMvThreads * kMvQ;
 constexpr int kMvStage = 1536;                 // sources staged per pass
-constexpr int kMvWords = kMvStage / 32;        // mask words per lane
+constexpr int kMvWords = kMvStage / 32;        // mask words per target
 constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 
 struct MvParams {
@@ -31,41 +36,48 @@ struct MvParams {
     const int32_t* cell_s;     // global cell id of each cell-ordered point
     const int32_t* cell_start;
     const int32_t* work;       // (cell, first target) per block
-    const double* tab;         // 2^(-j/2048)
+    const unsigned long long* fxtab;   // T1, T2 of fixexp.cuh
     const Prob* prob;          // per-problem grid and kernel constants
     const int32_t* pid_cell;   // problem of each cell
     const int32_t* active;     // per-problem mask (null: every problem)
-    double c1, c2, c3;         // exp cubic
 };
 
-constexpr size_t kMvSmem = kExpTab2048 * sizeof(double)            // table
-                           + 2 * kMvStage * sizeof(double)         // staged xy
-                           + kMvStage * sizeof(double)             // staged w
-                           + 2 * kMvStage * sizeof(float)          // staged FP32 offsets
-                           + (size_t)kMvWords * kMvThreads * 4;    // accept masks
+constexpr size_t kMvSmem = 2 * kFxTab * sizeof(unsigned long long)   // tables
+                           + 2 * kMvStage * sizeof(double)             // staged xy
+                           + 2 * kMvStage * sizeof(long long)          // staged fixed-point xy
+                           + kMvStage * sizeof(double)                 // staged w
+                           + 2 * kMvStage * sizeof(float)              // staged FP32 offsets
+                           + (size_t)kMvWords * kMvThreads * 4         // accept masks
+                           + (size_t)kMvQ * kMvThreads * sizeof(double);   // partial sums
 
-__global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const double* __restrict__ w,
-                                                              double* __restrict__ y)
+__global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, const double* __restrict__ w,
+                                                                double* __restrict__ y)
 {
-    extern __shared__ double smem[];
-    double* tab = smem;
-    double* SX = tab + kExpTab2048;
-    double* SW = SX + 2 * kMvStage;
-    float* SF = (float*)(SW + kMvStage);
+    extern __shared__ unsigned long long smem_u64[];
+    unsigned long long* T1 = smem_u64;
+    unsigned long long* T2 = T1 + kFxTab;
+    double* SX = (double*)(T2 + kFxTab);
+    long long* SXF = (long long*)(SX + 2 * kMvStage);
+    double* SW = (double*)(SXF + 2 * kMvStage);
+    double* PART = SW + kMvStage;
+    float* SF = (float*)(PART + kMvQ * kMvThreads);
     uint32_t* MASK = (uint32_t*)(SF + 2 * kMvStage);
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
 
     const int tid = threadIdx.x;
-    for (int i = tid; i < kExpTab2048; i += kMvThreads) tab[i] = P.tab[i];
+    const int t = tid & (kMvThreads - 1), qtr = tid / kMvThreads;   // target, quarter (warp-uniform)
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
     const int pcell = P.pid_cell[cell];
     if (P.active && !P.active[pcell]) return;   // masked problem (the whole block belongs to it)
+    for (int i = tid; i < 2 * kFxTab; i += kMv64Threads) T1[i] = P.fxtab[i];
     const Prob& pr = P.prob[pcell];
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
-    const double rc2 = pr.rc2, K = pr.K, knorm = pr.knorm;
+    const double rc2 = pr.rc2, knorm = pr.knorm, fxs = pr.fx_scale;
+    const int sh = pr.fx_sh, F = pr.fx_F;
+    const unsigned long long M = pr.fx_M;
     const float ca = pr.ca, rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
     const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
-    const int p = cb + first + tid;
+    const int p = cb + first + t;
     const bool active = p < ce;
     const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
     const int y0 = max(cy - kst, 0), y1 = min(cy + kst, ncy - 1);
@@ -83,10 +95,13 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
         row_pre[nrow] = s;
     }
     double xi = 0.0, yi = 0.0;
+    long long xf = 0, yf = 0;
     float fx = 0.f, fy = 0.f;
     if (active) {
         xi = P.xy[2 * p];
         yi = P.xy[2 * p + 1];
+        xf = __double2ll_rn(xi * fxs);
+        yf = __double2ll_rn(yi * fxs);
         fx = P.loc[2 * p];
         fy = P.loc[2 * p + 1];
     }
@@ -96,13 +111,16 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
     for (int base = 0; base < S; base += kMvStage) {
         const int ns = min(kMvStage, S - base);
         if (base > 0) __syncthreads();   // the previous pass is done with the staged data
-        for (int idx = tid; idx < ns; idx += kMvThreads) {
+        for (int idx = tid; idx < ns; idx += kMv64Threads) {
             int g = base + idx;
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
             int q = row_beg[r] + (g - row_pre[r]);
-            SX[2 * idx] = P.xy[2 * q];
-            SX[2 * idx + 1] = P.xy[2 * q + 1];
+            const double qx = P.xy[2 * q], qy = P.xy[2 * q + 1];
+            SX[2 * idx] = qx;
+            SX[2 * idx + 1] = qy;
+            SXF[2 * idx] = __double2ll_rn(qx * fxs);
+            SXF[2 * idx + 1] = __double2ll_rn(qy * fxs);
             SW[idx] = w[q];
             int cq = P.cell_s[q] - cbase;
             SF[2 * idx] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
@@ -114,7 +132,7 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
         // exact FP64 test, in a loop of its own so that no FP64 instruction is
         // issued (predicated or not) for the ordinary candidates.
         const int nw = (ns + 31) >> 5;
-        for (int wi = 0; wi < nw; ++wi) {
+        for (int wi = qtr; wi < nw; wi += kMvQ) {
             uint32_t m = 0, band = 0;
             if (active) {
                 const int lim = min(32, ns - wi * 32);
@@ -133,28 +151,30 @@ __global__ void __launch_bounds__(kMvThreads, 2) k_matvec_f64(MvParams P, const 
                 double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
                 if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
             }
-            MASK[wi * kMvThreads + tid] = m;
+            MASK[wi * kMvThreads + t] = m;
         }
-        // FP64 pairs: each lane walks its own accepted sources; the warp steps together
-        int wi = 0;
-        uint32_t cur = nw > 0 ? MASK[tid] : 0u;
+        // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
+        int wi = qtr;
+        uint32_t cur = wi < nw ? MASK[wi * kMvThreads + t] : 0u;
         for (;;) {
-            while (cur == 0u && wi + 1 < nw) {
-                ++wi;
-                cur = MASK[wi * kMvThreads + tid];
+            while (cur == 0u && wi + kMvQ < nw) {
+                wi += kMvQ;
+                cur = MASK[wi * kMvThreads + t];
             }
             const bool has = cur != 0u;
             if (!__any_sync(0xffffffffu, has)) break;
             if (has) {
                 const int idx = wi * 32 + (__ffs(cur) - 1);
                 cur &= cur - 1u;
-                double dx = xi - SX[2 * idx], dy = yi - SX[2 * idx + 1];
-                double r2 = fma(dy, dy, dx * dx);
-                acc = fma(exp_neg_r2(r2, K, tab, P.c1, P.c2, P.c3), SW[idx], acc);
+                const double kv = kernel_fx(xf - SXF[2 * idx], yf - SXF[2 * idx + 1], sh, F, M, T1, T2);
+                acc = fma(kv, SW[idx], acc);
             }
         }
     }
-    if (active) y[p] = acc * knorm;
+    PART[qtr * kMvThreads + t] = acc;
+    __syncthreads();
+    if (qtr == 0 && active)
+        y[p] = (((PART[t] + PART[kMvThreads + t]) + PART[2 * kMvThreads + t]) + PART[3 * kMvThreads + t]) * knorm;
 }
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -288,13 +308,10 @@ MvParams mv_params(const rbf_ctx* ctx)
     P.cell_s = ctx->cell_s.p;
     P.cell_start = ctx->cell_start.p;
     P.work = ctx->mv_work.p;
-    P.tab = ctx->exp2048.p;
+    P.fxtab = ctx->fxtab.p;
     P.prob = ctx->prob.p;
     P.pid_cell = ctx->pid_cell.p;
     P.active = ctx->active_mask;
-    P.c1 = ctx->exp2048_c[0];
-    P.c2 = ctx->exp2048_c[1];
-    P.c3 = ctx->exp2048_c[2];
     return P;
 }
 
@@ -311,7 +328,7 @@ rbf_status matvec_prepare(rbf_ctx* ctx)
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
     if (ctx->n_work == 0) return RBF_OK;
-    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMvThreads, kMvSmem, st, mv_params(ctx), w, y);
+    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMv64Threads, kMvSmem, st, mv_params(ctx), w, y);
     return RBF_OK;
 }
 

@@ -28,7 +28,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
-            "rbf_request_footprint"]
+            "rbf_request_footprint", "rbf_debug_kernel_pairs"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -127,6 +127,7 @@ def load(path: str | None = None):
     L.rbf_profile_read.argtypes = [P, C.c_int, I64, D]
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
     L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
+    L.rbf_debug_kernel_pairs.argtypes = [P, P, P, C.c_int64, P]
     L.rbf_bin_batch.argtypes = [P, P, I64, C.c_int64, C.POINTER(RbfParams), P]
     L.rbf_rasm_setup_batch.argtypes = [P, C.POINTER(RbfRasmParams), P]
     L.rbf_solve_batch.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
@@ -302,6 +303,10 @@ def rbf_profile_read(ctx, kernel: int) -> tuple[int, float]:
 
 def rbf_debug_exp(ctx, t_dev, out_dev, variant: int = 0, stream=None) -> None:
     _check(ctx, load().rbf_debug_exp(ctx, _ptr(t_dev), _ptr(out_dev), t_dev.numel(), int(variant), _stream(stream)))
+
+
+def rbf_debug_kernel_pairs(ctx, pairs_dev, out_dev, stream=None) -> None:
+    _check(ctx, load().rbf_debug_kernel_pairs(ctx, _ptr(pairs_dev), _ptr(out_dev), out_dev.numel(), _stream(stream)))
 
 
 def rbf_status_string(status: int) -> str:

@@ -241,6 +241,68 @@ def test_library_exp_against_cuda_exp(rbf, variant):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["lattice64", "lattice1024_scale", "offset_domain", "wide_cutoff"])
+def test_fixed_point_kernel_values(rbf, case):
+    """The FP64 matvec's kernel value (64-bit fixed-point offsets and exp, FP64
+    bits assembled at the end) against exp(-r2 s) evaluated in long double
+    from the same FP64 coordinates and the same FP64 s = 1/(2 sigma^2): within
+    4e-16 relative over the whole cutoff disc for r_c = 8.6 sigma, 0 beyond it.
+    The log2 argument carries about 57 - log2(t_max) fraction bits, so at
+    r_c = 30 sigma (t up to 450) the bound is 2e-15 -- still below the FP64
+    rounding of the argument itself there (t 2^-53 = 5e-14)."""
+    rng = np.random.default_rng(17)
+    if case == "lattice64":
+        p = W.config_small()
+        xy, sigma, rc = p.xy, p.sigma, p.cutoff
+    elif case == "lattice1024_scale":   # sigma and r_c of the 1M-point lattice, on a small point set
+        sigma = (2.0 / 1023) / 0.8
+        rc = 8.6 * sigma
+        xy = rng.uniform(-1.0, 1.0, (4096, 2))
+    elif case == "offset_domain":       # coordinates far from the origin (few low bits left)
+        sigma, rc = 0.01, 0.086
+        xy = 1000.0 + rng.uniform(0.0, 1.0, (4096, 2))
+    else:                               # r_c = 30 sigma: longer exp range (t up to 450)
+        sigma = 0.02
+        rc = 30 * sigma
+        xy = rng.uniform(-1.0, 1.0, (4096, 2))
+    ctx = rbf.Context(0)
+    rbf.rbf_bin(ctx.handle, dev(xy), xy.shape[0], rbf.RbfParams(sigma, rc, 0.0, 0))
+    m = 200000
+    i = rng.integers(0, xy.shape[0], m)
+    r = rc * np.sqrt(rng.uniform(0.0, 1.0, m))
+    r[:64] = rc * (1.0 - np.logspace(-15, -1, 64))   # at the cutoff
+    r[64:96] = 0.0
+    th = rng.uniform(0.0, 2.0 * np.pi, m)
+    xj = xy[i, 0] + r * np.cos(th)
+    yj = xy[i, 1] + r * np.sin(th)
+    pairs = np.stack([xy[i, 0], xy[i, 1], xj, yj], axis=1)
+    out = torch.empty(m, dtype=torch.float64, device="cuda")
+    rbf.rbf_debug_kernel_pairs(ctx.handle, dev(pairs), out)
+    got = host(out)
+    ctx.close()
+    L = np.longdouble
+    dx = pairs[:, 0].astype(L) - pairs[:, 2].astype(L)
+    dy = pairs[:, 1].astype(L) - pairs[:, 3].astype(L)
+    s = L(1.0 / (2.0 * sigma * sigma))
+    ref = np.exp(-(dx * dx + dy * dy) * s)
+    ex = pairs[:, 0] - pairs[:, 2]
+    ey = pairs[:, 1] - pairs[:, 3]
+    inside = (ex * ex + ey * ey) <= rc * rc   # the FP64 test of the index-list definition
+    assert np.all(got[~inside] == 0.0)
+    rel = np.abs(got[inside].astype(L) - ref[inside]) / ref[inside]
+    bound = 2e-15 if case == "wide_cutoff" else 4e-16
+    assert float(rel.max()) <= bound, float(rel.max())
+
+
+def test_bin_rejects_cutoff_below_fixed_point_resolution(rbf):
+    xy = 1.0e12 + np.random.default_rng(1).uniform(0.0, 1.0, (100, 2))
+    ctx = rbf.Context(0)
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_bin(ctx.handle, dev(xy), 100, rbf.RbfParams(1e-4, 8.6e-4, 0.0, 0))
+    assert e.value.status == 1
+    ctx.close()
+
+
 # ------------------------------------------------------------------ matvec
 
 def matvec_cases():
