@@ -174,9 +174,11 @@ __global__ void k_debug_kernel_pairs(const double* __restrict__ pr4, double* __r
         out[i] = 0.0;
         return;
     }
-    const long long dx = __double2ll_rn(xi * q.fx_scale) - __double2ll_rn(xj * q.fx_scale);
-    const long long dy = __double2ll_rn(yi * q.fx_scale) - __double2ll_rn(yj * q.fx_scale);
-    out[i] = kernel_fx(dx, dy, q.fx_sh, q.fx_F, q.fx_M, tab, tab + kFxTab);
+    const long long du = (long long)((unsigned long long)fx_coord(xi, q.fx_scale, q.fx_sh) -
+                                     (unsigned long long)fx_coord(xj, q.fx_scale, q.fx_sh));
+    const long long dv = (long long)((unsigned long long)fx_coord(yi, q.fx_scale, q.fx_sh) -
+                                     (unsigned long long)fx_coord(yj, q.fx_scale, q.fx_sh));
+    out[i] = kernel_fx(du, dv, q.fx_F, q.fx_M, tab, tab + kFxTab);
 }
 
 __global__ void k_debug_exp(const double* __restrict__ t, double* __restrict__ out, int64_t n, int variant,

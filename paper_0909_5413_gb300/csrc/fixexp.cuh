@@ -32,26 +32,53 @@ void make_fx_tables(unsigned long long* t1, unsigned long long* t2);
 // point (r_c < 2^-32 max|x|, or r_c / sigma beyond ~1000).
 bool make_fx_constants(double amax, double rc, double s, double* scale, int* sh, int* F, unsigned long long* M);
 
-__device__ __forceinline__ double kernel_fx(long long dx, long long dy, int sh, int F, unsigned long long M,
+// High 64 bits of a 64 x 64-bit product from three 32 x 32-bit products (the
+// low x low one is dropped): in [exact - 3, exact].
+__device__ __forceinline__ unsigned long long hi64a(unsigned long long a, unsigned long long b)
+{
+    const unsigned int ah = (unsigned int)(a >> 32), al = (unsigned int)a;
+    const unsigned int bh = (unsigned int)(b >> 32), bl = (unsigned int)b;
+    return (unsigned long long)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+
+// High 64 bits of u^2: in [exact - 2, exact].
+__device__ __forceinline__ unsigned long long sqhi(unsigned long long u)
+{
+    const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+    return (unsigned long long)uh * uh + 2ull * __umulhi(uh, ul);
+}
+
+// Fixed-point coordinate pre-shifted by sh (wrapping: differences of two such
+// values are the exact shifted offsets, which lie inside (-2^63, 2^63) for
+// pairs inside the cutoff).
+__device__ __forceinline__ long long fx_coord(double x, double scale, int sh)
+{
+    return (long long)((unsigned long long)__double2ll_rn(x * scale) << sh);
+}
+
+// exp(-s r2) from the shifted offsets du = (x_i - x_j) 2^(S+sh), dv likewise.
+__device__ __forceinline__ double kernel_fx(long long du, long long dv, int F, unsigned long long M,
                                             const unsigned long long* __restrict__ T1,
                                             const unsigned long long* __restrict__ T2)
 {
-    const unsigned long long ux = (unsigned long long)(dx < 0 ? -dx : dx) << sh;   // < 2^63 (1 + 2^-50)
-    const unsigned long long uy = (unsigned long long)(dy < 0 ? -dy : dy) << sh;
-    const unsigned long long q = __umul64hi(ux, ux) + __umul64hi(uy, uy) + 1ull;   // +1: centre the truncations
-    const unsigned long long z = __umul64hi(q, M);
+    const unsigned long long ux = (unsigned long long)(du < 0 ? -du : du);   // < 2^63 (1 + 2^-50)
+    const unsigned long long uy = (unsigned long long)(dv < 0 ? -dv : dv);
+    const unsigned long long q = sqhi(ux) + sqhi(uy) + 2ull;   // +2 centres the truncations
+    const unsigned long long z = hi64a(q, M) + 1ull;
     const unsigned int n = (unsigned int)(z >> F);
     const unsigned int i1 = (unsigned int)(z >> (F - 10)) & (kFxTab - 1);
     const unsigned int i2 = (unsigned int)(z >> (F - 20)) & (kFxTab - 1);
-    const unsigned long long rho = z << (84 - F);                 // rho 2^20 in [0, 1), units 2^-64
-    const unsigned long long x = __umul64hi(rho, 12193974156573ull);   // rho ln 2, units 2^-64 (ln 2 2^44)
-    const unsigned long long onem = x - (__umul64hi(x, x) >> 1);          // 1 - e^-x
-    unsigned long long m = __umul64hi(T1[i1], T2[i2]) << 1;               // Q1.63
-    m -= __umul64hi(m, onem);
-    const int lz = __clzll((long long)m);
-    const unsigned long long mn = m << lz;                                // [2^63, 2^64)
-    const unsigned long long bits =
-        ((unsigned long long)(1022 - lz - (int)n) << 52) + (mn >> 11) + ((mn >> 10) & 1ull);
+    const unsigned long long rho = z << (84 - F);                   // rho 2^20 in [0, 1), units 2^-64
+    const unsigned long long x = hi64a(rho, 12193974156573ull);       // rho ln 2, units 2^-64 (ln 2 2^44)
+    const unsigned int xh = (unsigned int)(x >> 12);                 // x < 2^43.5: 32 bits suffice for x^2
+    const unsigned long long onem = x - (((unsigned long long)xh * xh) >> 41);   // 1 - e^-x = x - x^2/2
+    unsigned long long m = hi64a(T1[i1], T2[i2]) << 1;                // Q1.63, in (2^62, 2^63]
+    m -= hi64a(m, onem);
+    // m / 2^63 in (1/2, 1]: cap 1.0 at 1 - 2^-63 (which rounds back to 1.0), round
+    // the 10 dropped bits to nearest, and let the implicit bit carry into the
+    // exponent field: 2^-n m / 2^63 = (m / 2^62) 2^(-1-n).
+    m = m - (m >> 63) + 512ull;
+    const unsigned long long bits = ((unsigned long long)(1021 - (int)n) << 52) + (m >> 10);
     return n < 1000u ? __longlong_as_double((long long)bits) : 0.0;
 }
 

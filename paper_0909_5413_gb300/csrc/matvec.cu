@@ -26,7 +26,7 @@ namespace {
 constexpr int kMvThreads = 128;                // targets per block (FP32 kernel: threads per block)
 constexpr int kMvQ = 4;                        // source quarters of the FP64 kernel
 constexpr int kMv64Threads = kMvThreads * kMvQ;
-constexpr int kMvStage = 1536;                 // sources staged per pass
+constexpr int kMvStage = 1152;                 // sources staged per pass (3 x 3 cells of ~115 points: one pass)
 constexpr int kMvWords = kMvStage / 32;        // mask words per target
 constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 
@@ -41,6 +41,36 @@ struct MvParams {
     const int32_t* pid_cell;   // problem of each cell
     const int32_t* active;     // per-problem mask (null: every problem)
 };
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Packed FP32 pairs (two lanes of work per instruction on sm_100-class SMs).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
+    return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b),
+                          Cc = *reinterpret_cast<unsigned long long*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(A), "l"(B), "l"(Cc));
+    return *reinterpret_cast<float2*>(&d);
+}
 
 constexpr size_t kMvSmem = 2 * kFxTab * sizeof(unsigned long long)   // tables
                            + 2 * kMvStage * sizeof(double)             // staged xy
@@ -100,8 +130,8 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
     if (active) {
         xi = P.xy[2 * p];
         yi = P.xy[2 * p + 1];
-        xf = __double2ll_rn(xi * fxs);
-        yf = __double2ll_rn(yi * fxs);
+        xf = fx_coord(xi, fxs, sh);
+        yf = fx_coord(yi, fxs, sh);
         fx = P.loc[2 * p];
         fy = P.loc[2 * p + 1];
     }
@@ -119,31 +149,43 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
             const double qx = P.xy[2 * q], qy = P.xy[2 * q + 1];
             SX[2 * idx] = qx;
             SX[2 * idx + 1] = qy;
-            SXF[2 * idx] = __double2ll_rn(qx * fxs);
-            SXF[2 * idx + 1] = __double2ll_rn(qy * fxs);
+            SXF[2 * idx] = fx_coord(qx, fxs, sh);
+            SXF[2 * idx + 1] = fx_coord(qy, fxs, sh);
             SW[idx] = w[q];
             int cq = P.cell_s[q] - cbase;
-            SF[2 * idx] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
-            SF[2 * idx + 1] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
+            // FP32 offsets, two sources per float4: (x_a, x_b, y_a, y_b)
+            SF[4 * (idx >> 1) + (idx & 1)] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
+            SF[4 * (idx >> 1) + 2 + (idx & 1)] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
         }
         __syncthreads();
         // FP32 filter: one accept bit per staged source. Sources in the thin band
         // around the cutoff get a second bit and are settled afterwards by the
         // exact FP64 test, in a loop of its own so that no FP64 instruction is
-        // issued (predicated or not) for the ordinary candidates.
+        // issued (predicated or not) for the ordinary candidates. Two
+        // candidates per packed f32x2 step; a partial last word is masked.
         const int nw = (ns + 31) >> 5;
+        const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
         for (int wi = qtr; wi < nw; wi += kMvQ) {
-            uint32_t m = 0, band = 0;
+            uint32_t m = 0, mh = 0;
             if (active) {
-                const int lim = min(32, ns - wi * 32);
-                for (int b = 0; b < lim; ++b) {
-                    const int idx = wi * 32 + b;
-                    float dx = fx - SF[2 * idx], dy = fy - SF[2 * idx + 1];
-                    float r2 = fmaf(dy, dy, dx * dx);
-                    m |= (uint32_t)(r2 < rc2f_lo) << b;
-                    band |= (uint32_t)(r2 >= rc2f_lo && r2 <= rc2f_hi) << b;
+                const float4* S4 = reinterpret_cast<const float4*>(SF) + wi * 16;
+#pragma unroll
+                for (int b = 0; b < 32; b += 2) {
+                    const float4 v = S4[b >> 1];
+                    const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
+                    const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
+                    const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
+                    m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
+                    mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
+                }
+                const int lim = ns - wi * 32;
+                if (lim < 32) {
+                    const uint32_t keep = (1u << lim) - 1u;
+                    m &= keep;
+                    mh &= keep;
                 }
             }
+            uint32_t band = mh & ~m;
             while (band != 0u) {
                 const int b = __ffs(band) - 1;
                 band &= band - 1u;
@@ -166,7 +208,9 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
             if (has) {
                 const int idx = wi * 32 + (__ffs(cur) - 1);
                 cur &= cur - 1u;
-                const double kv = kernel_fx(xf - SXF[2 * idx], yf - SXF[2 * idx + 1], sh, F, M, T1, T2);
+                const double kv = kernel_fx((long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]),
+                                            (long long)((unsigned long long)yf - (unsigned long long)SXF[2 * idx + 1]),
+                                            F, M, T1, T2);
                 acc = fma(kv, SW[idx], acc);
             }
         }
@@ -175,36 +219,6 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
     __syncthreads();
     if (qtr == 0 && active)
         y[p] = (((PART[t] + PART[kMvThreads + t]) + PART[2 * kMvThreads + t]) + PART[3 * kMvThreads + t]) * knorm;
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Packed FP32 pairs (two lanes of work per instruction on sm_100-class SMs).
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
-    return *reinterpret_cast<float2*>(&d);
-}
-
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
-    return *reinterpret_cast<float2*>(&d);
-}
-
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b),
-                          Cc = *reinterpret_cast<unsigned long long*>(&c);
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(A), "l"(B), "l"(Cc));
-    return *reinterpret_cast<float2*>(&d);
 }
 
 constexpr int kMv32Stage = 3072;   // sources staged per pass (even; 36 KB of static shared memory)
