@@ -62,6 +62,7 @@ def lib():
         L.orc_matvec_cutoff.argtypes = [_D, C.c_int64, C.POINTER(OrcGrid), _I32, _I32,
                                         C.POINTER(OrcKernelParams), _D, _D]
         L.orc_matvec_dense.argtypes = [_D, C.c_int64, C.POINTER(OrcKernelParams), _D, _D]
+        L.orc_eval.argtypes = [_D, C.c_int64, C.POINTER(OrcKernelParams), _D, _D, C.c_int64, _D]
         L.orc_cholesky.argtypes = [_D, C.c_int64]
         L.orc_cholesky_solve.argtypes = [_D, C.c_int64, _D]
         L.orc_dense_solve.argtypes = [_D, C.c_int64, C.POINTER(OrcKernelParams), _D, _D]
@@ -80,6 +81,8 @@ def lib():
             getattr(L, name).restype = rt
             getattr(L, name).argtypes = [C.c_void_p]
         L.orc_problem_matvec.argtypes = [C.c_void_p, _D, _D]
+        L.orc_problem_set_additive.argtypes = [C.c_void_p, C.c_int]
+        L.orc_problem_set_additive.restype = None
         L.orc_problem_rasm_apply.argtypes = [C.c_void_p, _D, _D]
         L.orc_problem_solve.argtypes = [C.c_void_p, _D, _D, C.c_int64, C.c_double, C.c_int64, C.c_int, _D,
                                         C.POINTER(OrcGmresInfo)]
@@ -209,6 +212,16 @@ def matvec_dense(xy: np.ndarray, w: np.ndarray, sigma: float, normalized: bool =
     return y
 
 
+def eval_points(xy: np.ndarray, w: np.ndarray, xe: np.ndarray, sigma: float, rc: float,
+                normalized: bool = False) -> np.ndarray:
+    """Interpolant s at the points xe: every centre within r_c, in index order."""
+    xy, w, xe = _f64(xy), _f64(w), _f64(xe)
+    kp = OrcKernelParams(sigma, rc, int(normalized))
+    out = np.empty(xe.shape[0])
+    lib().orc_eval(_dp(xy), xy.shape[0], C.byref(kp), _dp(w), _dp(xe), xe.shape[0], _dp(out))
+    return out
+
+
 def cholesky(a: np.ndarray) -> np.ndarray:
     """Lower Cholesky factor of an SPD matrix (raises on a non-positive pivot)."""
     a = _f64(a).copy()
@@ -287,7 +300,8 @@ class Problem:
     """Binning, subdomain lists and RASM factors for one point set (Sec. 2)."""
 
     def __init__(self, xy: np.ndarray, sigma: float, rc: float, x0: float, y0: float, B: float,
-                 delta: float, normalized: bool = False, cell_size: float = 0.0, max_sub_points: int = 4096):
+                 delta: float, normalized: bool = False, cell_size: float = 0.0, max_sub_points: int = 4096,
+                 additive: bool = False):
         self.xy = _f64(xy)
         self.n = self.xy.shape[0]
         self.sigma, self.rc = float(sigma), float(rc)
@@ -304,6 +318,7 @@ class Problem:
         self.grid = Grid(g.xmin, g.ymin, g.xmax, g.ymax, g.c, g.ncx, g.ncy)
         self.nbx, self.nby = int(b.nbx), int(b.nby)
         self.nsub = self.nbx * self.nby
+        lib().orc_problem_set_additive(h, int(additive))   # Eq. asm instead of Eq. rasm
 
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:

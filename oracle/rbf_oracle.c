@@ -28,6 +28,10 @@
  *                 the overlap list), solved directly (Sec. 3.1 uses a dense
  *                 direct solve; A_i is SPD, so Cholesky).
  *   RASM          Eq. rasm: z = sum_i ~R_i^T A_i^{-1} R_i r.
+ *   ASM           Eq. asm (for the comparison of Sec. 2.2): the same solves
+ *                 with every overlap entry added back, z = sum_i R_i^T A_i^{-1} R_i r.
+ *   evaluation    Eq. rbf2 at points other than the centres (the use of
+ *                 Sec. 3.2: interpolation onto a lattice), same truncation.
  *   GMRES         Sec. 2.2 / Sec. 3.1: GMRES with the RASM preconditioner,
  *                 restarted, relative tolerance 1e-13. Right preconditioning,
  *                 classical Gram-Schmidt applied twice, Givens rotations.
@@ -254,6 +258,27 @@ int orc_matvec_dense(const double* xy, int64_t n, const orc_kernel_params* kp,
     return ORC_OK;
 }
 
+/* Interpolant at other points (Eq. rbf2 evaluated off the centres, with the
+ * truncation of Sec. 2.3): s_i = sum over all centres j, in index order, of
+ * k(r2) w_j where r2 = |xe_i - x_j|^2 <= rc^2 (same rounding as pair_r2). */
+int orc_eval(const double* xy, int64_t n, const orc_kernel_params* kp, const double* w,
+             const double* xe, int64_t m, double* s)
+{
+    double rc2 = kp->rc * kp->rc;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double dx = xe[2 * i] - xy[2 * j];
+            double dy = xe[2 * i + 1] - xy[2 * j + 1];
+            double r2 = dx * dx + dy * dy;
+            if (r2 <= rc2) acc += orc_kernel(r2, kp) * w[j];
+        }
+        s[i] = acc;
+    }
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------------- Cholesky */
 
 /* Textbook Cholesky A = L L^T of an n x n row-major SPD matrix (row by row:
@@ -404,6 +429,7 @@ typedef struct {
     int64_t* fac_ptr;        /* offsets of each n_i x n_i factor */
     double* fac;             /* Cholesky factors (lower triangles, row-major) */
     int32_t* core_of;        /* subdomain whose core holds each point */
+    int additive;            /* 1: plain additive Schwarz, Eq. asm (no restriction) */
 } orc_rasm;
 
 /* Form A_i = R_i A~ R_i^T over each overlap list and factor it (Sec. 2.2). */
@@ -441,11 +467,37 @@ int orc_rasm_setup(orc_rasm* r, int64_t max_sub_points)
     return status;
 }
 
+/* Additive Schwarz, Eq. asm: z = sum_i R_i^T A_i^{-1} R_i v, every overlap
+ * entry of every subdomain added back. The subdomain solves run in parallel
+ * into a scratch copy of the overlap lists; the sums are then taken serially
+ * in subdomain order (deterministic). */
+static void asm_apply(const orc_rasm* r, const double* v, double* z)
+{
+    memset(z, 0, sizeof(double) * (size_t)r->n);
+    int64_t tot = r->ov_ptr[r->nsub];
+    double* u = (double*)malloc(sizeof(double) * (size_t)(tot > 0 ? tot : 1));
+    if (!u) return;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t s = 0; s < r->nsub; ++s) {
+        const int32_t* ov = r->ov_idx + r->ov_ptr[s];
+        int64_t m = r->ov_ptr[s + 1] - r->ov_ptr[s];
+        double* buf = u + r->ov_ptr[s];
+        for (int64_t p = 0; p < m; ++p) buf[p] = v[ov[p]];
+        orc_cholesky_solve(r->fac + r->fac_ptr[s], m, buf);
+    }
+    for (int64_t e = 0; e < tot; ++e) z[r->ov_idx[e]] += u[e];
+    free(u);
+}
+
 /* z = sum_i ~R_i^T A_i^{-1} R_i v (Eq. rasm): restrict v to the overlap list,
  * solve with the factor, keep only the entries whose point is in the core
  * of the same subdomain. Vectors in original order. */
 void orc_rasm_apply(const orc_rasm* r, const double* v, double* z)
 {
+    if (r->additive) {
+        asm_apply(r, v, z);
+        return;
+    }
     memset(z, 0, sizeof(double) * (size_t)r->n);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t s = 0; s < r->nsub; ++s) {
@@ -686,6 +738,9 @@ const int64_t* orc_problem_core_ptr(const orc_problem* p) { return p->core_ptr; 
 const int32_t* orc_problem_core_idx(const orc_problem* p) { return p->core_idx; }
 const int64_t* orc_problem_ov_ptr(const orc_problem* p) { return p->ov_ptr; }
 const int32_t* orc_problem_ov_idx(const orc_problem* p) { return p->ov_idx; }
+
+/* Select the plain additive Schwarz preconditioner (Eq. asm) instead of RASM. */
+void orc_problem_set_additive(orc_problem* p, int additive) { p->rasm.additive = additive; }
 
 void orc_problem_matvec(orc_problem* p, const double* w, double* y) { op_amul(p, w, y); }
 void orc_problem_rasm_apply(orc_problem* p, const double* v, double* z) { op_minv(p, v, z); }

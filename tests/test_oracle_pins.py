@@ -401,3 +401,82 @@ def test_paper_parameters_converge_quickly():
     _, info = pr.solve(p.f, rtol=1e-13)
     assert info.status == 0
     assert info.iters < 20, info.iters
+
+
+# ------------------------------------------------- ASM and evaluation
+
+def asm_dense(p, B, delta):
+    """sum_i R_i^T A_i^{-1} R_i (Eq. asm) from explicit numpy matrices."""
+    a = np_matrix(p.xy, p.sigma, p.cutoff)
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, B, delta)
+    op, oi = pr.overlap_lists()
+    m = np.zeros((p.n, p.n))
+    for s in range(pr.nsub):
+        o = oi[op[s]:op[s + 1]]
+        m[np.ix_(o, o)] += np.linalg.inv(a[np.ix_(o, o)])
+    return m
+
+
+@pytest.mark.parametrize("ring", [1, 2])
+def test_asm_apply_matches_explicit_matrices(ring):
+    p = W.lattice_problem(14, 0.8, seed=31, ring_points=ring)
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=True)
+    v = np.random.default_rng(5).standard_normal(p.n)
+    ref = asm_dense(p, p.core_size, p.overlap) @ v
+    np.testing.assert_allclose(pr.rasm_apply(v), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+def test_asm_is_symmetric_and_reduces_to_block_jacobi():
+    p = W.lattice_problem(12, 0.8, seed=32)
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=True)
+    rng = np.random.default_rng(6)
+    u, v = rng.standard_normal(p.n), rng.standard_normal(p.n)
+    a, b = v @ pr.rasm_apply(u), u @ pr.rasm_apply(v)
+    assert abs(a - b) <= 1e-10 * (abs(a) + abs(b))      # M^-1 of Eq. asm is symmetric (Eq. rasm's is not)
+    q = W.lattice_problem(12, 0.8, seed=33, ring_points=0)
+    r0 = O.Problem(q.xy, q.sigma, q.cutoff, q.x0, q.x0, q.core_size, 0.0)
+    a0 = O.Problem(q.xy, q.sigma, q.cutoff, q.x0, q.x0, q.core_size, 0.0, additive=True)
+    np.testing.assert_array_equal(a0.rasm_apply(u[:q.n]), r0.rasm_apply(u[:q.n]))   # no overlap: identical
+
+
+def test_rasm_converges_faster_than_asm():
+    """Sec. 2.2: the restricted variant converges in fewer GMRES steps than the
+    plain additive one on the same subdomains (paper sizes B = 5 sigma, D = 1.9 B)."""
+    p = W.unit_square_problem(0.9, sigma=0.02, seed=34)
+    it = {}
+    for additive in (False, True):
+        pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=additive)
+        _, info = pr.solve(p.f, max_iters=600)
+        assert info.status == 0
+        it[additive] = info.iters
+    assert it[False] < it[True], it
+
+
+def test_eval_matches_numpy_definition():
+    p = W.lattice_problem(24, 0.8, seed=35)
+    rng = np.random.default_rng(7)
+    w = rng.standard_normal(p.n)
+    xe = rng.uniform(-1.1, 1.1, (3000, 2))
+    dx = xe[:, None, 0] - p.xy[None, :, 0]
+    dy = xe[:, None, 1] - p.xy[None, :, 1]
+    r2 = dx * dx + dy * dy
+    k = np.exp(-r2 / (2 * p.sigma * p.sigma))
+    k[r2 > p.cutoff * p.cutoff] = 0.0
+    ref = k @ w
+    got = O.eval_points(p.xy, w, xe, p.sigma, p.cutoff)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+    # at the centres the interpolant is the matvec (same truncated operator)
+    np.testing.assert_allclose(O.eval_points(p.xy, w, p.xy, p.sigma, p.cutoff),
+                               O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff), rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+def test_eval_single_centre_and_far_points():
+    xy = np.array([[0.3, -0.2]])
+    sigma, rc = 0.05, 0.43
+    xe = np.array([[0.3, -0.2], [0.35, -0.2], [0.3, 0.0], [5.0, 5.0], [0.3 + 0.43, -0.2], [0.3 + 0.4301, -0.2]])
+    got = O.eval_points(xy, np.array([2.5]), xe, sigma, rc)
+    r2 = ((xe - xy) ** 2).sum(1)
+    ref = 2.5 * np.exp(-r2 / (2 * sigma * sigma))
+    ref[r2 > rc * rc] = 0.0
+    np.testing.assert_allclose(got, ref, rtol=1e-15, atol=0)
+    assert got[3] == 0.0 and got[5] == 0.0 and got[4] > 0.0
