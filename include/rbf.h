@@ -66,8 +66,11 @@ typedef struct {
     double x0, y0;        /* box origin */
     double core_size;     /* B > 0 */
     double overlap;       /* delta >= 0 */
-    int max_sub_points;   /* cap on an overlap list, 1..128 (0 = 128) */
+    int max_sub_points;   /* cap on an overlap list, 1..192 (0 = 192) */
     int precision;        /* storage of the subdomain inverses: RBF_FP64 or RBF_FP32 */
+    int additive;         /* 0: restricted (Eq. rasm, default); 1: plain additive Schwarz (Eq. asm), for
+                           * comparison: every overlap entry of A_i^{-1} r_i is added back (full n x n
+                           * inverses, about n_overlap / n_core times the memory) */
 } rbf_rasm_params;
 
 /* GMRES settings (Sec. 2.2, Sec. 3.1: GMRES with RASM, rtol 1e-13). */
@@ -139,6 +142,20 @@ rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf
 rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const double* f_host, double* w_host,
                                 int64_t n, const rbf_params* params, const rbf_rasm_params* rasm,
                                 const rbf_solve_params* solve, rbf_solve_info* info, rbf_stream stream);
+
+/* Evaluate the interpolant s(x) = sum_j w_j phi(|x - x_j|) (Eq. rbf2 with the
+ * truncated kernel of Sec. 2.3: terms with |x - x_j|^2 > r_c^2 dropped, the
+ * same FP64 pair test as the system matrix) at m points x: the paper's target
+ * use, interpolation from the scattered centres onto other points such as a
+ * lattice (Sec. 3.2). xe_dev: m x 2 interleaved (x, y), device, any order;
+ * w_dev: n weights in user order (from rbf_solve); s_dev: m outputs (device,
+ * caller-owned). At the centres themselves s equals rbf_matvec's y bit for
+ * bit. Points farther than r_c from every centre get 0. Needs rbf_bin (one
+ * problem: STATE for a batch); INVALID_ARG for a non-finite point. The
+ * points are binned into the centres' grid on each call (clamped to the edge
+ * cells). */
+rbf_status rbf_eval(rbf_ctx* ctx, const double* xe_dev, int64_t m, const double* w_dev, double* s_dev,
+                    rbf_stream stream);
 
 /* y = A~ w in FP64, like rbf_matvec(..., RBF_FP64, ...), without allocating.
  * The paper has no counterpart: this entry point exists for callers that

@@ -276,6 +276,28 @@ __global__ void k_neighbors(const double* __restrict__ xy_s, const int32_t* __re
     }
 }
 
+// Cell of each evaluation point in problem 0's grid (clamped to the edge
+// cells, so the (2k+1)^2 stencil still covers every source within r_c of a
+// point outside the bounding box); flags a non-finite coordinate.
+__global__ void k_target_count(const double* __restrict__ xe, int64_t m, const Prob* __restrict__ prob,
+                               int32_t* __restrict__ cell_u, int32_t* __restrict__ counts, int* __restrict__ bad)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const Prob& P = prob[0];
+    const double x = xe[2 * i], y = xe[2 * i + 1];
+    int32_t cell = 0;
+    if (isfinite(x) && isfinite(y)) {
+        int64_t cx = cell_axis(x, P.xmin, P.c, P.ncx);
+        int64_t cy = cell_axis(y, P.ymin, P.c, P.ncy);
+        cell = (int32_t)(cy * P.ncx + cx);
+    } else {
+        *bad = 1;
+    }
+    cell_u[i] = cell;
+    atomicAdd(&counts[cell], 1);
+}
+
 __global__ void k_widen_i32_i64(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,6 +441,61 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
                ctx->cell_s.p, ctx->cell_start.p, n, ctx->prob.p, ctx->pid.p, (const int64_t*)p64, ctx->nbr_cnt.p, idx,
                1);
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    return RBF_OK;
+}
+
+// Bins m evaluation points (user order, device) into the grid of problem 0:
+// cell-sorted coordinates, FP32 offsets, per-cell ranges and work items for
+// the matvec kernel, in ctx->ev. INVALID_ARG for a non-finite coordinate.
+rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st)
+{
+    EvalBins& E = ctx->ev;
+    const int64_t ncell = ctx->ncell_total;
+    RBF_CHECK(ensure(ctx, E.pid, m));
+    RBF_CHECK(ensure(ctx, E.cell_u, m));
+    RBF_CHECK(ensure(ctx, E.cell_s, m));
+    RBF_CHECK(ensure(ctx, E.perm, m));
+    RBF_CHECK(ensure(ctx, E.iperm, m));
+    RBF_CHECK(ensure(ctx, E.tmp, std::max<int64_t>(m, 2 * kNumSMs + 1)));
+    RBF_CHECK(ensure(ctx, E.counts, ncell + 1));
+    RBF_CHECK(ensure(ctx, E.cell_start, ncell + 1));
+    RBF_CHECK(ensure(ctx, E.wcnt, ncell + 1));
+    RBF_CHECK(ensure(ctx, E.woff, ncell + 1));
+    RBF_CHECK(ensure(ctx, E.xy_s, 2 * m));
+    RBF_CHECK(ensure(ctx, E.loc, 2 * m));
+    RBF_CHECK(ensure(ctx, E.flag, 1));
+    RBF_CUDA(ctx, cudaMemsetAsync(E.pid.p, 0, sizeof(int32_t) * m, st));
+    RBF_CUDA(ctx, cudaMemsetAsync(E.flag.p, 0, sizeof(int), st));
+    RBF_CUDA(ctx, cudaMemsetAsync(E.counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
+    RBF_LAUNCH(ctx, k_target_count, blocks_for(m, 256), 256, 0, st, xe, m, ctx->prob.p, E.cell_u.p, E.counts.p,
+               E.flag.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, E.counts.p, E.cell_start.p, ncell, st));
+    RBF_CUDA(ctx, cudaMemsetAsync(E.counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
+    RBF_LAUNCH(ctx, k_cell_scatter, blocks_for(m, 256), 256, 0, st, E.cell_u.p, m, E.cell_start.p, E.counts.p,
+               E.tmp.p);
+    RBF_LAUNCH(ctx, k_cell_rank, blocks_for(ncell * 32, 256), 256, 0, st, E.cell_start.p, ncell, E.tmp.p, E.perm.p);
+    RBF_LAUNCH(ctx, k_gather_sorted, blocks_for(m, 256), 256, 0, st, xe, m, E.perm.p, E.cell_u.p, E.xy_s.p,
+               E.iperm.p, E.cell_s.p);
+    RBF_LAUNCH(ctx, k_local_coords, blocks_for(m, 256), 256, 0, st, E.xy_s.p, E.cell_s.p, m, ctx->prob.p, E.pid.p,
+               E.loc.p);
+    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, E.cell_start.p, ncell, E.wcnt.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, E.wcnt.p, E.woff.p, ncell, st));
+    int32_t hv[2] = {0, 0};
+    RBF_CUDA(ctx, cudaMemcpyAsync(&hv[0], E.woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&hv[1], E.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    if (hv[1]) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_eval: non-finite evaluation point");
+    E.m = m;
+    E.nwork = hv[0];
+    RBF_CHECK(ensure(ctx, E.work, 2 * (size_t)std::max<int32_t>(hv[0], 1)));
+    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, E.wcnt.p, E.woff.p, ncell, E.work.p);
+    return RBF_OK;
+}
+
+rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, k_permute_to_user, blocks_for(ctx->ev.m, 256), 256, 0, st, sorted, ctx->ev.perm.p, ctx->ev.m,
+               user);
     return RBF_OK;
 }
 

@@ -417,6 +417,7 @@ static rbf_status rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params, 
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->rasm_ready = false;
     ctx->rasm_precision = precision;
+    ctx->rasm_additive = params[0].additive != 0;
     ctx->nsub = nsub;
     if (ctx->nprob == 1) {
         const Prob& q = ctx->prob_h[0];
@@ -436,6 +437,7 @@ static rbf_status rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params, 
     if (ctx->max_ov > cap)
         return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE, "rbf_rasm_setup: an overlap list has %d points (cap %d)",
                     ctx->max_ov, cap);
+    if (ctx->rasm_additive) RBF_CHECK(asm_lists(ctx, st));
     RBF_CHECK(rasm_factor(ctx, st));
     ctx->rasm_ready = true;
     return RBF_OK;
@@ -637,6 +639,27 @@ rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double*
     if (total_ms) *total_ms = tot;
     s.used = 0;
     return RBF_OK;
+}
+
+rbf_status rbf_eval(rbf_ctx* ctx, const double* xe_dev, int64_t m, const double* w_dev, double* s_dev,
+                    rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_eval: call rbf_bin first");
+    if (ctx->nprob != 1) return fail(ctx, RBF_ERR_STATE, "rbf_eval: the context holds a batch of problems");
+    if (m < 0 || m > (int64_t)0x7fffffff - 1)
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_eval: need 0 <= m < 2^31 (m = %lld)", (long long)m);
+    if (m == 0) return RBF_OK;
+    if (!xe_dev || !w_dev || !s_dev) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_eval: null buffer");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = S(stream);
+    RBF_CHECK(bin_targets(ctx, xe_dev, m, st));
+    EvalBins& E = ctx->ev;
+    RBF_CHECK(ensure(ctx, E.w_s, ctx->n));
+    RBF_CHECK(ensure(ctx, E.s_s, m));
+    RBF_CHECK(permute_to_sorted(ctx, w_dev, E.w_s.p, st));
+    RBF_CHECK(eval_sorted_f64(ctx, E.xy_s.p, E.loc.p, E.cell_start.p, E.work.p, E.nwork, E.w_s.p, E.s_s.p, st));
+    return targets_to_user(ctx, E.s_s.p, s_dev, st);
 }
 
 rbf_status rbf_debug_kernel_pairs(rbf_ctx* ctx, const double* pairs_dev, double* out_dev, int64_t n,

@@ -15,7 +15,7 @@
 namespace rbf {
 
 constexpr int kMaxRestart = 32;   // GMRES(m): m <= 32 (the CGS2 kernels keep V_k[i] in registers)
-constexpr int kMaxSub = 128;      // overlap list cap (subdomain matrix dimension)
+constexpr int kMaxSub = 192;      // overlap list cap (subdomain matrix dimension)
 constexpr int kNumSMs = 152;      // GB300
 
 // Device-resident small state of one GMRES cycle (Hessenberg, Givens, g).
@@ -71,6 +71,15 @@ struct Prob {
 
 }  // namespace rbf
 
+// Evaluation points binned into a context's grid (rbf_eval).
+struct EvalBins {
+    int64_t m = 0, nwork = 0;
+    rbf::DevArray<int32_t> pid, cell_u, cell_s, perm, iperm, tmp, counts, cell_start, wcnt, woff, work;
+    rbf::DevArray<double> xy_s, w_s, s_s;   // sorted targets; w in cell order; s in target order
+    rbf::DevArray<float> loc;
+    rbf::DevArray<int> flag;
+};
+
 struct rbf_prof_slot {
     std::vector<cudaEvent_t> ev;   // pairs (start, stop)
     int64_t used = 0;
@@ -112,6 +121,7 @@ struct rbf_ctx {
     int64_t n_work = 0;
     rbf::DevArray<double> exp2048; // 2^(-j/2048), j < 2048
     rbf::DevArray<unsigned long long> fxtab;   // T1 (1024) then T2 (1024), Q1.63
+    EvalBins ev;                   // rbf_eval targets
     double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)
@@ -124,6 +134,10 @@ struct rbf_ctx {
     rbf::DevArray<int64_t> w_off, w_size;
     rbf::DevArray<double> W64;
     rbf::DevArray<float> W32;
+    bool rasm_additive = false;    // Eq. asm: W holds full inverses, applies gather through asm_t*
+    rbf::DevArray<int32_t> asm_tptr, asm_tidx, asm_fill, asm_iota;   // overlap entries of each point
+    rbf::DevArray<double> asm_u64;
+    rbf::DevArray<float> asm_u32;
     rbf::DevArray<int> status_dev;
 
     // ---- solver workspace
@@ -202,6 +216,9 @@ rbf_status permute_to_user(rbf_ctx* ctx, const double* sorted, double* user, cud
 rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capacity, int64_t* total,
                           cudaStream_t st);
 
+rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st);
+rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cudaStream_t st);
+
 // ---- subdomain.cu
 rbf_status build_subdomains(rbf_ctx* ctx, cudaStream_t st);
 rbf_status export_subdomains(rbf_ctx* ctx, int32_t* core_ptr, int32_t* core_idx, int32_t* ov_ptr,
@@ -212,6 +229,9 @@ rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStrea
 rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 // The FP64 matvec launch alone (no profiler events), for the allocation-free entry point.
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+// The FP64 kernel for targets binned by bin_targets (cell-sorted; s in target order).
+rbf_status eval_sorted_f64(rbf_ctx* ctx, const double* txy, const float* tloc, const int32_t* tcell_start,
+                           const int32_t* twork, int64_t nwork, const double* w, double* s, cudaStream_t st);
 // Function attributes of the matvec kernels (called once per binning, outside any capture).
 rbf_status matvec_prepare(rbf_ctx* ctx);
 // Drop the captured batched cycle (its kernels hold pointers into the context).
@@ -219,6 +239,7 @@ void batch_graph_reset(rbf_ctx* ctx);
 
 // ---- rasm.cu  (vectors in cell order)
 rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st);
+rbf_status asm_lists(rbf_ctx* ctx, cudaStream_t st);   // overlap entries per point (Eq. asm only)
 rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStream_t st);
 
 // ---- gmres.cu

@@ -31,11 +31,15 @@ constexpr int kMvWords = kMvStage / 32;        // mask words per target
 constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 
 struct MvParams {
-    const double* xy;          // cell-ordered coordinates (x, y)
+    const double* xy;          // cell-ordered source coordinates (x, y)
     const float* loc;          // FP32 scaled offsets from the point's cell corner (x, y)
     const int32_t* cell_s;     // global cell id of each cell-ordered point
     const int32_t* cell_start;
     const int32_t* work;       // (cell, first target) per block
+    // targets (the sources themselves for A~ w; other points for s(x))
+    const double* txy;
+    const float* tloc;
+    const int32_t* tcell_start;
     const unsigned long long* fxtab;   // T1, T2 of fixexp.cuh
     const Prob* prob;          // per-problem grid and kernel constants
     const int32_t* pid_cell;   // problem of each cell
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
     const int sh = pr.fx_sh, F = pr.fx_F;
     const unsigned long long M = pr.fx_M;
     const float ca = pr.ca, rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
-    const int cb = P.cell_start[cell], ce = P.cell_start[cell + 1];
+    const int cb = P.tcell_start[cell], ce = P.tcell_start[cell + 1];
     const int p = cb + first + t;
     const bool active = p < ce;
     const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
@@ -128,12 +132,12 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
     long long xf = 0, yf = 0;
     float fx = 0.f, fy = 0.f;
     if (active) {
-        xi = P.xy[2 * p];
-        yi = P.xy[2 * p + 1];
+        xi = P.txy[2 * p];
+        yi = P.txy[2 * p + 1];
         xf = fx_coord(xi, fxs, sh);
         yf = fx_coord(yi, fxs, sh);
-        fx = P.loc[2 * p];
-        fy = P.loc[2 * p + 1];
+        fx = P.tloc[2 * p];
+        fy = P.tloc[2 * p + 1];
     }
     __syncthreads();
     const int S = row_pre[nrow];
@@ -322,6 +326,9 @@ MvParams mv_params(const rbf_ctx* ctx)
     P.cell_s = ctx->cell_s.p;
     P.cell_start = ctx->cell_start.p;
     P.work = ctx->mv_work.p;
+    P.txy = ctx->xy_s.p;
+    P.tloc = ctx->loc32.p;
+    P.tcell_start = ctx->cell_start.p;
     P.fxtab = ctx->fxtab.p;
     P.prob = ctx->prob.p;
     P.pid_cell = ctx->pid_cell.p;
@@ -343,6 +350,21 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
 {
     if (ctx->n_work == 0) return RBF_OK;
     RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMv64Threads, kMvSmem, st, mv_params(ctx), w, y);
+    return RBF_OK;
+}
+
+// s = sum_j k(|t - x_j|) w_j for the cell-sorted targets of another point
+// set binned into the same grid (txy, tloc, tcell_start, twork, nwork).
+rbf_status eval_sorted_f64(rbf_ctx* ctx, const double* txy, const float* tloc, const int32_t* tcell_start,
+                           const int32_t* twork, int64_t nwork, const double* w, double* s, cudaStream_t st)
+{
+    if (nwork == 0) return RBF_OK;
+    MvParams P = mv_params(ctx);
+    P.work = twork;
+    P.txy = txy;
+    P.tloc = tloc;
+    P.tcell_start = tcell_start;
+    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)nwork, kMv64Threads, kMvSmem, st, P, w, s);
     return RBF_OK;
 }
 

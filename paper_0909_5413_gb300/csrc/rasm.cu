@@ -9,6 +9,12 @@
 // so that the apply is one small dense GEMV per subdomain, z_core = W_i r_ov,
 // with no triangular-solve dependency chain. Each point is in exactly one
 // core, so every z entry is written once (no atomics, deterministic).
+//
+// The plain additive Schwarz method of Eq. asm (kept for the comparison the
+// paper makes between the two) stores the full A_i^{-1} (n x n) and adds
+// every overlap entry back: the per-subdomain GEMV writes u_i = A_i^{-1} r_i
+// to a scratch copy of the overlap lists, and a gather sums, for each point,
+// its entries in subdomain order (deterministic, no atomics).
 #include <cmath>
 
 #include "common.cuh"
@@ -18,12 +24,22 @@ namespace {
 
 constexpr int kSetupWarps = 4;
 
-// Per-warp shared layout (doubles): A[n*n] | X[nc*n] | xs[n] | ys[n].
+// Packed lower triangle: row i starts at i (i + 1) / 2.
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Shared layout per warp (doubles): L[nmax (nmax + 1) / 2] | X[32 * xs] | px[nmax] | py[nmax],
+// xs = nmax rounded up to odd (conflict-free column buffers, one per lane).
+__host__ __device__ inline size_t setup_doubles(int nmax)
+{
+    const size_t xs = (size_t)(nmax | 1);
+    return (size_t)nmax * (nmax + 1) / 2 + 32 * xs + 2 * (size_t)nmax;
+}
+
 __global__ void __launch_bounds__(kSetupWarps * 32)
     k_rasm_setup(const double* __restrict__ xy_s, const int32_t* __restrict__ ov_ptr,
                  const int32_t* __restrict__ ov_idx, const int32_t* __restrict__ core_of,
                  const int32_t* __restrict__ core_ptr, const int64_t* __restrict__ w_off, int64_t nsub, int nmax,
-                 int ncmax, int wpb, const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub,
+                 int wpb, const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub, int full,
                  double* __restrict__ W64, float* __restrict__ W32, int* __restrict__ status)
 {
     extern __shared__ double sm[];
@@ -32,38 +48,37 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
     if (warp >= wpb || sub >= nsub) return;
     const Prob& pr = prob[pid_sub[sub]];
     const double rc2 = pr.rc2, s = pr.s, knorm = pr.knorm;
-    const size_t per = (size_t)nmax * nmax + (size_t)ncmax * nmax + 2 * (size_t)nmax;
-    double* A = sm + per * warp;
-    double* X = A + (size_t)nmax * nmax;
-    double* xs = X + (size_t)ncmax * nmax;
-    double* ys = xs + nmax;
+    const int xstride = nmax | 1;
+    double* A = sm + setup_doubles(nmax) * warp;
+    double* X = A + (size_t)nmax * (nmax + 1) / 2;
+    double* px = X + 32 * (size_t)xstride;
+    double* py = px + nmax;
     __shared__ int cpos_all[kSetupWarps][kMaxSub];
     int* cpos = cpos_all[warp];
 
     const int b = ov_ptr[sub];
     const int n = ov_ptr[sub + 1] - b;
-    const int nc = core_ptr[sub + 1] - core_ptr[sub];
+    const int nc = full ? n : core_ptr[sub + 1] - core_ptr[sub];   // full: every overlap row
     if (n == 0) return;
     for (int a = lane; a < n; a += 32) {
         int p = ov_idx[b + a];
-        xs[a] = xy_s[2 * (int64_t)p];
-        ys[a] = xy_s[2 * (int64_t)p + 1];
+        px[a] = xy_s[2 * (int64_t)p];
+        py[a] = xy_s[2 * (int64_t)p + 1];
     }
-    // positions of the core entries inside the overlap list (ascending)
+    // positions of the kept rows inside the overlap list (ascending)
     if (lane == 0) {
         int q = 0;
         for (int a = 0; a < n; ++a)
-            if (core_of[ov_idx[b + a]] == (int32_t)sub) cpos[q++] = a;
+            if (full || core_of[ov_idx[b + a]] == (int32_t)sub) cpos[q++] = a;
     }
     __syncwarp();
     // A_i (lower triangle and diagonal), truncated exactly like A~
-    for (int t = lane; t < n * n; t += 32) {
-        int i = t / n, j = t % n;
-        if (j > i) continue;
-        double dx = __dsub_rn(xs[i], xs[j]), dy = __dsub_rn(ys[i], ys[j]);
-        double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        A[i * n + j] = (r2 <= rc2) ? exp(-r2 * s) * knorm : 0.0;
-    }
+    for (int i = 0; i < n; ++i)
+        for (int j = lane; j <= i; j += 32) {
+            double dx = __dsub_rn(px[i], px[j]), dy = __dsub_rn(py[i], py[j]);
+            double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            A[tri(i, j)] = (r2 <= rc2) ? exp(-r2 * s) * knorm : 0.0;
+        }
     __syncwarp();
     // right-looking Cholesky, lower triangle in place; a pivot below 1e-14 of
     // the diagonal k(0) counts as not positive definite (numerically singular,
@@ -71,16 +86,16 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
     bool ok = true;
     const double pivot_min = 1e-14 * knorm;
     for (int j = 0; j < n; ++j) {
-        double d = A[j * n + j];
+        double d = A[tri(j, j)];
         if (!(d > pivot_min)) { ok = false; d = 1.0; }
         double ljj = sqrt(d);
         __syncwarp();
-        for (int i = j + 1 + lane; i < n; i += 32) A[i * n + j] = A[i * n + j] / ljj;
-        if (lane == 0) A[j * n + j] = ljj;
+        for (int i = j + 1 + lane; i < n; i += 32) A[tri(i, j)] = A[tri(i, j)] / ljj;
+        if (lane == 0) A[tri(j, j)] = ljj;
         __syncwarp();
         for (int i = j + 1 + lane; i < n; i += 32) {
-            double lij = A[i * n + j];
-            for (int kk = j + 1; kk <= i; ++kk) A[i * n + kk] -= lij * A[kk * n + j];
+            double lij = A[tri(i, j)];
+            for (int kk = j + 1; kk <= i; ++kk) A[tri(i, kk)] -= lij * A[tri(kk, j)];
         }
         __syncwarp();
     }
@@ -88,32 +103,33 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
         if (lane == 0) atomicExch(status, RBF_ERR_NOT_SPD);
         return;
     }
-    // X[c][:] = A_i^{-1} e_{cpos[c]} (= row cpos[c] of A_i^{-1}, A_i symmetric);
-    // one right-hand side per lane, L read by all lanes in lockstep
+    // 32 kept rows at a time: lane c computes x = A_i^{-1} e_{cpos[c]} (= row
+    // cpos[c] of A_i^{-1}, A_i symmetric) in its own column buffer, L read by
+    // all lanes in lockstep, then the warp writes the chunk to W_i, stored
+    // column-major (W[off + a * nc + c] = x_c[a]: consecutive lanes, consecutive c)
+    const int64_t off = w_off[sub];
+    double* x = X + (size_t)lane * xstride;
     for (int c0 = 0; c0 < nc; c0 += 32) {
-        int c = c0 + lane;
-        bool act = c < nc;
-        int cp = act ? cpos[c] : 0;
-        double* x = X + (size_t)(act ? c : 0) * n;
+        const int c = c0 + lane;
+        const bool act = c < nc;
+        const int cp = act ? cpos[c] : 0;
         for (int i = 0; i < n; ++i) {                 // L y = e_cp
             double v = (i == cp) ? 1.0 : 0.0;
-            for (int kk = 0; kk < i; ++kk) v -= A[i * n + kk] * (act ? x[kk] : 0.0);
-            if (act) x[i] = v / A[i * n + i];
+            for (int kk = 0; kk < i; ++kk) v -= A[tri(i, kk)] * x[kk];
+            x[i] = v / A[tri(i, i)];
         }
         for (int i = n - 1; i >= 0; --i) {            // L^T x = y
-            double v = act ? x[i] : 0.0;
-            for (int kk = i + 1; kk < n; ++kk) v -= A[kk * n + i] * (act ? x[kk] : 0.0);
-            if (act) x[i] = v / A[i * n + i];
+            double v = x[i];
+            for (int kk = i + 1; kk < n; ++kk) v -= A[tri(kk, i)] * x[kk];
+            x[i] = v / A[tri(i, i)];
         }
+        if (act)
+            for (int a = 0; a < n; ++a) {
+                const double v = x[a];
+                if (W64) W64[off + (int64_t)a * nc + c] = v;
+                if (W32) W32[off + (int64_t)a * nc + c] = (float)v;
+            }
         __syncwarp();
-    }
-    // W_i column-major: W[off + a * nc + c] = X[c][a]
-    const int64_t off = w_off[sub];
-    for (int t = lane; t < n * nc; t += 32) {
-        int a = t / nc, c = t % nc;
-        double v = X[(size_t)c * n + a];
-        if (W64) W64[off + t] = v;
-        if (W32) W32[off + t] = (float)v;
     }
 }
 
@@ -154,20 +170,94 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void k_sizes(const int32_t* __restrict__ ov_ptr, const int32_t* __restrict__ core_ptr, int64_t nsub,
-                        int64_t* __restrict__ sizes)
+                        int full, int64_t* __restrict__ sizes)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nsub) sizes[s] = (int64_t)(ov_ptr[s + 1] - ov_ptr[s]) * (core_ptr[s + 1] - core_ptr[s]);
+    if (s >= nsub) return;
+    const int64_t n = ov_ptr[s + 1] - ov_ptr[s];
+    sizes[s] = n * (full ? n : (int64_t)(core_ptr[s + 1] - core_ptr[s]));
+}
+
+// Eq. asm: overlap entries of each point (CSR over points, entries ascending).
+__global__ void k_asm_count(const int32_t* __restrict__ ov_idx, int64_t tot, int32_t* __restrict__ cnt,
+                            int32_t* __restrict__ iota)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    iota[e] = (int32_t)e;
+    atomicAdd(&cnt[ov_idx[e]], 1);
+}
+
+__global__ void k_asm_fill(const int32_t* __restrict__ ov_idx, int64_t tot, const int32_t* __restrict__ tptr,
+                           int32_t* __restrict__ fill, int32_t* __restrict__ tidx)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    const int32_t p = ov_idx[e];
+    tidx[tptr[p] + atomicAdd(&fill[p], 1)] = (int32_t)e;
+}
+
+__global__ void k_asm_sort(const int32_t* __restrict__ tptr, int64_t n, int32_t* __restrict__ tidx)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int32_t* row = tidx + tptr[p];
+    const int32_t len = tptr[p + 1] - tptr[p];
+    for (int32_t a = 1; a < len; ++a) {
+        int32_t v = row[a], b = a - 1;
+        while (b >= 0 && row[b] > v) { row[b + 1] = row[b]; --b; }
+        row[b + 1] = v;
+    }
+}
+
+// z_p = sum of the subdomain results u_e of p's overlap entries, in entry order.
+template <class T>
+__global__ void k_asm_gather(const int32_t* __restrict__ tptr, const int32_t* __restrict__ tidx,
+                             const T* __restrict__ u, int64_t n, const int32_t* __restrict__ pid,
+                             const int32_t* __restrict__ active, T* __restrict__ z)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (active && !active[pid[p]]) return;
+    T acc = 0;
+    for (int32_t q = tptr[p]; q < tptr[p + 1]; ++q) acc += u[tidx[q]];
+    z[p] = acc;
 }
 
 }  // namespace
+
+rbf_status asm_lists(rbf_ctx* ctx, cudaStream_t st)
+{
+    const int64_t n = ctx->n, nsub = ctx->nsub;
+    int32_t tot32 = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&tot32, ctx->ov_ptr.p + nsub, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    const int64_t tot = tot32;
+    RBF_CHECK(ensure(ctx, ctx->asm_fill, n + 1));
+    RBF_CHECK(ensure(ctx, ctx->asm_tptr, n + 1));
+    RBF_CHECK(ensure(ctx, ctx->asm_tidx, tot));
+    RBF_CHECK(ensure(ctx, ctx->asm_iota, tot));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->asm_fill.p, 0, sizeof(int32_t) * (n + 1), st));
+    RBF_LAUNCH(ctx, k_asm_count, blocks_for(tot, 256), 256, 0, st, ctx->ov_idx.p, tot, ctx->asm_fill.p,
+               ctx->asm_iota.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, ctx->asm_fill.p, ctx->asm_tptr.p, n, st));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->asm_fill.p, 0, sizeof(int32_t) * (n + 1), st));
+    RBF_LAUNCH(ctx, k_asm_fill, blocks_for(tot, 256), 256, 0, st, ctx->ov_idx.p, tot, ctx->asm_tptr.p,
+               ctx->asm_fill.p, ctx->asm_tidx.p);
+    RBF_LAUNCH(ctx, k_asm_sort, blocks_for(n, 256), 256, 0, st, ctx->asm_tptr.p, n, ctx->asm_tidx.p);
+    RBF_CHECK(ensure(ctx, ctx->asm_u64, tot));
+    if (ctx->rasm_precision == RBF_FP32) RBF_CHECK(ensure(ctx, ctx->asm_u32, tot));
+    return RBF_OK;
+}
 
 rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
 {
     const int64_t nsub = ctx->nsub;
     RBF_CHECK(ensure(ctx, ctx->w_off, nsub + 1));
     RBF_CHECK(ensure(ctx, ctx->w_size, nsub + 1));
-    RBF_LAUNCH(ctx, k_sizes, blocks_for(nsub, 256), 256, 0, st, ctx->ov_ptr.p, ctx->core_ptr.p, nsub, ctx->w_size.p);
+    const int full = ctx->rasm_additive ? 1 : 0;
+    RBF_LAUNCH(ctx, k_sizes, blocks_for(nsub, 256), 256, 0, st, ctx->ov_ptr.p, ctx->core_ptr.p, nsub, full,
+               ctx->w_size.p);
     RBF_CHECK(exclusive_scan_i64(ctx, ctx->w_size.p, ctx->w_off.p, nsub, st));
     int64_t total = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&total, ctx->w_off.p + nsub, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -183,21 +273,20 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
         RBF_CHECK(ensure(ctx, ctx->W32, (size_t)total));
         W32 = ctx->W32.p;
     }
-    const int nmax = ctx->max_ov, ncmax = ctx->max_core;
+    const int nmax = ctx->max_ov;
     if (nmax == 0) return RBF_OK;
-    size_t per = ((size_t)nmax * nmax + (size_t)ncmax * nmax + 2 * (size_t)nmax) * sizeof(double);
+    const size_t per = setup_doubles(nmax) * sizeof(double);
     if (per > 200u * 1024u)
         return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
-                    "rbf_rasm_setup: a %d-point overlap list with %d core points needs %zu KB of shared memory", nmax,
-                    ncmax, per / 1024);
+                    "rbf_rasm_setup: a %d-point overlap list needs %zu KB of shared memory", nmax, per / 1024);
     // as many warps per block as fit in 200 KB of shared memory (at most kSetupWarps)
     int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, (200u * 1024u) / per));
     size_t smem = per * wpb;
     RBF_CUDA(ctx, cudaFuncSetAttribute(k_rasm_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_SETUP, st));
     RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nsub, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
-               ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, ncmax, wpb, ctx->prob.p,
-               ctx->pid_sub.p, W64, W32, ctx->status_dev.p);
+               ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, wpb, ctx->prob.p,
+               ctx->pid_sub.p, full, W64, W32, ctx->status_dev.p);
     RBF_CHECK(prof_end(ctx, RBF_PROF_RASM_SETUP, st));
     int status = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&status, ctx->status_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -210,23 +299,41 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
 rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
-    if (ctx->rasm_precision == RBF_FP64)
+    // Eq. asm: the GEMV writes every overlap row to the scratch list, then a gather
+    const bool add = ctx->rasm_additive;
+    const int32_t* rows_ptr = add ? ctx->ov_ptr.p : ctx->core_ptr.p;
+    const int32_t* rows_idx = add ? ctx->asm_iota.p : ctx->core_idx.p;
+    if (ctx->rasm_precision == RBF_FP64) {
+        double* out = add ? ctx->asm_u64.p : z;
         RBF_LAUNCH(ctx, (k_rasm_apply<double, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W64.p, ctx->nsub,
-                   ctx->pid_sub.p, ctx->active_mask, r, z);
-    else
+                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W64.p, ctx->nsub, ctx->pid_sub.p,
+                   ctx->active_mask, r, out);
+        if (add)
+            RBF_LAUNCH(ctx, k_asm_gather<double>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p,
+                       ctx->asm_tidx.p, (const double*)out, ctx->n, ctx->pid.p, ctx->active_mask, z);
+    } else {
+        double* out = add ? ctx->asm_u64.p : z;
         RBF_LAUNCH(ctx, (k_rasm_apply<float, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub,
-                   ctx->pid_sub.p, ctx->active_mask, r, z);
+                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W32.p, ctx->nsub, ctx->pid_sub.p,
+                   ctx->active_mask, r, out);
+        if (add)
+            RBF_LAUNCH(ctx, k_asm_gather<double>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p,
+                       ctx->asm_tidx.p, (const double*)out, ctx->n, ctx->pid.p, ctx->active_mask, z);
+    }
     return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
 }
 
 rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
+    const bool add = ctx->rasm_additive;
+    float* out = add ? ctx->asm_u32.p : z;
     RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p, ctx->ov_idx.p,
-               ctx->core_ptr.p, ctx->core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub, ctx->pid_sub.p,
-               ctx->active_mask, r, z);
+               add ? ctx->ov_ptr.p : ctx->core_ptr.p, add ? ctx->asm_iota.p : ctx->core_idx.p, ctx->w_off.p,
+               ctx->W32.p, ctx->nsub, ctx->pid_sub.p, ctx->active_mask, r, out);
+    if (add)
+        RBF_LAUNCH(ctx, k_asm_gather<float>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p, ctx->asm_tidx.p,
+                   (const float*)out, ctx->n, ctx->pid.p, ctx->active_mask, z);
     return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
 }
 

@@ -217,7 +217,7 @@ int64_t rbf_request_footprint(const rbf_request* r)
         }
         area = (x1 - x0) * (y1 - y0);
     }
-    const int cap = (r->rasm.max_sub_points > 0 && r->rasm.max_sub_points <= 128) ? r->rasm.max_sub_points : 128;
+    const int cap = (r->rasm.max_sub_points > 0 && r->rasm.max_sub_points <= 192) ? r->rasm.max_sub_points : 192;
     double n_ov = cap, n_core = 1.0;
     if (area > 0.0 && r->rasm.core_size > 0.0) {
         const double rho = n / area, B = r->rasm.core_size, D = B + 2.0 * std::max(r->rasm.overlap, 0.0);

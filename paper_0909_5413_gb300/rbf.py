@@ -28,7 +28,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
-            "rbf_request_footprint", "rbf_debug_kernel_pairs"]
+            "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -40,7 +40,7 @@ class RbfParams(C.Structure):
 
 class RbfRasmParams(C.Structure):
     _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("core_size", C.c_double), ("overlap", C.c_double),
-                ("max_sub_points", C.c_int), ("precision", C.c_int)]
+                ("max_sub_points", C.c_int), ("precision", C.c_int), ("additive", C.c_int)]
 
 
 class RbfSolveParams(C.Structure):
@@ -128,6 +128,7 @@ def load(path: str | None = None):
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
     L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
     L.rbf_debug_kernel_pairs.argtypes = [P, P, P, C.c_int64, P]
+    L.rbf_eval.argtypes = [P, P, C.c_int64, P, P, P]
     L.rbf_bin_batch.argtypes = [P, P, I64, C.c_int64, C.POINTER(RbfParams), P]
     L.rbf_rasm_setup_batch.argtypes = [P, C.POINTER(RbfRasmParams), P]
     L.rbf_solve_batch.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
@@ -195,6 +196,10 @@ def rbf_bin(ctx, xy_dev, n: int, params: RbfParams, stream=None) -> None:
 
 def rbf_matvec(ctx, w_dev, y_dev, precision: int = RBF_FP64, stream=None) -> None:
     _check(ctx, load().rbf_matvec(ctx, _ptr(w_dev), _ptr(y_dev), int(precision), _stream(stream)))
+
+
+def rbf_eval(ctx, xe_dev, m: int, w_dev, s_dev, stream=None) -> None:
+    _check(ctx, load().rbf_eval(ctx, _ptr(xe_dev), int(m), _ptr(w_dev), _ptr(s_dev), _stream(stream)))
 
 
 def rbf_matvec_noalloc(ctx, w_dev, y_dev, stream=None) -> None:
@@ -327,6 +332,7 @@ class SolverConfig:
     normalized: bool = False
     max_sub_points: int = 0
     factor_precision: int = RBF_FP64
+    additive: bool = False          # Eq. asm instead of Eq. rasm
     rtol: float = 1e-13
     restart: int = 30
     max_iters: int = 10000
@@ -339,7 +345,7 @@ class SolverConfig:
 
     def rasm(self) -> RbfRasmParams:
         return RbfRasmParams(self.x0, self.y0, self.core_size, self.overlap, self.max_sub_points,
-                             self.factor_precision)
+                             self.factor_precision, int(self.additive))
 
     def solve(self) -> RbfSolveParams:
         return RbfSolveParams(self.rtol, self.restart, self.max_iters, int(self.mixed), self.max_refine,

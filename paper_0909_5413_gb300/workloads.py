@@ -77,6 +77,11 @@ def rhs_franke(xy: np.ndarray) -> np.ndarray:
     return _franke_terms(xy[:, 0], xy[:, 1])
 
 
+def franke(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Franke's function at arbitrary points (x, y arrays)."""
+    return _franke_terms(x, y)
+
+
 def _franke_terms(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     t1 = 0.75 * np.exp(-0.25 * ((9 * x - 2) ** 2 + (9 * y - 2) ** 2))
     # Sec. 3.1 prints the second term's y part squared, -(9y+1)^2/10; that

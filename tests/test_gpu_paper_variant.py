@@ -1,0 +1,203 @@
+"""The paper-parameter variant on the GPU: subdomains sized in sigma units
+(B = 5 sigma, D = 1.9 B) on Franke's function over [0, 1]^2, the plain
+additive Schwarz preconditioner (Eq. asm) next to the restricted one
+(Eq. rasm), and evaluation of the interpolant at other points (rbf_eval),
+all against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0909_5413_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    from paper_0909_5413_gb300 import rbf as R
+    R.load()
+    return R
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def setup(rbf, p, additive=False, precision=0, **kw):
+    cfg = rbf.config_for(p, additive=additive, factor_precision=precision, **kw)
+    ctx = rbf.Context(0)
+    ctx.bin(dev(p.xy), cfg)
+    ctx.rasm_setup(cfg)
+    return ctx, cfg
+
+
+# ------------------------------------------------------------------ ASM
+
+@pytest.mark.parametrize("ring,tol", [(1, 1e-10), (2, 1e-8)])
+def test_asm_apply_matches_oracle(rbf, ring, tol):
+    p = W.lattice_problem(40, 0.8, seed=41, ring_points=ring)
+    ctx, _ = setup(rbf, p, additive=True)
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=True)
+    v = np.random.default_rng(8).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_rasm_apply(ctx.handle, dev(v), z)
+    assert rel_err(host(z), pr.rasm_apply(v)) <= tol
+    ctx.close()
+
+
+def test_asm_apply_fp32_inverses(rbf):
+    p = W.lattice_problem(32, 0.9, seed=42)
+    ctx, _ = setup(rbf, p, additive=True, precision=1)
+    pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=True)
+    v = np.random.default_rng(9).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_rasm_apply(ctx.handle, dev(v), z)
+    assert rel_err(host(z), pr.rasm_apply(v)) <= 1e-4
+    ctx.close()
+
+
+@pytest.mark.parametrize("ratio", [0.8, 0.9, 1.0])
+def test_paper_parameters_rasm_beats_asm(rbf, ratio):
+    """B = 5 sigma, D = 1.9 B, Franke's function: both preconditioners reach the
+    tolerance; the restricted one needs fewer GMRES steps (Sec. 2.2), and each
+    GPU count is within 3 of the oracle's GMRES on the same problem."""
+    p = W.unit_square_problem(ratio, sigma=0.02, seed=34)
+    it = {}
+    for additive in (False, True):
+        ctx, cfg = setup(rbf, p, additive=additive)
+        w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+        ctx.close()
+        assert st == 0 and info.relres <= 1e-13, info.as_dict()
+        pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap, additive=additive)
+        _, oinfo = pr.solve(p.f, max_iters=600)
+        assert abs(info.iters - oinfo.iters) <= 3, (additive, info.iters, oinfo.iters)
+        it[additive] = info.iters
+    assert it[False] < it[True], it
+    if ratio >= 0.9:
+        assert it[False] <= 25, it
+
+
+def test_paper_iterations_independent_of_n(rbf):
+    """Sec. 3.2: with h/sigma, B/sigma and D/sigma fixed, the step count does not
+    change with N (here N grows about 4x)."""
+    its = []
+    for sigma in (0.02, 0.01):
+        p = W.unit_square_problem(0.9, sigma=sigma, seed=35)
+        ctx, cfg = setup(rbf, p)
+        w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+        ctx.close()
+        assert st == 0
+        its.append(info.iters)
+    assert abs(its[0] - its[1]) <= 2, its
+
+
+def test_mixed_solve_with_asm(rbf):
+    p = W.lattice_problem(48, 0.85, seed=43)
+    ctx, cfg = setup(rbf, p, additive=True, precision=1, mixed=True)
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+    ctx.close()
+    assert st == 0 and info.relres <= 1e-13, info.as_dict()
+
+
+def test_batch_with_asm_matches_single(rbf):
+    probs = [W.lattice_problem(n, r, seed=50 + n, rhs="four_gaussians") for n, r in ((20, 0.9), (33, 0.85), (16, 1.0))]
+    xy, f, ptr, params, rasm = rbf.batch_arrays(probs)
+    for r in rasm:
+        r.additive = 1
+    ctx = rbf.Context(0)
+    rbf.rbf_bin_batch(ctx.handle, dev(xy), ptr, params)
+    rbf.rbf_rasm_setup_batch(ctx.handle, rasm)
+    w = torch.zeros(ptr[-1], dtype=torch.float64, device="cuda")
+    st, infos = rbf.rbf_solve_batch(ctx.handle, dev(f), w, rbf.RbfSolveParams(1e-13, 30, 5000, 0, 0, 0.0),
+                                    len(probs), check=False)
+    wb = host(w)
+    ctx.close()
+    assert st == 0
+    for b, p in enumerate(probs):
+        c1, cfg = setup(rbf, p, additive=True)
+        w1 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        c1.solve(dev(p.f), w1, cfg)
+        c1.close()
+        np.testing.assert_array_equal(host(w1), wb[ptr[b]:ptr[b + 1]])
+
+
+# ------------------------------------------------------------ evaluation
+
+def test_eval_matches_oracle_and_matvec(rbf):
+    p = W.lattice_problem(64, 0.8, seed=44)
+    ctx, cfg = setup(rbf, p)
+    rng = np.random.default_rng(10)
+    w = rng.standard_normal(p.n)
+    xe = np.concatenate([rng.uniform(-1.2, 1.2, (20000, 2)),       # inside and around the box
+                         np.array([[5.0, 5.0], [-1.0, -1.0], [1.0 + p.cutoff * 0.999, 0.0]])])
+    s = torch.empty(xe.shape[0], dtype=torch.float64, device="cuda")
+    rbf.rbf_eval(ctx.handle, dev(xe), xe.shape[0], dev(w), s)
+    got = host(s)
+    ref = O.eval_points(p.xy, w, xe, p.sigma, p.cutoff)
+    assert rel_err(got, ref) <= 1e-13
+    assert got[20000] == 0.0
+    # at the centres (user order) the interpolant is the matvec, bit for bit
+    s2 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_eval(ctx.handle, dev(p.xy), p.n, dev(w), s2)
+    rbf.rbf_matvec(ctx.handle, dev(w), y)
+    np.testing.assert_array_equal(host(s2), host(y))
+    ctx.close()
+
+
+def test_eval_reproduces_data_and_approximates_franke(rbf):
+    """After the solve, s(x_j) = f_j to the solve tolerance; on a finer lattice
+    inside the data the interpolant of Franke's function is close to it."""
+    p = W.unit_square_problem(0.9, sigma=0.02, seed=36)
+    ctx, cfg = setup(rbf, p)
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = ctx.solve(dev(p.f), w, cfg)
+    s = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_eval(ctx.handle, dev(p.xy), p.n, w, s)
+    assert rel_err(host(s), p.f) <= 1e-13
+    g = np.linspace(0.05, 0.95, 181)
+    gx, gy = np.meshgrid(g, g)
+    xe = np.stack([gx.ravel(), gy.ravel()], axis=1)
+    se = torch.empty(xe.shape[0], dtype=torch.float64, device="cuda")
+    rbf.rbf_eval(ctx.handle, dev(xe), xe.shape[0], w, se)
+    exact = W.franke(xe[:, 0], xe[:, 1])
+    err = np.abs(host(se) - exact).max() / np.abs(exact).max()
+    assert err < 1e-2, err
+    np.testing.assert_allclose(host(se), O.eval_points(p.xy, host(w), xe, p.sigma, p.cutoff), rtol=0,
+                               atol=1e-13 * np.abs(exact).max() * 100)
+    ctx.close()
+
+
+def test_eval_errors_and_edge_cases(rbf):
+    p = W.lattice_problem(16, 0.8, seed=45)
+    ctx = rbf.Context(0)
+    s = torch.empty(4, dtype=torch.float64, device="cuda")
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_eval(ctx.handle, dev(np.zeros((4, 2))), 4, w, s)
+    assert e.value.status == 8
+    rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(p.sigma, p.cutoff, 0.0, 0))
+    rbf.rbf_eval(ctx.handle, dev(np.zeros((4, 2))), 0, w, s)            # m = 0: nothing to do
+    bad = np.array([[0.0, 0.0], [np.nan, 0.0], [0.1, 0.1], [0.2, 0.2]])
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_eval(ctx.handle, dev(bad), 4, w, s)
+    assert e.value.status == 1
+    one = np.array([[0.05, -0.02]])
+    s1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    rbf.rbf_eval(ctx.handle, dev(one), 1, dev(np.ones(p.n)), s1)
+    assert abs(host(s1)[0] - O.eval_points(p.xy, np.ones(p.n), one, p.sigma, p.cutoff)[0]) <= 1e-13 * host(s1)[0]
+    ctx.close()

@@ -182,6 +182,12 @@ def test_subdomain_too_large_is_reported(rbf):
     with pytest.raises(rbf.RbfError) as e:
         rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, 8 * p.h, p.h, 64, 0))
     assert e.value.status == 5
+    # the default cap is the largest supported list, 192 points: 14 x 14 boxes exceed it
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, 12 * p.h, p.h, 0, 0))
+    assert e.value.status == 5
+    # 12 x 12 = 144 points (the paper's D = 1.9 B at h/sigma = 0.8) fit
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, 10 * p.h, p.h, 0, 0))
     ctx.close()
 
 
