@@ -61,6 +61,9 @@ WORKLOADS = {
                         "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians, one seed per problem"),
     "serve": (None, "requests with Poisson arrivals, N log-uniform in [1e3, 4e6] (jittered lattices on [-1,1]^2), "
                     "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians"),
+    "paper": (None, "Franke's function on a lattice over [0,1]^2, sigma = 0.001 (N about 1.0e6 to 1.6e6), "
+                    "subdomains B = 5 sigma, D = 1.9 B, h/sigma in {0.8, 0.9, 1.0}; RASM and ASM; "
+                    "interpolant evaluated onto a 2048 x 2048 lattice"),
 }
 
 
@@ -78,6 +81,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=64, help="requests of the serve workload")
     ap.add_argument("--slots", type=int, default=8, help="server slots (serve)")
     ap.add_argument("--rates", default="0.5,0.9", help="arrival rates swept, as fractions of the saturated rate")
+    ap.add_argument("--sigma", type=float, default=0.001, help="Gaussian width of the paper workload")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
@@ -814,14 +818,101 @@ def matvec_roofline(rbf, p, local) -> dict:
             "launches": n_mv, "note": f"largest request, N={p.n}"}
 
 
+# ------------------------------------------------- paper-parameter variant
+
+PAPER_METRIC = "RBF solve time at 1e-13 rel. residual, paper subdomain sizes (B = 5 sigma, D = 1.9 B)"
+
+
+def run_paper(args, ws, rank, local):
+    import torch
+
+    from paper_0909_5413_gb300 import rbf
+
+    torch.cuda.set_device(local)
+    g = np.linspace(0.0, 1.0, 2048)
+    gx, gy = np.meshgrid(g, g)
+    xe_h = np.ascontiguousarray(np.stack([gx.ravel(), gy.ravel()], axis=1))
+    xe = torch.from_numpy(xe_h).cuda()
+    exact = W.franke(xe_h[:, 0], xe_h[:, 1])
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    rows, times_all = [], []
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches = 0
+    for ratio in (0.8, 0.9, 1.0):
+        p = W.unit_square_problem(ratio, sigma=args.sigma, seed=W.DEFAULT_SEED)
+        xy = torch.from_numpy(p.xy).cuda()
+        f = torch.from_numpy(p.f).cuda()
+        row = {"h_over_sigma": ratio, "n_points": p.n}
+        for additive in (False, True):
+            cfg = rbf.config_for(p, additive=additive)
+            ctx = rbf.Context(local)
+            w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+
+            def step():
+                w.zero_()
+                ctx.bin(xy, cfg)
+                ctx.rasm_setup(cfg)
+                return ctx.solve(f, w, cfg, check=False)
+            for _ in range(args.warmup):
+                step()
+            l0 = ctx.launches
+            ts = []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, info = step()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            key = "asm" if additive else "rasm"
+            row[key] = {"ms": statistics.mean(ts), "iters": info.iters, "relres": info.relres, "status": st}
+            launches += ctx.launches - l0
+            if not additive:
+                times_all.append(statistics.mean(ts))
+                s = torch.empty(xe_h.shape[0], dtype=torch.float64, device="cuda")
+                rbf.rbf_eval(ctx.handle, xe, xe_h.shape[0], w, s)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rbf.rbf_eval(ctx.handle, xe, xe_h.shape[0], w, s)
+                e1.record()
+                torch.cuda.synchronize()
+                err = np.abs(s.cpu().numpy() - exact)
+                row["eval"] = {"points": int(xe_h.shape[0]), "ms": e0.elapsed_time(e1),
+                               "max_abs_error_vs_franke": float(err.max()),
+                               "rms_error_vs_franke": float(np.sqrt(np.mean(err ** 2)))}
+            ctx.close()
+        rows.append(row)
+    clk = clocks.stop()
+    if rank == 0:
+        v = times_all[1]   # h/sigma = 0.9, the paper's main case
+        out = {"metric": PAPER_METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "paper", "description": WORKLOADS["paper"][1], "sigma": args.sigma,
+                          "value_is": "RASM solve (bin + setup + GMRES) at h/sigma = 0.9",
+                          "l2": "flushed (256 MB write) before each timed step", "parallelism": "replicas"},
+               "rows": rows, "roofline": None, "cpu_baseline": None,
+               "e2e": None, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
-    kind = "batch" if args.workload.startswith("batch") else ("serve" if args.workload == "serve" else "one")
+    kind = "batch" if args.workload.startswith("batch") else (args.workload if args.workload in ("serve", "paper")
+                                                                else "one")
     if args.impl == "reference":
+        if kind == "paper":
+            print(json.dumps({"impl": "reference", "unavailable": "the paper workload is reported by the GPU arm only; "
+                              "its oracle comparison is in the tests"}), flush=True)
+            return
         {"batch": run_reference_batch, "serve": run_reference_serve, "one": run_reference}[kind](args, ws, rank)
         return
-    {"batch": run_batch, "serve": run_serve, "one": run_ours}[kind](args, ws, rank, local)
+    {"batch": run_batch, "serve": run_serve, "paper": run_paper, "one": run_ours}[kind](args, ws, rank, local)
 
 
 if __name__ == "__main__":

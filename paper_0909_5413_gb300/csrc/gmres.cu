@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kDotThreads)
            double* __restrict__ partial)
 {
     __shared__ double red[kDotThreads / 32];
+    __shared__ DF redf[kDotThreads / 32];
     const int k = (int)(blockIdx.x % (unsigned)nv);
     const int64_t chunk = blockIdx.x / (unsigned)nv;
     const int64_t base = chunk * kChunk + threadIdx.x;
@@ -56,7 +57,9 @@ __global__ void __launch_bounds__(kDotThreads)
             int64_t i = base + (int64_t)u * kDotThreads;
             if (i < n) df_add_prod(s, v[i], x[i]);
         }
-        a = (double)s.hi + (double)s.lo;
+        const double t = block_sum_df(s, redf);
+        if (threadIdx.x == 0) partial[chunk * 32 + k] = t;
+        return;
     } else {
 #pragma unroll
         for (int u = 0; u < kChunkPerThread; ++u) {
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(kDotThreads)
     __shared__ double cf[kMaxRestart + 1];
     __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
     __shared__ double red[kDotThreads / 32];
+    __shared__ DF redf[kDotThreads / 32];
     if (threadIdx.x < (unsigned)nv) {
         double c = coef[threadIdx.x];
         cf[threadIdx.x] = c;
@@ -122,7 +126,11 @@ __global__ void __launch_bounds__(kDotThreads)
                 if (NORM) df_add_prod(s, xs, xs);
             }
         }
-        a = (double)s.hi + (double)s.lo;
+        if (NORM) {
+            const double t = block_sum_df(s, redf);
+            if (threadIdx.x == 0) partial[chunk * 32] = t;
+        }
+        return;
     } else {
         // vector index outermost, the thread's 16 elements innermost: 16 independent loads in flight
         double xl[kChunkPerThread];
@@ -315,14 +323,14 @@ __global__ void __launch_bounds__(kDotThreads)
     k_inner_residual(const float* __restrict__ b, const float* __restrict__ t, float* __restrict__ r, int64_t n,
                      double* __restrict__ partial)
 {
-    __shared__ double red[kDotThreads / 32];
+    __shared__ DF red[kDotThreads / 32];
     DF s{0.f, 0.f};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float v = b[i] - t[i];
         r[i] = v;
         df_add_prod(s, v, v);
     }
-    double tot = block_sum((double)s.hi + (double)s.lo, red);
+    double tot = block_sum_df(s, red);
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 32] = tot;
 }
 

@@ -25,7 +25,7 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float
 
 namespace {
 
-constexpr int kBPer = 16;                       // elements per thread
+constexpr int kBPer = 16;                       // elements per thread (the single solver's chunking)
 constexpr int kBChunk = kDotThreads * kBPer;    // elements per chunk
 
 enum BField { F_H1 = 0, F_H2 = 1, F_NRM2 = 2, F_BETA2 = 3, F_FNORM2 = 4 };
@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kDotThreads)
             const int32_t* __restrict__ active, double* __restrict__ partial)
 {
     __shared__ double red[kDotThreads / 32];
+    __shared__ DF redf[kDotThreads / 32];
     const int k = (int)(blockIdx.x % (unsigned)nv);
     const int64_t c = blockIdx.x / (unsigned)nv;
     if (!active[C.pid[c]]) {
@@ -72,7 +73,9 @@ __global__ void __launch_bounds__(kDotThreads)
             int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
             if (i < e) df_add_prod(s, v[i], x[i]);
         }
-        a = (double)s.hi + (double)s.lo;
+        const double t = block_sum_df(s, redf);
+        if (threadIdx.x == 0) partial[c * 32 + k] = t;
+        return;
     } else {
 #pragma unroll
         for (int u = 0; u < kBPer; ++u) {
@@ -94,6 +97,7 @@ __global__ void __launch_bounds__(kDotThreads)
     __shared__ double cf[kMaxRestart + 1];
     __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
     __shared__ double red[kDotThreads / 32];
+    __shared__ DF redf[kDotThreads / 32];
     const int64_t c = blockIdx.x;
     const int pb = C.pid[c];
     if (!active[pb]) {
@@ -142,7 +146,11 @@ __global__ void __launch_bounds__(kDotThreads)
                 if (NORM) df_add_prod(s, xs, xs);
             }
         }
-        a = (double)s.hi + (double)s.lo;
+        if (NORM) {
+            const double t = block_sum_df(s, redf);
+            if (threadIdx.x == 0) partial[c * 32] = t;
+        }
+        return;
     } else {
         double xl[kBPer];
 #pragma unroll

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
         y[p] = (((PART[t] + PART[kMvThreads + t]) + PART[2 * kMvThreads + t]) + PART[3 * kMvThreads + t]) * knorm;
 }
 
-constexpr int kMv32Stage = 3072;   // sources staged per pass (even; 36 KB of static shared memory)
+constexpr int kMv32Stage = 1536;   // sources staged per pass (even; 18 KB of static shared memory)
 
 // FP32 matvec for the inner solves of the mixed form: block per (cell, 128
 // targets), sources staged in shared memory as FP32 offsets from the target

@@ -44,6 +44,34 @@ __device__ __forceinline__ void df_add_prod(DF& s, float a, float b)
     df_add(s, h, r);
 }
 
+// a += b for two double-float values: TwoSum of the high parts, low parts and
+// the rounding error added (the sum keeps about 2 x 24 bits).
+__device__ __forceinline__ void df_merge(DF& a, float bh, float bl)
+{
+    df_add(a, bh, bl);
+}
+
+// Block sum of one double-float value per thread, carried in double-float on
+// the FP32 pipe through the shuffle tree and across warps (fixed order), and
+// converted to FP64 once, by thread 0 (the only thread that gets the result).
+__device__ __forceinline__ double block_sum_df(DF s, DF* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 16; d > 0; d >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, s.hi, d), ol = __shfl_xor_sync(0xffffffffu, s.lo, d);
+        df_merge(s, oh, ol);
+    }
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+        DF t = red[0];
+        for (int w = 1; w < kDotThreads / 32; ++w) df_merge(t, red[w].hi, red[w].lo);
+        out = (double)t.hi + (double)t.lo;
+    }
+    return out;
+}
+
 // Sum of one value per thread over a block of kDotThreads threads, returned
 // to thread 0 (fixed order: shuffle tree within warps, warps in order).
 __device__ __forceinline__ double block_sum(double a, double* red)
