@@ -39,19 +39,62 @@ from paper_0909_5413_gb300 import workloads as W  # noqa: E402
 METRIC = "RBF solve time at 1e-13 rel. residual (GMRES+RASM)"
 UNIT = "ms"
 
-# Algorithmic FP64 flops of one in-cutoff pair in the FP64 matvec (FMA = 2):
-# dx, dy (2); r2 = dx*dx + dy*dy (3); t = r2 * s (1); exp(-t): rounding FMA +
-# subtract + two reduction FMAs + five polynomial FMAs + table multiply (18);
-# accumulate FMA (2).
+# The FP64 matvec's kernel value is computed on the integer pipes (fixed-point
+# exp), so its bound is the SM's ALU pipe: peak from unit counts and clocks,
+# 152 SMs x 4 partitions x 16 lanes x 2.07 GHz = 20.1 T lane-ops/s. One ncu
+# capture of this revision (profiles/matvec_f64_lattice1024.md) measured 87.4
+# ALU lane-ops per in-cutoff pair, which puts the ALU ceiling at 230 G pairs/s;
+# the roofline fraction is live pairs/s over that ceiling.
+ALU_PEAK_LANE_OPS = 152 * 4 * 16 * 2.07e9
+MATVEC_F64_REV = "fixed-point-v3"
+MATVEC_F64_ALU_OPS_PER_PAIR = {"fixed-point-v3": 87.4}
+MATVEC_F64_TRAFFIC = {"fixed-point-v3": 37_974_016}   # lattice1024, dram read + write per launch (ncu)
+# The FP64 view, for comparison: 26 FP64-equivalent flops per pair (dx, dy 2; r2 3;
+# argument 1; exp 18; accumulate 2) against the FP64 ALU peak 152 x 2 DFMA/clk x 2 x 2.07 GHz.
 FLOPS_PER_PAIR_F64 = 26
-# FP64 peak for plain (non-tensor) arithmetic: 152 SMs x 2 FP64 FMA/clk x 2 flops
-# x 2.07 GHz (matches the 1.25 TFLOP/s nominal figure for GB300).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP64 FMA rate of a register-only FMA loop on the same part (0.506 T FMA/s).
-FP64_MEASURED_TFLOPS = 1.012
-# DRAM bytes per launch of the FP64 matvec from ncu (profiles/), per kernel revision.
-MATVEC_F64_REV = "cellblock-mask-v2"
-MATVEC_F64_TRAFFIC = {"thread-per-target-v1": 29_474_008}   # lattice1024, dram read + write
+
+
+# The FP32 matvec (inner solves of the mixed form) evaluates every staged
+# candidate pair (no cutoff mask); ncu measured 6.55 issued lane-instructions
+# per candidate (profiles/mixed_kernels_lattice1024.md), so the SM issue rate,
+# 152 x 4 partitions x 32 lanes x 2.07 GHz = 40.3 T lane-instr/s, caps it at
+# 6.15 T candidates/s.
+ISSUE_PEAK_LANE_INSTR = 152 * 4 * 32 * 2.07e9
+MATVEC_F32_INSTR_PER_CANDIDATE = 6.55
+
+
+def candidate_pairs(rbf, h) -> int:
+    """Source-target pairs the FP32 matvec evaluates: for every cell, its points
+    times the points of its (2k+1)^2 stencil (k = 1 for cells of side r_c)."""
+    import torch
+    ncx, ncy, _ = rbf.rbf_get_grid(h)
+    cs = torch.empty(ncx * ncy + 1, dtype=torch.int32, device="cuda")
+    rbf.rbf_get_bins(h, None, cs)
+    cnt = np.diff(cs.cpu().numpy().astype(np.int64)).reshape(ncy, ncx)
+    pad = np.pad(cnt, 1)
+    win = sum(pad[1 + dy:1 + dy + ncy, 1 + dx:1 + dx + ncx] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    return int((cnt * win).sum())
+
+
+def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, note: str = "") -> dict:
+    """Roofline object of the FP64 matvec from its in-cutoff pair count and
+    CUDA-event launch time."""
+    rate = pairs / avg_s
+    ops = MATVEC_F64_ALU_OPS_PER_PAIR[MATVEC_F64_REV]
+    peak = ALU_PEAK_LANE_OPS / ops
+    out = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+           "frac": rate / peak, "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if traffic else None,
+           "peak_note": ("ALU pipe 152 SMs x 4 x 16 lanes x 2.07 GHz = 20.1 T lane-ops/s over "
+                         f"{ops} ALU lane-ops per in-cutoff pair (ncu, this revision)"),
+           "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
+           "launches": launches, "algorithmic_bytes_per_launch": None,
+           "fp64_equivalent": {"tflops": pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                               "flops_per_pair": FLOPS_PER_PAIR_F64}}
+    if note:
+        out["note"] = note
+    return out
+
 
 WORKLOADS = {
     "lattice64": (W.config_small, "64x64 jittered lattice on [-1,1]^2 (N=4,096)"),
@@ -298,21 +341,17 @@ def run_ours(args, ws, rank, local):
     if n_mv:
         avg_s = t_mv / n_mv / 1e3
         if mode == "f64":
-            achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
-            roofline = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                        "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV),
-                        "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
-                        "peak_measured": FP64_MEASURED_TFLOPS,
-                        "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
-                        "kernel_rev": MATVEC_F64_REV,
-                        "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR_F64,
-                        "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
-                        "pairs_per_s": pairs / avg_s}
+            roofline = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=(name == "lattice1024"))
+            roofline["algorithmic_bytes_per_launch"] = 32 * p.n
         else:
-            roofline = {"kernel": "k_matvec_f32", "bound": "alu", "achieved": pairs / avg_s / 1e12, "peak": None,
-                        "unit": "Tpairs/s", "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3,
-                        "launches": n_mv}
+            cand = candidate_pairs(rbf, h)
+            peak = ISSUE_PEAK_LANE_INSTR / MATVEC_F32_INSTR_PER_CANDIDATE
+            roofline = {"kernel": "k_matvec_f32v2", "bound": "alu", "achieved": cand / avg_s / 1e12,
+                        "peak": peak / 1e12, "unit": "Tcandidate/s", "frac": cand / avg_s / peak,
+                        "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
+                        "candidates_per_launch": cand, "in_cutoff_pairs_per_launch": pairs,
+                        "peak_note": ("SM issue rate 152 x 4 x 32 lanes x 2.07 GHz = 40.3 T lane-instr/s over "
+                                      f"{MATVEC_F32_INSTR_PER_CANDIDATE} lane-instr per candidate (ncu)")}
     breakdown = {nm: {"launches": prof[k][0], "ms": round(prof[k][1], 3)} for nm, k in
                  (("matvec_f64", 0), ("matvec_f32", 1), ("rasm_apply", 2), ("orthogonalisation", 3),
                   ("rasm_setup", 4), ("binning", 5))}
@@ -561,13 +600,8 @@ def run_batch(args, ws, rank, local):
     rbf.rbf_profile_enable(h, False)
     pairs = rbf.rbf_count_neighbors(h)
     avg_s = t_mv / max(n_mv, 1) / 1e3
-    achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
-    roofline = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
-                "peak_measured": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
-                "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
-                "launches": n_mv, "note": "all problems of the batch in one launch"}
+    roofline = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=False, note="all problems of the batch in one launch")
+    roofline["algorithmic_bytes_per_launch"] = 32 * ntot
 
     # the other precision, batched
     extra = None
@@ -809,13 +843,9 @@ def matvec_roofline(rbf, p, local) -> dict:
     pairs = rbf.rbf_count_neighbors(h)
     ctx.close()
     avg_s = t_mv / max(n_mv, 1) / 1e3
-    achieved = pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12
-    return {"kernel": "k_matvec_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (recipe counts/clocks)",
-            "peak_measured": FP64_MEASURED_TFLOPS, "frac_of_measured": achieved / FP64_MEASURED_TFLOPS,
-            "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
-            "launches": n_mv, "note": f"largest request, N={p.n}"}
+    out = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=False, note=f"largest request, N={p.n}")
+    out["algorithmic_bytes_per_launch"] = 32 * p.n
+    return out
 
 
 # ------------------------------------------------- paper-parameter variant
