@@ -27,20 +27,23 @@ constexpr int kSetupWarps = 4;
 // Packed lower triangle: row i starts at i (i + 1) / 2.
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// Shared layout per warp (doubles): L[nmax (nmax + 1) / 2] | X[32 * xs] | px[nmax] | py[nmax],
-// xs = nmax rounded up to odd (conflict-free column buffers, one per lane).
+// Shared layout per warp (8-byte words): L[nmax (nmax + 1) / 2] | X[32 * xs] | px | py | pxf | pyf |
+// dinv (nmax each), xs = nmax rounded up to odd (conflict-free column buffers, one per lane).
 __host__ __device__ inline size_t setup_doubles(int nmax)
 {
     const size_t xs = (size_t)(nmax | 1);
-    return (size_t)nmax * (nmax + 1) / 2 + 32 * xs + 2 * (size_t)nmax;
+    return (size_t)nmax * (nmax + 1) / 2 + 32 * xs + 5 * (size_t)nmax;
 }
+
+constexpr size_t kSetupSmemMax = 216u * 1024u;   // per warp (the block also holds cpos and the driver's 1 KB)
 
 __global__ void __launch_bounds__(kSetupWarps * 32)
     k_rasm_setup(const double* __restrict__ xy_s, const int32_t* __restrict__ ov_ptr,
                  const int32_t* __restrict__ ov_idx, const int32_t* __restrict__ core_of,
                  const int32_t* __restrict__ core_ptr, const int64_t* __restrict__ w_off, int64_t nsub, int nmax,
                  int wpb, const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub, int full,
-                 double* __restrict__ W64, float* __restrict__ W32, int* __restrict__ status)
+                 const unsigned long long* __restrict__ fxtab, double* __restrict__ W64, float* __restrict__ W32,
+                 int* __restrict__ status)
 {
     extern __shared__ double sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -53,6 +56,12 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
     double* X = A + (size_t)nmax * (nmax + 1) / 2;
     double* px = X + 32 * (size_t)xstride;
     double* py = px + nmax;
+    long long* pxf = (long long*)(py + nmax);
+    long long* pyf = pxf + nmax;
+    double* dinv = (double*)(pyf + nmax);
+    const double fxs = pr.fx_scale;
+    const int sh = pr.fx_sh, F = pr.fx_F;
+    const unsigned long long M = pr.fx_M;
     __shared__ int cpos_all[kSetupWarps][kMaxSub];
     int* cpos = cpos_all[warp];
 
@@ -64,6 +73,8 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
         int p = ov_idx[b + a];
         px[a] = xy_s[2 * (int64_t)p];
         py[a] = xy_s[2 * (int64_t)p + 1];
+        pxf[a] = fx_coord(px[a], fxs, sh);
+        pyf[a] = fx_coord(py[a], fxs, sh);
     }
     // positions of the kept rows inside the overlap list (ascending)
     if (lane == 0) {
@@ -72,12 +83,21 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
             if (full || core_of[ov_idx[b + a]] == (int32_t)sub) cpos[q++] = a;
     }
     __syncwarp();
-    // A_i (lower triangle and diagonal), truncated exactly like A~
+    // A_i (lower triangle and diagonal): the entries of A~ itself, truncated by
+    // the same FP64 pair test and valued by the same fixed-point evaluation as
+    // the FP64 matvec, so A_i = R_i A~ R_i^T holds for the operator the GPU applies
+    (void)s;
     for (int i = 0; i < n; ++i)
         for (int j = lane; j <= i; j += 32) {
             double dx = __dsub_rn(px[i], px[j]), dy = __dsub_rn(py[i], py[j]);
             double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            A[tri(i, j)] = (r2 <= rc2) ? exp(-r2 * s) * knorm : 0.0;
+            double v = 0.0;
+            if (r2 <= rc2) {
+                const long long du = (long long)((unsigned long long)pxf[i] - (unsigned long long)pxf[j]);
+                const long long dv = (long long)((unsigned long long)pyf[i] - (unsigned long long)pyf[j]);
+                v = kernel_fx(du, dv, F, M, fxtab, fxtab + kFxTab) * knorm;
+            }
+            A[tri(i, j)] = v;
         }
     __syncwarp();
     // right-looking Cholesky, lower triangle in place; a pivot below 1e-14 of
@@ -88,10 +108,13 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
     for (int j = 0; j < n; ++j) {
         double d = A[tri(j, j)];
         if (!(d > pivot_min)) { ok = false; d = 1.0; }
-        double ljj = sqrt(d);
+        const double ljj = sqrt(d), inv = 1.0 / ljj;
         __syncwarp();
-        for (int i = j + 1 + lane; i < n; i += 32) A[tri(i, j)] = A[tri(i, j)] / ljj;
-        if (lane == 0) A[tri(j, j)] = ljj;
+        for (int i = j + 1 + lane; i < n; i += 32) A[tri(i, j)] = A[tri(i, j)] * inv;
+        if (lane == 0) {
+            A[tri(j, j)] = ljj;
+            dinv[j] = inv;
+        }
         __syncwarp();
         for (int i = j + 1 + lane; i < n; i += 32) {
             double lij = A[tri(i, j)];
@@ -116,12 +139,12 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
         for (int i = 0; i < n; ++i) {                 // L y = e_cp
             double v = (i == cp) ? 1.0 : 0.0;
             for (int kk = 0; kk < i; ++kk) v -= A[tri(i, kk)] * x[kk];
-            x[i] = v / A[tri(i, i)];
+            x[i] = v * dinv[i];
         }
         for (int i = n - 1; i >= 0; --i) {            // L^T x = y
             double v = x[i];
             for (int kk = i + 1; kk < n; ++kk) v -= A[tri(kk, i)] * x[kk];
-            x[i] = v / A[tri(i, i)];
+            x[i] = v * dinv[i];
         }
         if (act)
             for (int a = 0; a < n; ++a) {
@@ -276,17 +299,17 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
     const int nmax = ctx->max_ov;
     if (nmax == 0) return RBF_OK;
     const size_t per = setup_doubles(nmax) * sizeof(double);
-    if (per > 200u * 1024u)
+    if (per > kSetupSmemMax)
         return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
                     "rbf_rasm_setup: a %d-point overlap list needs %zu KB of shared memory", nmax, per / 1024);
-    // as many warps per block as fit in 200 KB of shared memory (at most kSetupWarps)
-    int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, (200u * 1024u) / per));
+    // as many warps per block as fit in kSetupSmemMax of shared memory (at most kSetupWarps)
+    int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, kSetupSmemMax / per));
     size_t smem = per * wpb;
     RBF_CUDA(ctx, cudaFuncSetAttribute(k_rasm_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_SETUP, st));
     RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nsub, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
                ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, wpb, ctx->prob.p,
-               ctx->pid_sub.p, full, W64, W32, ctx->status_dev.p);
+               ctx->pid_sub.p, full, ctx->fxtab.p, W64, W32, ctx->status_dev.p);
     RBF_CHECK(prof_end(ctx, RBF_PROF_RASM_SETUP, st));
     int status = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&status, ctx->status_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
