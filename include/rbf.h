@@ -57,6 +57,8 @@ typedef struct {
     double cutoff;     /* r_c > 0; pairs with r2 > r_c^2 are dropped */
     double cell_size;  /* cell side c of the cell list; <= 0 selects c = r_c */
     int normalized;    /* 1: multiply the kernel by 1/(2 pi sigma^2) (Sec. 2.3) */
+    int tile_f64;      /* targets per block of the FP64 matvec: 32, 64 or 128 (0 = 128) */
+    int tile_f32;      /* targets per block of the FP32 matvec: 32, 64 or 128 (0 = 128) */
 } rbf_params;
 
 /* Subdomain boxes (Sec. 2.2, Sec. 3.1): core box (bx, by) covers
@@ -200,6 +202,22 @@ rbf_status rbf_rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params_host
  * complete. */
 rbf_status rbf_solve_batch(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf_solve_params* params,
                            rbf_solve_info* info_host, rbf_stream stream);
+
+/* ---- autotuning of the cell size and the matvec tiles ----
+ *
+ * No counterpart in the paper. Bins the points with each candidate cell side
+ * c in {r_c, r_c/2, r_c/3} (times base->cell_size / r_c when that is set, as a
+ * base) and times the FP64 and FP32 matvecs with each tile (32, 64, 128
+ * targets per block) on the device (CUDA events, the best of 3 launches
+ * each); the score of a candidate is w_f64 * t_f64 + w_f32 * t_f32 (for a
+ * plain FP64 solve w_f32 = 0; for the mixed form about 1 FP64 matvec per 26
+ * FP32 ones). Writes the fastest setting to *best (a copy of *base with
+ * cell_size, tile_f64 and tile_f32 set) and its score in ms to *score_ms
+ * (optional), and leaves the context binned with it. Results of the matvec do
+ * not depend on the tile; they depend on the cell size only through the
+ * summation order (within the matvec tolerance). Errors as rbf_bin. */
+rbf_status rbf_tune(rbf_ctx* ctx, const double* xy_dev, int64_t n, const rbf_params* base, double w_f64,
+                    double w_f32, rbf_params* best, double* score_ms, rbf_stream stream);
 
 /* ---- serving: independent requests admitted while others run ----
  *

@@ -200,22 +200,39 @@ __global__ void k_local_coords(const double* __restrict__ xy_s, const int32_t* _
     loc[2 * p + 1] = (float)((xy_s[2 * p + 1] - oy) * (double)P.a_loc);
 }
 
-// Matvec work items: cell c with m points gives ceil(m / 128) items (c, 128 q).
-__global__ void k_work_count(const int32_t* __restrict__ cell_start, int64_t ncell, int32_t* __restrict__ cnt)
+// Matvec work items: cell c with m points gives ceil(m / T) items (c, T q).
+__global__ void k_work_count(const int32_t* __restrict__ cell_start, int64_t ncell, int tile,
+                             int32_t* __restrict__ cnt)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell) cnt[c] = (cell_start[c + 1] - cell_start[c] + 127) / 128;
+    if (c < ncell) cnt[c] = (cell_start[c + 1] - cell_start[c] + tile - 1) / tile;
 }
 
 __global__ void k_work_fill(const int32_t* __restrict__ cnt, const int32_t* __restrict__ off, int64_t ncell,
-                            int32_t* __restrict__ work)
+                            int tile, int32_t* __restrict__ work)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     for (int q = 0; q < cnt[c]; ++q) {
         work[2 * (off[c] + q)] = (int32_t)c;
-        work[2 * (off[c] + q) + 1] = 128 * q;
+        work[2 * (off[c] + q) + 1] = tile * q;
     }
+}
+
+// Sources in the (2k+1)^2 stencil of each cell (what the matvec stages for it).
+__global__ void k_stencil_count(const int32_t* __restrict__ cell_start, const Prob* __restrict__ prob,
+                                const int32_t* __restrict__ pid_cell, int64_t ncell, int32_t* __restrict__ out)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const Prob& P = prob[pid_cell[c]];
+    const int64_t lc = c - P.cellbase, cx = lc % P.ncx, cy = lc / P.ncx;
+    const int64_t x0 = max(cx - P.k, (int64_t)0), x1 = min(cx + P.k, P.ncx - 1);
+    const int64_t y0 = max(cy - P.k, (int64_t)0), y1 = min(cy + P.k, P.ncy - 1);
+    int64_t s = 0;
+    for (int64_t yy = y0; yy <= y1; ++yy)
+        s += cell_start[P.cellbase + yy * P.ncx + x1 + 1] - cell_start[P.cellbase + yy * P.ncx + x0];
+    out[c] = (int32_t)min(s, (int64_t)0x7fffffff);
 }
 
 __global__ void k_permute_to_sorted(const double* __restrict__ user, const int32_t* __restrict__ perm, int64_t n,
@@ -306,6 +323,22 @@ __global__ void k_widen_i32_i64(const int32_t* __restrict__ in, int64_t n, int64
 
 }  // namespace
 
+// Work items (cell, first target) of tile T over cells with the given starts.
+rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int tile, DevArray<int32_t>& work,
+                      int64_t* nwork_out, cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, cell_start, ncell, tile, ctx->mv_wcnt.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell, st));
+    int32_t nwork = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&nwork, ctx->mv_woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *nwork_out = nwork;
+    RBF_CHECK(ensure(ctx, work, 2 * (size_t)std::max<int32_t>(nwork, 1)));
+    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell, tile,
+               work.p);
+    return RBF_OK;
+}
+
 // Bins all problems of ctx->prob_h (kernel parameters and point ranges filled
 // in; grids are set here from the bounding boxes).
 rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
@@ -392,15 +425,14 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
                ctx->pid.p, ctx->loc32.p);
     RBF_CHECK(ensure(ctx, ctx->mv_wcnt, ncell + 1));
     RBF_CHECK(ensure(ctx, ctx->mv_woff, ncell + 1));
-    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell, ctx->mv_wcnt.p);
-    RBF_CHECK(exclusive_scan_i32(ctx, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell, st));
-    int32_t nwork = 0;
-    RBF_CUDA(ctx, cudaMemcpyAsync(&nwork, ctx->mv_woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    RBF_CUDA(ctx, cudaStreamSynchronize(st));
-    ctx->n_work = nwork;
-    RBF_CHECK(ensure(ctx, ctx->mv_work, 2 * (size_t)std::max<int32_t>(nwork, 1)));
-    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, ctx->mv_wcnt.p, ctx->mv_woff.p, ncell,
-               ctx->mv_work.p);
+    RBF_CHECK(build_work(ctx, ctx->cell_start.p, ncell, ctx->tile64, ctx->mv_work, &ctx->n_work, st));
+    RBF_CHECK(build_work(ctx, ctx->cell_start.p, ncell, ctx->tile32, ctx->mv_work32, &ctx->n_work32, st));
+    // the largest stencil any cell stages
+    RBF_LAUNCH(ctx, k_stencil_count, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ctx->prob.p,
+               ctx->pid_cell.p, ncell, ctx->mv_wcnt.p);
+    int32_t smax = 0;
+    RBF_CHECK(reduce_max_i32(ctx, ctx->mv_wcnt.p, ncell, &smax, st));
+    ctx->stage_max = smax;
     RBF_CHECK(matvec_prepare(ctx));
     return prof_end(ctx, RBF_PROF_BIN, st);
 }
@@ -478,7 +510,7 @@ rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t s
                E.iperm.p, E.cell_s.p);
     RBF_LAUNCH(ctx, k_local_coords, blocks_for(m, 256), 256, 0, st, E.xy_s.p, E.cell_s.p, m, ctx->prob.p, E.pid.p,
                E.loc.p);
-    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, E.cell_start.p, ncell, E.wcnt.p);
+    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, E.cell_start.p, ncell, ctx->tile64, E.wcnt.p);
     RBF_CHECK(exclusive_scan_i32(ctx, E.wcnt.p, E.woff.p, ncell, st));
     int32_t hv[2] = {0, 0};
     RBF_CUDA(ctx, cudaMemcpyAsync(&hv[0], E.woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -488,7 +520,8 @@ rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t s
     E.m = m;
     E.nwork = hv[0];
     RBF_CHECK(ensure(ctx, E.work, 2 * (size_t)std::max<int32_t>(hv[0], 1)));
-    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, E.wcnt.p, E.woff.p, ncell, E.work.p);
+    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, E.wcnt.p, E.woff.p, ncell, ctx->tile64,
+               E.work.p);
     return RBF_OK;
 }
 

@@ -330,6 +330,13 @@ static rbf_status bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* p
             return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: problem %lld has no points", (long long)b);
         RBF_CHECK(init_prob(ctx, ctx->prob_h[b], &params[b], ptr[b], ptr[b + 1]));
     }
+    for (int which = 0; which < 2; ++which) {
+        const int t = which == 0 ? params[0].tile_f64 : params[0].tile_f32;
+        if (t != 0 && t != 32 && t != 64 && t != 128)
+            return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_bin: tiles must be 0, 32, 64 or 128 (got %d)", t);
+    }
+    ctx->tile64 = params[0].tile_f64 > 0 ? params[0].tile_f64 : 128;
+    ctx->tile32 = params[0].tile_f32 > 0 ? params[0].tile_f32 : 128;
     ctx->nprob = nprob;
     ctx->n = n;
     const Prob& q = ctx->prob_h[0];

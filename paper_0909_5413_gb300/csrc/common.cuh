@@ -117,8 +117,11 @@ struct rbf_ctx {
     rbf::DevArray<double> xy_s;    // sorted coordinates, interleaved (x, y)
     rbf::DevArray<double> bbox_part, bbox_dev;
     rbf::DevArray<float> loc32;    // FP32 cell-local offsets scaled by sqrt(log2(e) s), interleaved
-    rbf::DevArray<int32_t> mv_work, mv_wcnt, mv_woff;   // matvec work items (cell, first target) and their scan
-    int64_t n_work = 0;
+    rbf::DevArray<int32_t> mv_work, mv_wcnt, mv_woff;   // FP64 matvec work items (cell, first target), scan
+    rbf::DevArray<int32_t> mv_work32;                    // FP32 matvec work items
+    int64_t n_work = 0, n_work32 = 0;
+    int tile64 = 128, tile32 = 128;   // targets per block of the FP64 / FP32 matvec
+    int stage_max = 0;                // largest stencil source count of any cell (matvec staging)
     rbf::DevArray<double> exp2048; // 2^(-j/2048), j < 2048
     rbf::DevArray<unsigned long long> fxtab;   // T1 (1024) then T2 (1024), Q1.63
     EvalBins ev;                   // rbf_eval targets
@@ -217,6 +220,9 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
                           cudaStream_t st);
 
 rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st);
+rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int tile, DevArray<int32_t>& work,
+                      int64_t* nwork_out, cudaStream_t st);
+rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float* y, cudaStream_t st);
 rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cudaStream_t st);
 
 // ---- subdomain.cu

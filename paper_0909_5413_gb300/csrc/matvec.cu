@@ -8,7 +8,8 @@
 // kernel value is computed on the integer pipes (fixexp.cuh: exact
 // fixed-point offsets, table-driven exp in 64-bit fixed point, FP64 bits
 // assembled at the end) and the FP64 pipe only does the accumulate FMA. One
-// block per (cell, 128 targets) with four warps per target set: the stencil's
+// block per (cell, T targets), T = 32, 64 or 128 (the tile; autotuned with the
+// cell size by rbf_tune), with four warps per target set: the stencil's
 // sources are staged in shared memory and split by 32-source word among the
 // four quarters (word w goes to quarter w mod 4); each target tests its
 // candidates in FP32 on scaled cell-local offsets (a thin band around the
@@ -16,6 +17,7 @@
 // index-list definition) and keeps a bitmask of accepted sources; each warp
 // then walks its lanes' accepted sources in lockstep. The four partial sums of
 // a target are added in quarter order (deterministic).
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -23,11 +25,9 @@
 namespace rbf {
 namespace {
 
-constexpr int kMvThreads = 128;                // targets per block (FP32 kernel: threads per block)
 constexpr int kMvQ = 4;                        // source quarters of the FP64 kernel
-constexpr int kMv64Threads = kMvThreads * kMvQ;
-constexpr int kMvStage = 1152;                 // sources staged per pass (3 x 3 cells of ~115 points: one pass)
-constexpr int kMvWords = kMvStage / 32;        // mask words per target
+constexpr int kMvStage = 1152;                 // FP64: sources staged per pass at most (3 x 3 cells of ~115 points)
+constexpr int kMv32StageMax = 1536;            // FP32: the same
 constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 
 struct MvParams {
@@ -44,7 +44,15 @@ struct MvParams {
     const Prob* prob;          // per-problem grid and kernel constants
     const int32_t* pid_cell;   // problem of each cell
     const int32_t* active;     // per-problem mask (null: every problem)
+    int stage;                 // sources staged per pass (a multiple of 32)
 };
+
+// Stage size for a context: the largest stencil, rounded up to 32, capped.
+inline int stage_for(const rbf_ctx* ctx, int cap)
+{
+    const int s = ((std::max(ctx->stage_max, 1) + 31) / 32) * 32;
+    return std::min(s, cap);
+}
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -76,34 +84,38 @@ __device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
     return *reinterpret_cast<float2*>(&d);
 }
 
-constexpr size_t kMvSmem = 2 * kFxTab * sizeof(unsigned long long)   // tables
-                           + 2 * kMvStage * sizeof(double)             // staged xy
-                           + 2 * kMvStage * sizeof(long long)          // staged fixed-point xy
-                           + kMvStage * sizeof(double)                 // staged w
-                           + 2 * kMvStage * sizeof(float)              // staged FP32 offsets
-                           + (size_t)kMvWords * kMvThreads * 4         // accept masks
-                           + (size_t)kMvQ * kMvThreads * sizeof(double);   // partial sums
-
-__global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, const double* __restrict__ w,
-                                                                double* __restrict__ y)
+// Dynamic shared memory of the FP64 kernel for tile T and stage S: tables, staged
+// FP64 and fixed-point coordinates, weights, partial sums, FP32 offsets, masks.
+__host__ __device__ constexpr size_t mv64_smem(int T, int S)
 {
+    return 2 * kFxTab * sizeof(unsigned long long) + (size_t)S * (2 * sizeof(double) + 2 * sizeof(long long) +
+                                                                   sizeof(double) + 2 * sizeof(float)) +
+           (size_t)kMvQ * T * sizeof(double) + (size_t)(S / 32) * T * 4;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, const double* __restrict__ w,
+                                                                 double* __restrict__ y)
+{
+    constexpr int kThreads = T * kMvQ;
+    const int kStage = P.stage;
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long* T1 = smem_u64;
     unsigned long long* T2 = T1 + kFxTab;
     double* SX = (double*)(T2 + kFxTab);
-    long long* SXF = (long long*)(SX + 2 * kMvStage);
-    double* SW = (double*)(SXF + 2 * kMvStage);
-    double* PART = SW + kMvStage;
-    float* SF = (float*)(PART + kMvQ * kMvThreads);
-    uint32_t* MASK = (uint32_t*)(SF + 2 * kMvStage);
+    long long* SXF = (long long*)(SX + 2 * kStage);
+    double* SW = (double*)(SXF + 2 * kStage);
+    double* PART = SW + kStage;
+    float* SF = (float*)(PART + kMvQ * T);
+    uint32_t* MASK = (uint32_t*)(SF + 2 * kStage);
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
 
     const int tid = threadIdx.x;
-    const int t = tid & (kMvThreads - 1), qtr = tid / kMvThreads;   // target, quarter (warp-uniform)
+    const int t = tid & (T - 1), qtr = tid / T;   // target, quarter (warp-uniform)
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
     const int pcell = P.pid_cell[cell];
     if (P.active && !P.active[pcell]) return;   // masked problem (the whole block belongs to it)
-    for (int i = tid; i < 2 * kFxTab; i += kMv64Threads) T1[i] = P.fxtab[i];
+    for (int i = tid; i < 2 * kFxTab; i += kThreads) T1[i] = P.fxtab[i];
     const Prob& pr = P.prob[pcell];
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
     const double rc2 = pr.rc2, knorm = pr.knorm, fxs = pr.fx_scale;
@@ -142,10 +154,10 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
     __syncthreads();
     const int S = row_pre[nrow];
     double acc = 0.0;
-    for (int base = 0; base < S; base += kMvStage) {
-        const int ns = min(kMvStage, S - base);
+    for (int base = 0; base < S; base += kStage) {
+        const int ns = min(kStage, S - base);
         if (base > 0) __syncthreads();   // the previous pass is done with the staged data
-        for (int idx = tid; idx < ns; idx += kMv64Threads) {
+        for (int idx = tid; idx < ns; idx += kThreads) {
             int g = base + idx;
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
@@ -197,15 +209,15 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
                 double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
                 if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
             }
-            MASK[wi * kMvThreads + t] = m;
+            MASK[wi * T + t] = m;
         }
         // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
         int wi = qtr;
-        uint32_t cur = wi < nw ? MASK[wi * kMvThreads + t] : 0u;
+        uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
         for (;;) {
             while (cur == 0u && wi + kMvQ < nw) {
                 wi += kMvQ;
-                cur = MASK[wi * kMvThreads + t];
+                cur = MASK[wi * T + t];
             }
             const bool has = cur != 0u;
             if (!__any_sync(0xffffffffu, has)) break;
@@ -219,24 +231,26 @@ __global__ void __launch_bounds__(kMv64Threads, 2) k_matvec_f64(MvParams P, cons
             }
         }
     }
-    PART[qtr * kMvThreads + t] = acc;
+    PART[qtr * T + t] = acc;
     __syncthreads();
-    if (qtr == 0 && active)
-        y[p] = (((PART[t] + PART[kMvThreads + t]) + PART[2 * kMvThreads + t]) + PART[3 * kMvThreads + t]) * knorm;
+    if (qtr == 0 && active) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
 }
 
-constexpr int kMv32Stage = 1536;   // sources staged per pass (even; 18 KB of static shared memory)
 
-// FP32 matvec for the inner solves of the mixed form: block per (cell, 128
+// FP32 matvec for the inner solves of the mixed form: block per (cell, T
 // targets), sources staged in shared memory as FP32 offsets from the target
 // cell's corner (scaled so the kernel is exp2(-|dX|^2)), two sources per
 // packed f32x2 step. No cutoff mask: the entries beyond r_c that this adds
 // back are below 2^-53 relative to the diagonal, far under FP32 rounding, and
 // the outer FP64 residual uses the exact truncated matrix.
-__global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const float* __restrict__ w,
-                                                               float* __restrict__ y)
+template <int T>
+__global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __restrict__ w, float* __restrict__ y)
 {
-    __shared__ __align__(16) float SXs[kMv32Stage + 2], SYs[kMv32Stage + 2], SWs[kMv32Stage + 2];
+    const int kStage = P.stage;
+    extern __shared__ __align__(16) float smem_f32[];
+    float* SXs = smem_f32;                 // kStage + 4 each (16-byte aligned)
+    float* SYs = SXs + kStage + 4;
+    float* SWs = SYs + kStage + 4;
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
     const int tid = threadIdx.x;
     const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
@@ -272,10 +286,10 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec_f32v2(MvParams P, const f
     __syncthreads();
     const int S = row_pre[nrow];
     float2 acc2 = make_float2(0.f, 0.f);
-    for (int base = 0; base < S; base += kMv32Stage) {
-        const int ns = min(kMv32Stage, S - base);
+    for (int base = 0; base < S; base += kStage) {
+        const int ns = min(kStage, S - base);
         if (base > 0) __syncthreads();
-        for (int idx = tid; idx < ns; idx += kMvThreads) {
+        for (int idx = tid; idx < ns; idx += T) {
             int g = base + idx;
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
@@ -333,24 +347,60 @@ MvParams mv_params(const rbf_ctx* ctx)
     P.prob = ctx->prob.p;
     P.pid_cell = ctx->pid_cell.p;
     P.active = ctx->active_mask;
+    P.stage = 0;
     return P;
+}
+
+template <int T>
+rbf_status prepare_f64(rbf_ctx* ctx)
+{
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)mv64_smem(T, kMvStage)));
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared));
+    return RBF_OK;
+}
+
+template <int T>
+rbf_status launch_f64(rbf_ctx* ctx, const MvParams& P, int64_t nwork, const double* w, double* y, cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, k_matvec_f64<T>, (unsigned)nwork, T * kMvQ, mv64_smem(T, P.stage), st, P, w, y);
+    return RBF_OK;
+}
+
+rbf_status dispatch_f64(rbf_ctx* ctx, MvParams P, int64_t nwork, const double* w, double* y, cudaStream_t st)
+{
+    if (nwork == 0) return RBF_OK;
+    P.stage = stage_for(ctx, kMvStage);
+    switch (ctx->tile64) {
+    case 32: return launch_f64<32>(ctx, P, nwork, w, y, st);
+    case 64: return launch_f64<64>(ctx, P, nwork, w, y, st);
+    default: return launch_f64<128>(ctx, P, nwork, w, y, st);
+    }
+}
+
+template <int T>
+rbf_status launch_f32(rbf_ctx* ctx, MvParams P, const float* w, float* y, cudaStream_t st)
+{
+    P.work = ctx->mv_work32.p;
+    P.stage = stage_for(ctx, kMv32StageMax);
+    const size_t smem = 3 * (size_t)(P.stage + 4) * sizeof(float);
+    RBF_LAUNCH(ctx, k_matvec_f32v2<T>, (unsigned)ctx->n_work32, T, smem, st, P, w, y);
+    return RBF_OK;
 }
 
 }  // namespace
 
 rbf_status matvec_prepare(rbf_ctx* ctx)
 {
-    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMvSmem));
-    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       cudaSharedmemCarveoutMaxShared));
-    return RBF_OK;
+    RBF_CHECK(prepare_f64<32>(ctx));
+    RBF_CHECK(prepare_f64<64>(ctx));
+    return prepare_f64<128>(ctx);
 }
 
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
-    if (ctx->n_work == 0) return RBF_OK;
-    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)ctx->n_work, kMv64Threads, kMvSmem, st, mv_params(ctx), w, y);
-    return RBF_OK;
+    return dispatch_f64(ctx, mv_params(ctx), ctx->n_work, w, y, st);
 }
 
 // s = sum_j k(|t - x_j|) w_j for the cell-sorted targets of another point
@@ -358,14 +408,12 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
 rbf_status eval_sorted_f64(rbf_ctx* ctx, const double* txy, const float* tloc, const int32_t* tcell_start,
                            const int32_t* twork, int64_t nwork, const double* w, double* s, cudaStream_t st)
 {
-    if (nwork == 0) return RBF_OK;
     MvParams P = mv_params(ctx);
     P.work = twork;
     P.txy = txy;
     P.tloc = tloc;
     P.tcell_start = tcell_start;
-    RBF_LAUNCH(ctx, k_matvec_f64, (unsigned)nwork, kMv64Threads, kMvSmem, st, P, w, s);
-    return RBF_OK;
+    return dispatch_f64(ctx, P, nwork, w, s, st);
 }
 
 rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
@@ -384,8 +432,14 @@ rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t)
 rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_MATVEC_F32, st));
-    if (ctx->n_work > 0)
-        RBF_LAUNCH(ctx, k_matvec_f32v2, (unsigned)ctx->n_work, kMvThreads, 0, st, mv_params(ctx), w, y);
+    if (ctx->n_work32 > 0) {
+        const MvParams P = mv_params(ctx);
+        switch (ctx->tile32) {
+        case 32: RBF_CHECK(launch_f32<32>(ctx, P, w, y, st)); break;
+        case 64: RBF_CHECK(launch_f32<64>(ctx, P, w, y, st)); break;
+        default: RBF_CHECK(launch_f32<128>(ctx, P, w, y, st)); break;
+        }
+    }
     return prof_end(ctx, RBF_PROF_MATVEC_F32, st);
 }
 

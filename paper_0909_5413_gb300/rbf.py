@@ -28,14 +28,15 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
-            "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval"]
+            "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
 
 
 class RbfParams(C.Structure):
-    _fields_ = [("sigma", C.c_double), ("cutoff", C.c_double), ("cell_size", C.c_double), ("normalized", C.c_int)]
+    _fields_ = [("sigma", C.c_double), ("cutoff", C.c_double), ("cell_size", C.c_double), ("normalized", C.c_int),
+                ("tile_f64", C.c_int), ("tile_f32", C.c_int)]
 
 
 class RbfRasmParams(C.Structure):
@@ -129,6 +130,8 @@ def load(path: str | None = None):
     L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
     L.rbf_debug_kernel_pairs.argtypes = [P, P, P, C.c_int64, P]
     L.rbf_eval.argtypes = [P, P, C.c_int64, P, P, P]
+    L.rbf_tune.argtypes = [P, P, C.c_int64, C.POINTER(RbfParams), C.c_double, C.c_double, C.POINTER(RbfParams),
+                           C.POINTER(C.c_double), P]
     L.rbf_bin_batch.argtypes = [P, P, I64, C.c_int64, C.POINTER(RbfParams), P]
     L.rbf_rasm_setup_batch.argtypes = [P, C.POINTER(RbfRasmParams), P]
     L.rbf_solve_batch.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
@@ -200,6 +203,16 @@ def rbf_matvec(ctx, w_dev, y_dev, precision: int = RBF_FP64, stream=None) -> Non
 
 def rbf_eval(ctx, xe_dev, m: int, w_dev, s_dev, stream=None) -> None:
     _check(ctx, load().rbf_eval(ctx, _ptr(xe_dev), int(m), _ptr(w_dev), _ptr(s_dev), _stream(stream)))
+
+
+def rbf_tune(ctx, xy_dev, n: int, base: RbfParams, w_f64: float = 1.0, w_f32: float = 0.0,
+             stream=None) -> tuple[RbfParams, float]:
+    """Autotuned cell size and matvec tiles; the context is left binned with them."""
+    best = RbfParams()
+    score = C.c_double()
+    _check(ctx, load().rbf_tune(ctx, _ptr(xy_dev), int(n), C.byref(base), float(w_f64), float(w_f32), C.byref(best),
+                                C.byref(score), _stream(stream)))
+    return best, score.value
 
 
 def rbf_matvec_noalloc(ctx, w_dev, y_dev, stream=None) -> None:
@@ -329,6 +342,8 @@ class SolverConfig:
     core_size: float
     overlap: float
     cell_size: float = 0.0
+    tile_f64: int = 0               # targets per block of the FP64 / FP32 matvecs (0 = 128)
+    tile_f32: int = 0
     normalized: bool = False
     max_sub_points: int = 0
     factor_precision: int = RBF_FP64
@@ -341,7 +356,7 @@ class SolverConfig:
     inner_rtol: float = 1e-5
 
     def params(self) -> RbfParams:
-        return RbfParams(self.sigma, self.cutoff, self.cell_size, int(self.normalized))
+        return RbfParams(self.sigma, self.cutoff, self.cell_size, int(self.normalized), self.tile_f64, self.tile_f32)
 
     def rasm(self) -> RbfRasmParams:
         return RbfRasmParams(self.x0, self.y0, self.core_size, self.overlap, self.max_sub_points,

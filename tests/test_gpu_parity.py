@@ -509,3 +509,64 @@ def test_interpolate_host_matches_device_path(rbf):
     np.testing.assert_array_equal(w_h.numpy(), w)
     assert ctx.launches > 0
     ctx.close()
+
+
+# ------------------------------------------------- tiles, cell sizes, tuner
+
+def matvec_with(rbf, p, w, cell, t64, t32):
+    ctx = rbf.Context(0)
+    rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(p.sigma, p.cutoff, cell, 0, t64, t32))
+    y64 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    y32 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y64, rbf.RBF_FP64)
+    rbf.rbf_matvec(ctx.handle, dev(w), y32, rbf.RBF_FP32)
+    out = host(y64), host(y32)
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("cf", [1.0, 0.5, 1.0 / 3.0])
+def test_matvec_tiles_and_cell_sizes(rbf, cf):
+    """Every tile gives the same bits (the per-target summation order does not
+    depend on it); every cell size gives the oracle's truncated product."""
+    p = W.lattice_problem(72, 0.8, seed=61)
+    w = np.random.default_rng(12).standard_normal(p.n)
+    ref = O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)
+    res = {t: matvec_with(rbf, p, w, cf * p.cutoff, t, t) for t in (32, 64, 128)}
+    for t in (32, 64):
+        np.testing.assert_array_equal(res[t][0], res[128][0])
+        np.testing.assert_array_equal(res[t][1], res[128][1])
+    assert rel_err(res[128][0], ref) <= 1e-13
+    assert rel_err(res[128][1], ref) <= 2e-5
+
+
+def test_tile_validation(rbf):
+    p = W.lattice_problem(12, 0.8, seed=62)
+    ctx = rbf.Context(0)
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(p.sigma, p.cutoff, 0.0, 0, 48, 0))
+    assert e.value.status == 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("w32", [0.0, 26.0])
+def test_tune_picks_a_valid_setting_and_solves(rbf, w32):
+    p = W.lattice_problem(160, 0.8, seed=63)
+    ctx = rbf.Context(0)
+    xyd = dev(p.xy)
+    best, score = rbf.rbf_tune(ctx.handle, xyd, p.n, rbf.RbfParams(p.sigma, p.cutoff, 0.0, 0), 1.0, w32)
+    assert best.tile_f64 in (32, 64, 128) and best.tile_f32 in (32, 64, 128)
+    assert any(abs(best.cell_size - f * p.cutoff) <= 1e-12 * p.cutoff for f in (1.0, 0.5, 1.0 / 3.0))
+    assert score > 0.0
+    # the context is binned with the pick: the matvec is the oracle's, and a solve converges
+    w = np.random.default_rng(13).standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y)
+    assert rel_err(host(y), O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)) <= 1e-13
+    mixed = w32 > 0
+    rbf.rbf_rasm_setup(ctx.handle, rbf.RbfRasmParams(p.x0, p.x0, p.core_size, p.overlap, 0, int(mixed)))
+    wd = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = rbf.rbf_solve(ctx.handle, dev(p.f), wd, rbf.RbfSolveParams(1e-13, 30, 5000, int(mixed), 60, 1e-5),
+                             check=False)
+    assert st == 0 and info.relres <= 1e-13
+    ctx.close()
