@@ -125,6 +125,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="server slots (serve)")
     ap.add_argument("--rates", default="0.5,0.9", help="arrival rates swept, as fractions of the saturated rate")
     ap.add_argument("--sigma", type=float, default=0.001, help="Gaussian width of the paper workload")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the cell size and matvec tiles (rbf_tune) once, before the warm-up steps")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
@@ -292,6 +294,14 @@ def run_ours(args, ws, rank, local):
         st, info = ctx.solve(f, w, c, check=False)
         return st, info
 
+    tuned = None
+    if args.tune:
+        # one FP64 matvec per step for the FP64 form; about 1 FP64 per 26 FP32 ones for the mixed form
+        best, score = rbf.rbf_tune(h, xy, p.n, cfg.params(), 1.0, 26.0 if mode == "mixed" else 0.0)
+        cfg.cell_size, cfg.tile_f64, cfg.tile_f32 = best.cell_size, best.tile_f64, best.tile_f32
+        tuned = {"cell_size_over_rc": best.cell_size / p.cutoff, "tile_f64": best.tile_f64,
+                 "tile_f32": best.tile_f32, "score_ms": score}
+
     def barrier():
         if dist is not None:
             dist.barrier()
@@ -341,7 +351,8 @@ def run_ours(args, ws, rank, local):
     if n_mv:
         avg_s = t_mv / n_mv / 1e3
         if mode == "f64":
-            roofline = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=(name == "lattice1024"))
+            default_cfg = (cfg.cell_size in (0.0, p.cutoff)) and cfg.tile_f64 in (0, 128)
+            roofline = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=(name == "lattice1024" and default_cfg))
             roofline["algorithmic_bytes_per_launch"] = 32 * p.n
         else:
             cand = candidate_pairs(rbf, h)
@@ -404,7 +415,7 @@ def run_ours(args, ws, rank, local):
         out = {"metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if mode == "f64" else "f32-inner/f64-outer", "data": "synthetic",
-               "config": workload_config(name, p, mode), "ok": ok, "solve": info,
+               "config": {**workload_config(name, p, mode), "tuned": tuned}, "ok": ok, "solve": info,
                "step_ms": [round(t, 3) for t in times], "roofline": roofline, "breakdown_ms": breakdown,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "other_precision": extra}
