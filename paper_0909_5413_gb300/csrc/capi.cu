@@ -151,10 +151,19 @@ bool make_fx_constants(double amax, double rc, double s, double* scale, int* sh,
     const long double gm = std::frexp(g, &ge);                  // g = gm 2^ge, gm in [0.5, 1)
     const int f = 2 * S + 2 * shift - 64 - ge;                  // makes M = gm 2^64 in [2^63, 2^64); z < 2^62
     if (f < 21 || f > 63) return false;
+    unsigned long long m = (unsigned long long)std::ldexp(gm, 64);
+    int fb = f;
+    // the 32-bit layout of kernel_fx52 (M scaled down to exactly 52 fraction bits) when it
+    // fits and the exponent n = floor(r2 s log2 e) stays below 1000 inside the cutoff
+    // (r_c up to about 37 sigma); otherwise the general path
+    if (f >= 52 && (long double)rc * rc * g < 999.0L) {
+        m >>= (f - 52);
+        fb = 52;
+    }
     *scale = std::ldexp(1.0, S);
     *sh = shift;
-    *F = f;
-    *M = (unsigned long long)std::ldexp(gm, 64);
+    *F = fb;
+    *M = m;
     return true;
 }
 
@@ -178,7 +187,8 @@ __global__ void k_debug_kernel_pairs(const double* __restrict__ pr4, double* __r
                                      (unsigned long long)fx_coord(xj, q.fx_scale, q.fx_sh));
     const long long dv = (long long)((unsigned long long)fx_coord(yi, q.fx_scale, q.fx_sh) -
                                      (unsigned long long)fx_coord(yj, q.fx_scale, q.fx_sh));
-    out[i] = kernel_fx(du, dv, q.fx_F, q.fx_M, tab, tab + kFxTab);
+    out[i] = q.fx_F == 52 ? kernel_fx52(du, dv, q.fx_M, tab, tab + kFxTab)
+                          : kernel_fx(du, dv, q.fx_F, q.fx_M, tab, tab + kFxTab);
 }
 
 __global__ void k_debug_exp(const double* __restrict__ t, double* __restrict__ out, int64_t n, int variant,

@@ -82,4 +82,40 @@ __device__ __forceinline__ double kernel_fx(long long du, long long dv, int F, u
     return n < 1000u ? __longlong_as_double((long long)bits) : 0.0;
 }
 
+// The same value for problems whose multiplier was scaled to F = 52 fraction
+// bits (every r_c up to about 37 sigma on coordinates of moderate spread): z's
+// high word then holds n (top 12 bits), i1 and i2, and its low word the
+// remainder, so every extraction is a 32-bit operation; the squares use the
+// signed split d = a 2^32 + b with b in [-2^31, 2^31), d^2 / 2^64 ~ a^2 + 2 a b /
+// 2^32 (no absolute values); n < 1000 is guaranteed by the binning.
+__device__ __forceinline__ unsigned long long sqhi_s(long long d)
+{
+    const int b = (int)(unsigned int)d;
+    const int a = (int)(d >> 32) - (b >> 31);
+    return (unsigned long long)((long long)a * a) + 2ull * (unsigned long long)(long long)__mulhi(a, b);
+}
+
+__device__ __forceinline__ double kernel_fx52(long long du, long long dv, unsigned long long M,
+                                              const unsigned long long* __restrict__ T1,
+                                              const unsigned long long* __restrict__ T2)
+{
+    const unsigned long long q = sqhi_s(du) + sqhi_s(dv) + 2ull;
+    const unsigned long long z = __umul64hi(q, M);   // exact floor: 52 fraction bits leave no room for more
+    const unsigned int zh = (unsigned int)(z >> 32), zl = (unsigned int)z;
+    const unsigned int n = zh >> 20;
+    const unsigned int i1 = (zh >> 10) & (kFxTab - 1), i2 = zh & (kFxTab - 1);
+    // x = rho ln 2 in units 2^-64 with rho 2^20 = zl 2^-32: (zl * ln 2 2^44) >> 32
+    constexpr unsigned long long kC = 12193974156573ull;   // ln 2 2^44
+    const unsigned long long x =
+        (unsigned long long)zl * (unsigned int)(kC >> 32) + __umulhi(zl, (unsigned int)kC);
+    const unsigned int xh = (unsigned int)(x >> 12);
+    const unsigned long long onem = x - (((unsigned long long)xh * xh) >> 41);
+    unsigned long long m = hi64a(T1[i1], T2[i2]) << 1;
+    m -= hi64a(m, onem);
+    m = m - (m >> 63) + 512ull;
+    const unsigned int lo = (unsigned int)(m >> 10);
+    const unsigned int hi = (unsigned int)(m >> 42) + ((1021u - n) << 20);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 }  // namespace rbf

@@ -175,26 +175,28 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv
     if (lane == 0) out[k] = a;
 }
 
-// r = f - t (FP64); partial sums of |r|^2.
+// r = f - t (FP64); partial sums of |r|^2 per chunk (the chunks and the
+// order of the vector passes, so that a problem solved alone and in a batch
+// sums in the same order).
 __global__ void __launch_bounds__(kDotThreads)
     k_residual(const double* __restrict__ f, const double* __restrict__ t, double* __restrict__ r, int64_t n,
                double* __restrict__ partial)
 {
     __shared__ double red[kDotThreads / 32];
+    const int64_t chunk = blockIdx.x;
+    const int64_t base = chunk * kChunk + threadIdx.x;
     double a = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double v = f[i] - t[i];
-        r[i] = v;
-        a = fma(v, v, a);
+#pragma unroll
+    for (int u = 0; u < kChunkPerThread; ++u) {
+        const int64_t i = base + (int64_t)u * kDotThreads;
+        if (i < n) {
+            const double v = f[i] - t[i];
+            r[i] = v;
+            a = fma(v, v, a);
+        }
     }
-    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kDotThreads / 32; ++w) s += red[w];
-        partial[(int64_t)blockIdx.x * 32] = s;
-    }
+    const double s = block_sum(a, red);
+    if (threadIdx.x == 0) partial[chunk * 32] = s;
 }
 
 // Start of a cycle: beta = |r|, g = beta e_1, estimate beta / |f|. For an
@@ -477,9 +479,9 @@ rbf_status true_residual(rbf_ctx* ctx, const double* f, const double* w, double*
 {
     GmresDev* g = ctx->gm.p;
     RBF_CHECK(matvec_sorted_f64(ctx, w, t, st));
-    unsigned nb = dot_blocks(ctx->n);
-    RBF_LAUNCH(ctx, k_residual, nb, kDotThreads, 0, st, f, t, r64, ctx->n, ctx->partial.p);
-    RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nb, 1, &g->beta2);
+    const int64_t nc = num_chunks(ctx->n);
+    RBF_LAUNCH(ctx, k_residual, (unsigned)nc, kDotThreads, 0, st, f, t, r64, ctx->n, ctx->partial.p);
+    RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nc, 1, &g->beta2);
     RBF_CUDA(ctx, cudaMemcpyAsync(&ctx->gm_host->beta2, &g->beta2, sizeof(double), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
     *relres = std::sqrt(ctx->gm_host->beta2) / fnorm;

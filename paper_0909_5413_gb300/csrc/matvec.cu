@@ -19,6 +19,7 @@
 // a target are added in quarter order (deterministic).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -212,24 +213,30 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             MASK[wi * T + t] = m;
         }
         // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
-        int wi = qtr;
-        uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
-        for (;;) {
-            while (cur == 0u && wi + kMvQ < nw) {
-                wi += kMvQ;
-                cur = MASK[wi * T + t];
+        auto walk = [&](auto k52) {
+            int wi = qtr;
+            uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
+            for (;;) {
+                while (cur == 0u && wi + kMvQ < nw) {
+                    wi += kMvQ;
+                    cur = MASK[wi * T + t];
+                }
+                const bool has = cur != 0u;
+                if (!__any_sync(0xffffffffu, has)) break;
+                if (has) {
+                    const int idx = wi * 32 + (__ffs(cur) - 1);
+                    cur &= cur - 1u;
+                    const long long du = (long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]);
+                    const long long dv = (long long)((unsigned long long)yf - (unsigned long long)SXF[2 * idx + 1]);
+                    double kv;
+                    if constexpr (decltype(k52)::value) kv = kernel_fx52(du, dv, M, T1, T2);
+                    else kv = kernel_fx(du, dv, F, M, T1, T2);
+                    acc = fma(kv, SW[idx], acc);
+                }
             }
-            const bool has = cur != 0u;
-            if (!__any_sync(0xffffffffu, has)) break;
-            if (has) {
-                const int idx = wi * 32 + (__ffs(cur) - 1);
-                cur &= cur - 1u;
-                const double kv = kernel_fx((long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]),
-                                            (long long)((unsigned long long)yf - (unsigned long long)SXF[2 * idx + 1]),
-                                            F, M, T1, T2);
-                acc = fma(kv, SW[idx], acc);
-            }
-        }
+        };
+        if (F == 52) walk(std::true_type{});   // block-uniform
+        else walk(std::false_type{});
     }
     PART[qtr * T + t] = acc;
     __syncthreads();

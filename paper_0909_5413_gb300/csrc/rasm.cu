@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
             if (r2 <= rc2) {
                 const long long du = (long long)((unsigned long long)pxf[i] - (unsigned long long)pxf[j]);
                 const long long dv = (long long)((unsigned long long)pyf[i] - (unsigned long long)pyf[j]);
-                v = kernel_fx(du, dv, F, M, fxtab, fxtab + kFxTab) * knorm;
+                v = (F == 52 ? kernel_fx52(du, dv, M, fxtab, fxtab + kFxTab)
+                             : kernel_fx(du, dv, F, M, fxtab, fxtab + kFxTab)) * knorm;
             }
             A[tri(i, j)] = v;
         }
