@@ -40,27 +40,47 @@ METRIC = "RBF solve time at 1e-13 rel. residual (GMRES+RASM)"
 UNIT = "ms"
 
 # The FP64 matvec's kernel value is computed on the integer pipes (fixed-point
-# exp), so its bound is the SM's ALU pipe: peak from unit counts and clocks,
-# 152 SMs x 4 partitions x 16 lanes x 2.07 GHz = 20.1 T lane-ops/s. One ncu
-# capture of this revision (profiles/matvec_f64_lattice1024.md) measured 87.4
-# ALU lane-ops per in-cutoff pair, which puts the ALU ceiling at 230 G pairs/s;
-# the roofline fraction is live pairs/s over that ceiling.
-ALU_PEAK_LANE_OPS = 152 * 4 * 16 * 2.07e9
-MATVEC_F64_REV = "fixed-point-v3"
-MATVEC_F64_ALU_OPS_PER_PAIR = {"fixed-point-v3": 87.4}
-MATVEC_F64_TRAFFIC = {"fixed-point-v3": 37_974_016}   # lattice1024, dram read + write per launch (ncu)
+# exp), so the FP64 pipe no longer bounds it; what does is the SM's instruction
+# issue (65 % of issue slots, ALU pipe 51 %, the rest latency). Peak from unit
+# counts and clocks: 152 SMs x 4 partitions x 32 lanes x 2.07 GHz = 40.3 T
+# lane-instructions/s. One ncu capture of this revision
+# (profiles/matvec_f64_lattice1024.md) measured 164.2 issued lane-instructions
+# per in-cutoff pair (all lanes of each issued warp instruction, idle lockstep
+# lanes included), which puts the issue ceiling at 245 G pairs/s; the roofline
+# fraction is live pairs/s over that ceiling.
+ISSUE_PEAK_LANE_INSTR = 152 * 4 * 32 * 2.07e9
+MATVEC_F64_REV = "fixed-point-v4"
+MATVEC_F64_INSTR_PER_PAIR = {"fixed-point-v4": 164.2}
+MATVEC_F64_TRAFFIC = {"fixed-point-v4": 37_992_960}   # lattice1024, dram read + write per launch (ncu)
 # The FP64 view, for comparison: 26 FP64-equivalent flops per pair (dx, dy 2; r2 3;
 # argument 1; exp 18; accumulate 2) against the FP64 ALU peak 152 x 2 DFMA/clk x 2 x 2.07 GHz.
 FLOPS_PER_PAIR_F64 = 26
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, note: str = "") -> dict:
+    """Roofline object of the FP64 matvec from its in-cutoff pair count and
+    CUDA-event launch time."""
+    rate = pairs / avg_s
+    instr = MATVEC_F64_INSTR_PER_PAIR[MATVEC_F64_REV]
+    peak = ISSUE_PEAK_LANE_INSTR / instr
+    out = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+           "frac": rate / peak, "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if traffic else None,
+           "peak_note": ("SM issue 152 SMs x 4 x 32 lanes x 2.07 GHz = 40.3 T lane-instr/s over "
+                         f"{instr} issued lane-instructions per in-cutoff pair (ncu, this revision)"),
+           "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
+           "launches": launches, "algorithmic_bytes_per_launch": None,
+           "fp64_equivalent": {"tflops": pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                               "flops_per_pair": FLOPS_PER_PAIR_F64}}
+    if note:
+        out["note"] = note
+    return out
+
+
 # The FP32 matvec (inner solves of the mixed form) evaluates every staged
 # candidate pair (no cutoff mask); ncu measured 6.55 issued lane-instructions
-# per candidate (profiles/mixed_kernels_lattice1024.md), so the SM issue rate,
-# 152 x 4 partitions x 32 lanes x 2.07 GHz = 40.3 T lane-instr/s, caps it at
-# 6.15 T candidates/s.
-ISSUE_PEAK_LANE_INSTR = 152 * 4 * 32 * 2.07e9
+# per candidate (profiles/mixed_kernels_lattice1024.md), so the same issue
+# rate caps it at 6.15 T candidates/s.
 MATVEC_F32_INSTR_PER_CANDIDATE = 6.55
 
 
@@ -75,25 +95,6 @@ def candidate_pairs(rbf, h) -> int:
     pad = np.pad(cnt, 1)
     win = sum(pad[1 + dy:1 + dy + ncy, 1 + dx:1 + dx + ncx] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
     return int((cnt * win).sum())
-
-
-def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, note: str = "") -> dict:
-    """Roofline object of the FP64 matvec from its in-cutoff pair count and
-    CUDA-event launch time."""
-    rate = pairs / avg_s
-    ops = MATVEC_F64_ALU_OPS_PER_PAIR[MATVEC_F64_REV]
-    peak = ALU_PEAK_LANE_OPS / ops
-    out = {"kernel": "k_matvec_f64", "bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-           "frac": rate / peak, "traffic": MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if traffic else None,
-           "peak_note": ("ALU pipe 152 SMs x 4 x 16 lanes x 2.07 GHz = 20.1 T lane-ops/s over "
-                         f"{ops} ALU lane-ops per in-cutoff pair (ncu, this revision)"),
-           "kernel_rev": MATVEC_F64_REV, "pairs_per_launch": pairs, "avg_launch_ms": avg_s * 1e3,
-           "launches": launches, "algorithmic_bytes_per_launch": None,
-           "fp64_equivalent": {"tflops": pairs * FLOPS_PER_PAIR_F64 / avg_s / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
-                               "flops_per_pair": FLOPS_PER_PAIR_F64}}
-    if note:
-        out["note"] = note
-    return out
 
 
 WORKLOADS = {
