@@ -36,7 +36,7 @@ struct GmresDev {
     int j;                        // last completed step
     int done;                     // 1: cycle may stop (estimate met or breakdown)
     int breakdown;
-    int pad;
+    int budget;                   // batched solver: steps this problem may still take in the cycle
 };
 
 template <class T>

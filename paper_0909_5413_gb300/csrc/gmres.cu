@@ -398,7 +398,7 @@ struct StepStatus {
 rbf_status read_status(rbf_ctx* ctx, cudaStream_t st, StepStatus* s)
 {
     const size_t off = offsetof(GmresDev, est);
-    const size_t len = offsetof(GmresDev, pad) - off;
+    const size_t len = offsetof(GmresDev, budget) - off;
     RBF_CUDA(ctx, cudaMemcpyAsync((char*)ctx->gm_host + off, (char*)ctx->gm.p + off, len, cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
     s->est = ctx->gm_host->est;

@@ -11,6 +11,7 @@
 // at once. An Arnoldi cycle runs with no host synchronisation (each problem's
 // stop flag lives on the device), so the cycle is captured once as a CUDA
 // graph and replayed; the host reads the problems' residuals once per cycle.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -224,11 +225,12 @@ __global__ void k_breduce(const double* __restrict__ partial, Chunks C, int npro
 
 // Start of a cycle of every active problem (mode 1: reference norm = |r|).
 __global__ void k_bcycle_init(GmresDev* __restrict__ gm, int nprob, int m, int mode,
-                              const int32_t* __restrict__ active)
+                              const int32_t* __restrict__ active, const int32_t* __restrict__ budget)
 {
     int pb = blockIdx.x * blockDim.x + threadIdx.x;
     if (pb >= nprob || !active[pb]) return;
     GmresDev& g = gm[pb];
+    g.budget = budget[pb];   // steps left before max_iters (the cycle stops there, as the single solver's)
     if (mode == 1) g.fnorm2 = g.beta2;
     double beta = sqrt(g.beta2);
     double fn = sqrt(g.fnorm2);
@@ -272,7 +274,7 @@ __global__ void k_barnoldi(GmresDev* __restrict__ gm, int nprob, int j, const in
     g->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
     g->breakdown = (hn == 0.0) ? 1 : 0;
     g->est = fabs(g->g[j + 1]) / sqrt(g->fnorm2);
-    g->done = (g->est <= g->rtol || g->breakdown) ? 1 : 0;
+    g->done = (g->est <= g->rtol || g->breakdown || j + 1 >= g->budget) ? 1 : 0;
     g->j = j + 1;
 }
 
@@ -562,7 +564,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     Chunks C{dch, dch + nc, dch + 2 * nc, dch + 3 * nc, nc};
 
     RBF_CHECK(ensure(ctx, ctx->gmb, nprob));
-    RBF_CHECK(ensure(ctx, ctx->bactive, 2 * (size_t)nprob));
+    RBF_CHECK(ensure(ctx, ctx->bactive, 3 * (size_t)nprob));
     RBF_CHECK(ensure(ctx, ctx->bstat, 4 * (size_t)nprob));
     RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(nc, 1) * 32));
     RBF_CHECK(ensure(ctx, ctx->vec_a, n));
@@ -570,6 +572,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     GmresDev* gm = ctx->gmb.p;
     int32_t* active = ctx->bactive.p;
     int32_t* zero_mask = ctx->bactive.p + nprob;
+    int32_t* budget = ctx->bactive.p + 2 * nprob;   // steps left per problem
     RBF_CUDA(ctx, cudaMemsetAsync(gm, 0, sizeof(GmresDev) * nprob, st));
     const double rt = mixed ? (p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5) : p->rtol;
     RBF_LAUNCH(ctx, k_binit, blocks_for(nprob, 128), 128, 0, st, gm, nprob, rt);
@@ -622,6 +625,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     rbf_status result = RBF_ERR_NOT_CONVERGED;
     std::vector<std::vector<double>> hist(nprob);
     std::vector<int> stagnated(nprob, 0);
+    std::vector<int32_t> left(nprob, 0);
     ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
     batch_graph_reset(ctx);      // buffers may have moved since the last solve
     for (;;) {
@@ -648,8 +652,11 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         }
         RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         if (nact == 0) break;
+        for (int b = 0; b < nprob; ++b) left[b] = std::max(0, max_iters - iters[b]);
+        RBF_CUDA(ctx, cudaMemcpyAsync(budget, left.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         // one cycle of every active problem
-        RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active);
+        RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active,
+                   budget);
         if (!mixed) {
             RBF_LAUNCH(ctx, k_bscale<double>, bstream_blocks(n), 256, 0, st, V64, n, ctx->pid.p, gm, 0, active);
             RBF_CHECK(run_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));

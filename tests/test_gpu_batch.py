@@ -184,3 +184,25 @@ def test_single_solver_stops_on_stagnation(rbf):
     assert st == 6 and info.status == 6 and info.stagnated == 1, info.as_dict()
     assert info.iters < 400
     ctx.close()
+
+
+def test_batch_honours_max_iters_mid_cycle(rbf):
+    """A step cap inside a cycle stops every problem exactly there, as the
+    single-problem solver does (same iterate, bit for bit)."""
+    p = W.lattice_problem(30, 0.85, seed=7)
+    for cap in (17, 45):
+        ctx, xy, f, ptr = setup(rbf, [p])
+        wb = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        sp = rbf.RbfSolveParams(1e-13, 30, cap, 0, 0, 0.0)
+        st, infos = rbf.rbf_solve_batch(ctx.handle, dev(f), wb, sp, 1, check=False)
+        ctx.close()
+        assert st == 6 and infos[0].iters == cap
+        cfg = rbf.config_for(p, max_iters=cap)
+        c1 = rbf.Context(0)
+        c1.bin(dev(p.xy), cfg)
+        c1.rasm_setup(cfg)
+        w1 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        st1, info1 = c1.solve(dev(p.f), w1, cfg, check=False)
+        c1.close()
+        assert info1.iters == cap
+        np.testing.assert_array_equal(host(w1), host(wb))
