@@ -213,7 +213,15 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             MASK[wi * T + t] = m;
         }
         // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
+        // (up to two sources of the current mask word per step: two independent
+        // evaluation chains, accumulated in source order)
         auto walk = [&](auto k52) {
+            auto kval = [&](int idx) {
+                const long long du = (long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]);
+                const long long dv = (long long)((unsigned long long)yf - (unsigned long long)SXF[2 * idx + 1]);
+                if constexpr (decltype(k52)::value) return kernel_fx52(du, dv, M, T1, T2);
+                else return kernel_fx(du, dv, F, M, T1, T2);
+            };
             int wi = qtr;
             uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
             for (;;) {
@@ -224,14 +232,14 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                 const bool has = cur != 0u;
                 if (!__any_sync(0xffffffffu, has)) break;
                 if (has) {
-                    const int idx = wi * 32 + (__ffs(cur) - 1);
+                    const int i0 = wi * 32 + (__ffs(cur) - 1);
                     cur &= cur - 1u;
-                    const long long du = (long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]);
-                    const long long dv = (long long)((unsigned long long)yf - (unsigned long long)SXF[2 * idx + 1]);
-                    double kv;
-                    if constexpr (decltype(k52)::value) kv = kernel_fx52(du, dv, M, T1, T2);
-                    else kv = kernel_fx(du, dv, F, M, T1, T2);
-                    acc = fma(kv, SW[idx], acc);
+                    const bool two = cur != 0u;
+                    const int i1 = two ? wi * 32 + (__ffs(cur) - 1) : i0;
+                    cur &= cur - (two ? 1u : 0u);
+                    const double k0 = kval(i0), k1 = kval(i1);
+                    acc = fma(k0, SW[i0], acc);
+                    if (two) acc = fma(k1, SW[i1], acc);
                 }
             }
         };
