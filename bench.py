@@ -126,6 +126,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="server slots (serve)")
     ap.add_argument("--rates", default="0.5,0.9", help="arrival rates swept, as fractions of the saturated rate")
     ap.add_argument("--sigma", type=float, default=0.001, help="Gaussian width of the paper workload")
+    ap.add_argument("--inner-cutoff", type=float, default=6.1,
+                    help="mixed form: cutoff (in sigma) of the FP32 inner grid; 0 = the r_c grid")
     ap.add_argument("--tune", action="store_true",
                     help="autotune the cell size and matvec tiles (rbf_tune) once, before the warm-up steps")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -280,7 +282,8 @@ def run_ours(args, ws, rank, local):
     name = args.workload
     p = WORKLOADS[name][0]()
     mode = args.mode or "f64"
-    cfg = rbf.config_for(p, mixed=(mode == "mixed"), factor_precision=rbf.RBF_FP32 if mode == "mixed" else rbf.RBF_FP64)
+    cfg = rbf.config_for(p, mixed=(mode == "mixed"), factor_precision=rbf.RBF_FP32 if mode == "mixed" else rbf.RBF_FP64,
+                         inner_cutoff=args.inner_cutoff if mode == "mixed" else 0.0)
     xy = torch.from_numpy(p.xy).cuda()
     f = torch.from_numpy(p.f).cuda()
     w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
@@ -373,7 +376,8 @@ def run_ours(args, ws, rank, local):
     if not args.no_extra:
         other = "mixed" if mode == "f64" else "f64"
         c2 = rbf.config_for(p, mixed=(other == "mixed"),
-                            factor_precision=rbf.RBF_FP32 if other == "mixed" else rbf.RBF_FP64)
+                            factor_precision=rbf.RBF_FP32 if other == "mixed" else rbf.RBF_FP64,
+                            inner_cutoff=args.inner_cutoff if other == "mixed" else 0.0)
         step(c2)
         ts, inf2 = [], None
         for _ in range(max(1, min(args.steps, 3))):
@@ -416,7 +420,9 @@ def run_ours(args, ws, rank, local):
         out = {"metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if mode == "f64" else "f32-inner/f64-outer", "data": "synthetic",
-               "config": {**workload_config(name, p, mode), "tuned": tuned}, "ok": ok, "solve": info,
+               "config": {**workload_config(name, p, mode), "tuned": tuned,
+                          "inner_cutoff_sigmas": args.inner_cutoff if mode == "mixed" else None},
+               "ok": ok, "solve": info,
                "step_ms": [round(t, 3) for t in times], "roofline": roofline, "breakdown_ms": breakdown,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "other_precision": extra}
@@ -443,6 +449,7 @@ def batch_config(args, probs, mode: str) -> dict:
             "n_min": int(ns.min()), "n_max": int(ns.max()), "cutoff_sigmas": 8.6,
             "rasm": "4x4 lattice-point cores + 1-point ring", "gmres_restart": 30, "rtol": 1e-13,
             "max_iters_per_problem": args.max_iters, "precision": mode,
+            "inner_cutoff_sigmas": args.inner_cutoff if mode == "mixed" else None,
             "l2": "flushed (256 MB write) before each timed step", "parallelism": "replicas"}
 
 
@@ -554,7 +561,8 @@ def run_batch(args, ws, rank, local):
     h = ctx.handle
 
     def sparams(md):
-        return rbf.RbfSolveParams(1e-13, 30, args.max_iters, int(md == "mixed"), args.max_iters, 1e-5)
+        return rbf.RbfSolveParams(1e-13, 30, args.max_iters, int(md == "mixed"), args.max_iters, 1e-5,
+                                  args.inner_cutoff if md == "mixed" else 0.0)
 
     def step(md, xy_t=xy, f_t=f, w_t=w):
         w_t.zero_()
@@ -704,7 +712,7 @@ def serve_config(args, probs) -> dict:
             "n_points_total": int(ns.sum()), "n_min": int(ns.min()), "n_max": int(ns.max()),
             "cutoff_sigmas": 8.6, "rasm": "4x4 lattice-point cores + 1-point ring (FP32 inverses)",
             "gmres_restart": 30, "rtol": 1e-13, "max_iters_per_request": args.max_iters,
-            "precision": "mixed", "slots": args.slots, "rates": args.rates,
+            "precision": "mixed", "inner_cutoff_sigmas": args.inner_cutoff, "slots": args.slots, "rates": args.rates,
             "l2": "inputs (2.4-96 MB per request, 1.5 GB per sweep) far above L2", "parallelism": "replicas"}
 
 
@@ -747,7 +755,7 @@ def run_serve(args, ws, rank, local):
         f = torch.from_numpy(p.f.copy()).pin_memory().numpy()
         w = torch.zeros(p.n, dtype=torch.float64).pin_memory().numpy()
         cfg = rbf.config_for(p, mixed=True, factor_precision=rbf.RBF_FP32, max_iters=args.max_iters,
-                             max_refine=args.max_iters)
+                             max_refine=args.max_iters, inner_cutoff=args.inner_cutoff)
         host.append((xy, f, w, cfg))
     srv = rbf.Server(local, slots=args.slots)
 

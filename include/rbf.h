@@ -83,6 +83,10 @@ typedef struct {
     int mixed;            /* 1: FP32 inner GMRES + FP64 iterative refinement */
     int max_refine;       /* mixed only: outer refinement steps (0 = 40) */
     double inner_rtol;    /* mixed only: relative tolerance of each inner solve (0 = 1e-5) */
+    double inner_cutoff;  /* mixed only: > 0 runs the FP32 inner solves on a second grid with this shorter
+                           * cutoff, in units of sigma (6.1: dropped entries below e^-18.6 = 8e-9, under
+                           * FP32 rounding); the FP64 residual keeps r_c. 0 = the r_c grid. Not used with
+                           * the additive Schwarz variant. The grid is built at the first such solve. */
 } rbf_solve_params;
 
 typedef struct {

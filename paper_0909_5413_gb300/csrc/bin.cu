@@ -315,6 +315,22 @@ __global__ void k_target_count(const double* __restrict__ xe, int64_t m, const P
     atomicAdd(&counts[cell], 1);
 }
 
+__global__ void k_remap(const int32_t* __restrict__ idx, int64_t cnt, const int32_t* __restrict__ map,
+                        int32_t* __restrict__ out)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < cnt) out[e] = map[idx[e]];
+}
+
+// out[q] = r[perm[q]] * scale (inner order from main order, FP32)
+__global__ void k_inner_gather_scaled(const double* __restrict__ r, const int32_t* __restrict__ perm, int64_t n,
+                                      const double* __restrict__ scale, float* __restrict__ out)
+{
+    const double f = *scale;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = (float)(r[perm[q]] * f);
+}
+
 __global__ void k_widen_i32_i64(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -529,6 +545,96 @@ rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cud
 {
     RBF_LAUNCH(ctx, k_permute_to_user, blocks_for(ctx->ev.m, 256), 256, 0, st, sorted, ctx->ev.perm.p, ctx->ev.m,
                user);
+    return RBF_OK;
+}
+
+rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
+{
+    InnerGrid& G = ctx->in;
+    const int64_t n = ctx->n;
+    const int nprob = (int)ctx->nprob;
+    std::vector<Prob> P = ctx->prob_h;   // the main tables with the grid replaced
+    int64_t ncell = 0;
+    for (int b = 0; b < nprob; ++b) {
+        Prob& q = P[b];
+        q.c = std::min(ri_sigmas * q.sigma, q.rc);
+        const double fx = std::floor((q.xmax - q.xmin) / q.c), fy = std::floor((q.ymax - q.ymin) / q.c);
+        if (!(fx < 1.0e9) || !(fy < 1.0e9)) return fail(ctx, RBF_ERR_INVALID_ARG, "inner grid too large");
+        q.ncx = (int64_t)fx + 1;
+        q.ncy = (int64_t)fy + 1;
+        q.k = 1;
+        q.ca = (float)(q.c * (double)q.a_loc);
+        q.cellbase = ncell;
+        ncell += q.ncx * q.ncy;
+        if (ncell > ((int64_t)1 << 28)) return fail(ctx, RBF_ERR_INVALID_ARG, "inner grid: too many cells");
+    }
+    G.ready = false;
+    G.ncell = ncell;
+    RBF_CHECK(ensure(ctx, G.prob, nprob));
+    RBF_CUDA(ctx, cudaMemcpyAsync(G.prob.p, P.data(), sizeof(Prob) * nprob, cudaMemcpyHostToDevice, st));
+    RBF_CHECK(ensure(ctx, G.cell_u, n));
+    RBF_CHECK(ensure(ctx, G.cell_s, n));
+    RBF_CHECK(ensure(ctx, G.perm, n));
+    RBF_CHECK(ensure(ctx, G.iperm, n));
+    RBF_CHECK(ensure(ctx, G.tmp, std::max<int64_t>(n, 2 * kNumSMs + 1)));
+    RBF_CHECK(ensure(ctx, G.counts, ncell + 1));
+    RBF_CHECK(ensure(ctx, G.cell_start, ncell + 1));
+    RBF_CHECK(ensure(ctx, G.pid_cell, ncell));
+    RBF_CHECK(ensure(ctx, G.wcnt, ncell + 1));
+    RBF_CHECK(ensure(ctx, G.woff, ncell + 1));
+    RBF_CHECK(ensure(ctx, G.xy_s, 2 * n));
+    RBF_CHECK(ensure(ctx, G.loc, 2 * n));
+    // counting sort of the main cell-ordered points by inner cell (ties: main position)
+    RBF_CUDA(ctx, cudaMemsetAsync(G.counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
+    RBF_LAUNCH(ctx, k_cell_count, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, G.prob.p, ctx->pid.p, G.cell_u.p,
+               G.counts.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, G.counts.p, G.cell_start.p, ncell, st));
+    RBF_CUDA(ctx, cudaMemsetAsync(G.counts.p, 0, sizeof(int32_t) * (ncell + 1), st));
+    RBF_LAUNCH(ctx, k_cell_scatter, blocks_for(n, 256), 256, 0, st, G.cell_u.p, n, G.cell_start.p, G.counts.p,
+               G.tmp.p);
+    RBF_LAUNCH(ctx, k_cell_rank, blocks_for(ncell * 32, 256), 256, 0, st, G.cell_start.p, ncell, G.tmp.p, G.perm.p);
+    RBF_LAUNCH(ctx, k_gather_sorted, blocks_for(n, 256), 256, 0, st, ctx->xy_s.p, n, G.perm.p, G.cell_u.p, G.xy_s.p,
+               G.iperm.p, G.cell_s.p);
+    RBF_LAUNCH(ctx, k_pid_cells, blocks_for(ncell, 256), 256, 0, st, G.prob.p, nprob, ncell, G.pid_cell.p);
+    RBF_LAUNCH(ctx, k_local_coords, blocks_for(n, 256), 256, 0, st, G.xy_s.p, G.cell_s.p, n, G.prob.p, ctx->pid.p,
+               G.loc.p);
+    // work items of the FP32 kernel and the largest stencil
+    RBF_LAUNCH(ctx, k_work_count, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, G.tile, G.wcnt.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, G.wcnt.p, G.woff.p, ncell, st));
+    int32_t nwork = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&nwork, G.woff.p + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    G.n_work = nwork;
+    RBF_CHECK(ensure(ctx, G.work, 2 * (size_t)std::max<int32_t>(nwork, 1)));
+    RBF_LAUNCH(ctx, k_work_fill, blocks_for(ncell, 256), 256, 0, st, G.wcnt.p, G.woff.p, ncell, G.tile, G.work.p);
+    RBF_LAUNCH(ctx, k_stencil_count, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, G.prob.p, G.pid_cell.p,
+               ncell, G.wcnt.p);
+    int32_t smax = 0;
+    RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &smax, st));
+    G.stage_max = smax;
+    // subdomain lists in inner positions
+    if (ctx->rasm_ready) {
+        int32_t tot[2] = {0, 0};
+        RBF_CUDA(ctx, cudaMemcpyAsync(&tot[0], ctx->core_ptr.p + ctx->nsub, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaMemcpyAsync(&tot[1], ctx->ov_ptr.p + ctx->nsub, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+        RBF_CHECK(ensure(ctx, G.core_idx, std::max<int32_t>(tot[0], 1)));
+        RBF_CHECK(ensure(ctx, G.ov_idx, std::max<int32_t>(tot[1], 1)));
+        RBF_LAUNCH(ctx, k_remap, blocks_for(tot[0], 256), 256, 0, st, ctx->core_idx.p, (int64_t)tot[0], G.iperm.p,
+                   G.core_idx.p);
+        RBF_LAUNCH(ctx, k_remap, blocks_for(tot[1], 256), 256, 0, st, ctx->ov_idx.p, (int64_t)tot[1], G.iperm.p,
+                   G.ov_idx.p);
+    }
+    G.ri_sigmas = ri_sigmas;
+    G.ready = true;
+    return RBF_OK;
+}
+
+rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double* scale_dev, float* out_inner,
+                               cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, k_inner_gather_scaled, blocks_for(std::min<int64_t>(ctx->n, 16 * kNumSMs * 256), 256), 256, 0, st,
+               r_main, ctx->in.perm.p, ctx->n, scale_dev, out_inner);
     return RBF_OK;
 }
 

@@ -334,6 +334,7 @@ static rbf_status bin_batch(rbf_ctx* ctx, const double* xy_dev, const int64_t* p
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->binned = false;
     ctx->rasm_ready = false;
+    ctx->in.ready = false;
     ctx->prob_h.assign((size_t)nprob, Prob{});
     for (int64_t b = 0; b < nprob; ++b) {
         if (ptr[b + 1] <= ptr[b])
@@ -433,6 +434,7 @@ static rbf_status rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params, 
     }
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     ctx->rasm_ready = false;
+    ctx->in.ready = false;   // its re-indexed lists follow the subdomains
     ctx->rasm_precision = precision;
     ctx->rasm_additive = params[0].additive != 0;
     ctx->nsub = nsub;

@@ -71,6 +71,23 @@ struct Prob {
 
 }  // namespace rbf
 
+// The inner grid of the mixed form: the points binned again with cells of side
+// r_i (a shorter cutoff for the FP32 inner matvec, stencil 3 x 3), their own
+// order (inner position q holds main cell-ordered point perm[q]), and the
+// subdomain lists re-indexed into that order.
+struct InnerGrid {
+    bool ready = false;
+    double ri_sigmas = 0.0;
+    int tile = 64;
+    int stage_max = 0;
+    int64_t ncell = 0, n_work = 0;
+    rbf::DevArray<int32_t> perm, iperm, cell_u, cell_s, counts, cell_start, tmp, work, pid_cell, wcnt, woff;
+    rbf::DevArray<int32_t> ov_idx, core_idx;
+    rbf::DevArray<double> xy_s;
+    rbf::DevArray<float> loc;
+    rbf::DevArray<rbf::Prob> prob;
+};
+
 // Evaluation points binned into a context's grid (rbf_eval).
 struct EvalBins {
     int64_t m = 0, nwork = 0;
@@ -125,6 +142,8 @@ struct rbf_ctx {
     rbf::DevArray<double> exp2048; // 2^(-j/2048), j < 2048
     rbf::DevArray<unsigned long long> fxtab;   // T1 (1024) then T2 (1024), Q1.63
     EvalBins ev;                   // rbf_eval targets
+    InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
+    bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
     double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)
@@ -220,6 +239,11 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
                           cudaStream_t st);
 
 rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st);
+// Builds ctx->in for an inner cutoff of ri_sigmas sigma (after binning and RASM setup).
+rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st);
+// Main cell order <-> inner order for the FP32 hand-offs of the mixed form.
+rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double* scale_dev, float* out_inner,
+                               cudaStream_t st);
 rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int tile, DevArray<int32_t>& work,
                       int64_t* nwork_out, cudaStream_t st);
 rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float* y, cudaStream_t st);

@@ -336,6 +336,14 @@ __global__ void __launch_bounds__(kDotThreads)
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 32] = tot;
 }
 
+// w[perm[q]] += a d[q]: the correction of an inner solve run in the inner grid's order.
+__global__ void k_axpy_scaled_perm(double* __restrict__ w, const float* __restrict__ d, double a,
+                                   const int32_t* __restrict__ perm, int64_t n)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        w[perm[q]] = fma(a, (double)d[q], w[perm[q]]);
+}
+
 // FP32 copy of an FP64 vector scaled by a device factor: out = in * (*factor)
 __global__ void k_to_f32_scaled(const double* __restrict__ in, int64_t n, const double* __restrict__ factor,
                                 float* __restrict__ out)
@@ -554,6 +562,15 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
         }
         float2* loc = nullptr;
         RBF_CHECK(ensure_local_coords(ctx, &loc, st));
+        // the inner grid (shorter cutoff, own order) for the FP32 inner solves
+        const bool use_inner = p->inner_cutoff > 0.0 && !ctx->rasm_additive;
+        if (use_inner && (!ctx->in.ready || ctx->in.ri_sigmas != p->inner_cutoff))
+            RBF_CHECK(bin_inner(ctx, p->inner_cutoff, st));
+        struct InnerOn {
+            rbf_ctx* c;
+            ~InnerOn() { c->inner_on = false; }
+        } inner_guard{ctx};
+        ctx->inner_on = use_inner;
         // FP32 Krylov basis and four FP32 work vectors (u, t, b, d), in V's storage
         const int64_t ldv = ((n + 63) / 64) * 64;
         RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 5) * ldv + 1) / 2 + 1));
@@ -581,7 +598,8 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
             // inner solve of A d = b, b = r / |r| (norm 1), from d = 0, restarted on
             // the FP32 inner residual b - A d until inner_rtol or kMaxInnerCycles
             RBF_LAUNCH(ctx, k_cycle_init, 1, 1, 0, st, g, m, 1);   // inv_beta = 1 / |r|
-            RBF_LAUNCH(ctx, k_to_f32_scaled, stream_blocks(n), 256, 0, st, r64, n, &g->inv_beta, bf);
+            if (use_inner) RBF_CHECK(inner_gather_scaled(ctx, r64, &g->inv_beta, bf, st));
+            else RBF_LAUNCH(ctx, k_to_f32_scaled, stream_blocks(n), 256, 0, st, r64, n, &g->inv_beta, bf);
             RBF_CUDA(ctx, cudaMemsetAsync(df, 0, sizeof(float) * n, st));
             for (int ic = 0; ic < kMaxInnerCycles && it < max_iters; ++ic) {
                 if (ic == 0) {
@@ -609,7 +627,10 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
                 ++cycles;
                 if (est <= inner_rtol) break;
             }
-            RBF_LAUNCH(ctx, k_axpy_scaled, stream_blocks(n), 256, 0, st, w, df, rnorm, n);
+            if (use_inner)
+                RBF_LAUNCH(ctx, k_axpy_scaled_perm, stream_blocks(n), 256, 0, st, w, df, rnorm, ctx->in.perm.p, n);
+            else
+                RBF_LAUNCH(ctx, k_axpy_scaled, stream_blocks(n), 256, 0, st, w, df, rnorm, n);
             ++refine;
         }
     }

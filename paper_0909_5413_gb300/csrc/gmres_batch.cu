@@ -307,13 +307,14 @@ __global__ void k_bscale(T* __restrict__ x, int64_t n, const int32_t* __restrict
 }
 
 // FP32 copy of r scaled by the problem's inv_beta (inner start of the mixed form).
+// (with perm: out[q] = r[perm[q]] ..., the inner grid's order from the main one)
 __global__ void k_bto_f32_scaled(const double* __restrict__ r, int64_t n, const int32_t* __restrict__ pid,
                                  const GmresDev* __restrict__ gm, const int32_t* __restrict__ active,
-                                 float* __restrict__ out)
+                                 const int32_t* __restrict__ perm, float* __restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int pb = pid[i];
-        if (active[pb]) out[i] = (float)(r[i] * gm[pb].inv_beta);
+        if (active[pb]) out[i] = (float)(r[perm ? perm[i] : i] * gm[pb].inv_beta);
     }
 }
 
@@ -346,12 +347,13 @@ __global__ void k_bcombine(const T* __restrict__ V, int64_t ldv, const GmresDev*
     }
 }
 
+// w += u (with perm: w[perm[i]] += u[i], u in the inner grid's order)
 template <class T>
 __global__ void k_baxpy(double* __restrict__ w, const T* __restrict__ u, const int32_t* __restrict__ pid,
-                        const int32_t* __restrict__ active, int64_t n)
+                        const int32_t* __restrict__ active, const int32_t* __restrict__ perm, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (active[pid[i]]) w[i] += (double)u[i];
+        if (active[pid[i]]) w[perm ? perm[i] : i] += (double)u[i];
 }
 
 __global__ void k_binit(GmresDev* __restrict__ gm, int nprob, double rtol)
@@ -468,7 +470,8 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
     RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);
     RBF_LAUNCH(ctx, (k_bcombine<T>), bstream_blocks(n), 256, 0, st, V, ldv, B.gm, B.pid, B.active, t, n);
     RBF_CHECK(BOps<T>::minv(ctx, t, u, st));
-    RBF_LAUNCH(ctx, (k_baxpy<T>), bstream_blocks(n), 256, 0, st, w, u, B.pid, B.active, n);
+    RBF_LAUNCH(ctx, (k_baxpy<T>), bstream_blocks(n), 256, 0, st, w, u, B.pid, B.active,
+               (sizeof(T) == 4 && ctx->inner_on) ? (const int32_t*)ctx->in.perm.p : nullptr, n);
     return RBF_OK;
 }
 
@@ -507,10 +510,14 @@ rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double*
     return RBF_OK;
 }
 
-// Clears the matvec / apply mask when the batched solve returns.
+// Clears the matvec / apply mask and the inner-grid switch when the batched solve returns.
 struct MaskGuard {
     rbf_ctx* ctx;
-    ~MaskGuard() { ctx->active_mask = nullptr; }
+    ~MaskGuard()
+    {
+        ctx->active_mask = nullptr;
+        ctx->inner_on = false;
+    }
 };
 
 }  // namespace
@@ -617,6 +624,11 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             "rbf_solve_batch: the mixed form needs rbf_rasm_setup_batch with precision RBF_FP32");
         RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 3) * ldv + 1) / 2 + 1));
         Vf = (float*)ctx->V.p;
+        // the inner grid (shorter cutoff, own order) for the FP32 inner solves
+        if (p->inner_cutoff > 0.0 && !ctx->rasm_additive) {
+            if (!ctx->in.ready || ctx->in.ri_sigmas != p->inner_cutoff) RBF_CHECK(bin_inner(ctx, p->inner_cutoff, st));
+            ctx->inner_on = true;   // cleared with the mask when the solve returns
+        }
         uf = Vf + (int64_t)(m + 1) * ldv;
         tf = uf + ldv;
     }
@@ -661,7 +673,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             RBF_LAUNCH(ctx, k_bscale<double>, bstream_blocks(n), 256, 0, st, V64, n, ctx->pid.p, gm, 0, active);
             RBF_CHECK(run_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
         } else {
-            RBF_LAUNCH(ctx, k_bto_f32_scaled, bstream_blocks(n), 256, 0, st, r64, n, ctx->pid.p, gm, active, Vf);
+            RBF_LAUNCH(ctx, k_bto_f32_scaled, bstream_blocks(n), 256, 0, st, r64, n, ctx->pid.p, gm, active,
+                       ctx->inner_on ? (const int32_t*)ctx->in.perm.p : nullptr, Vf);
             RBF_CHECK(run_cycle<float>(B, Vf, ldv, m, uf, tf, w));
         }
         RBF_CHECK(read_stat());

@@ -48,12 +48,14 @@ struct MvParams {
     int stage;                 // sources staged per pass (a multiple of 32)
 };
 
-// Stage size for a context: the largest stencil, rounded up to 32, capped.
-inline int stage_for(const rbf_ctx* ctx, int cap)
+// Stage size for the largest stencil of a binning: rounded up to 32, capped.
+inline int round_stage(int stage_max, int cap)
 {
-    const int s = ((std::max(ctx->stage_max, 1) + 31) / 32) * 32;
+    const int s = ((std::max(stage_max, 1) + 31) / 32) * 32;
     return std::min(s, cap);
 }
+
+inline int stage_for(const rbf_ctx* ctx, int cap) { return round_stage(ctx->stage_max, cap); }
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -395,12 +397,10 @@ rbf_status dispatch_f64(rbf_ctx* ctx, MvParams P, int64_t nwork, const double* w
 }
 
 template <int T>
-rbf_status launch_f32(rbf_ctx* ctx, MvParams P, const float* w, float* y, cudaStream_t st)
+rbf_status launch_f32(rbf_ctx* ctx, MvParams P, int64_t nwork, const float* w, float* y, cudaStream_t st)
 {
-    P.work = ctx->mv_work32.p;
-    P.stage = stage_for(ctx, kMv32StageMax);
     const size_t smem = 3 * (size_t)(P.stage + 4) * sizeof(float);
-    RBF_LAUNCH(ctx, k_matvec_f32v2<T>, (unsigned)ctx->n_work32, T, smem, st, P, w, y);
+    RBF_LAUNCH(ctx, k_matvec_f32v2<T>, (unsigned)nwork, T, smem, st, P, w, y);
     return RBF_OK;
 }
 
@@ -447,12 +447,28 @@ rbf_status ensure_local_coords(rbf_ctx* ctx, float2** loc, cudaStream_t)
 rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_MATVEC_F32, st));
-    if (ctx->n_work32 > 0) {
-        const MvParams P = mv_params(ctx);
-        switch (ctx->tile32) {
-        case 32: RBF_CHECK(launch_f32<32>(ctx, P, w, y, st)); break;
-        case 64: RBF_CHECK(launch_f32<64>(ctx, P, w, y, st)); break;
-        default: RBF_CHECK(launch_f32<128>(ctx, P, w, y, st)); break;
+    MvParams P = mv_params(ctx);
+    int tile = ctx->tile32;
+    int64_t nwork = ctx->n_work32;
+    P.work = ctx->mv_work32.p;
+    P.stage = stage_for(ctx, kMv32StageMax);
+    if (ctx->inner_on) {   // the mixed form's inner grid (shorter cutoff, its own order)
+        const InnerGrid& G = ctx->in;
+        P.loc = G.loc.p;
+        P.cell_s = G.cell_s.p;
+        P.cell_start = G.cell_start.p;
+        P.work = G.work.p;
+        P.prob = G.prob.p;
+        P.pid_cell = G.pid_cell.p;
+        P.stage = round_stage(G.stage_max, kMv32StageMax);
+        tile = G.tile;
+        nwork = G.n_work;
+    }
+    if (nwork > 0) {
+        switch (tile) {
+        case 32: RBF_CHECK(launch_f32<32>(ctx, P, nwork, w, y, st)); break;
+        case 64: RBF_CHECK(launch_f32<64>(ctx, P, nwork, w, y, st)); break;
+        default: RBF_CHECK(launch_f32<128>(ctx, P, nwork, w, y, st)); break;
         }
     }
     return prof_end(ctx, RBF_PROF_MATVEC_F32, st);

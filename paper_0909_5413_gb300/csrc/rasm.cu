@@ -350,6 +350,12 @@ rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStrea
 rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
+    if (ctx->inner_on) {   // vectors in the inner grid's order: the lists re-indexed into it
+        RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
+                   ctx->in.ov_idx.p, ctx->core_ptr.p, ctx->in.core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub,
+                   ctx->pid_sub.p, ctx->active_mask, r, z);
+        return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
+    }
     const bool add = ctx->rasm_additive;
     float* out = add ? ctx->asm_u32.p : z;
     RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p, ctx->ov_idx.p,

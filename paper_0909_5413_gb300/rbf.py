@@ -46,7 +46,7 @@ class RbfRasmParams(C.Structure):
 
 class RbfSolveParams(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("max_iters", C.c_int), ("mixed", C.c_int),
-                ("max_refine", C.c_int), ("inner_rtol", C.c_double)]
+                ("max_refine", C.c_int), ("inner_rtol", C.c_double), ("inner_cutoff", C.c_double)]
 
 
 class RbfSolveInfo(C.Structure):
@@ -354,6 +354,7 @@ class SolverConfig:
     mixed: bool = False
     max_refine: int = 40
     inner_rtol: float = 1e-5
+    inner_cutoff: float = 0.0       # mixed only: shorter cutoff (in sigma) of the FP32 inner grid; 0 = r_c
 
     def params(self) -> RbfParams:
         return RbfParams(self.sigma, self.cutoff, self.cell_size, int(self.normalized), self.tile_f64, self.tile_f32)
@@ -364,7 +365,7 @@ class SolverConfig:
 
     def solve(self) -> RbfSolveParams:
         return RbfSolveParams(self.rtol, self.restart, self.max_iters, int(self.mixed), self.max_refine,
-                              self.inner_rtol)
+                              self.inner_rtol, self.inner_cutoff)
 
 
 class Context:
