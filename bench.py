@@ -84,17 +84,11 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, 
 MATVEC_F32_INSTR_PER_CANDIDATE = 6.55
 
 
-def candidate_pairs(rbf, h) -> int:
+def candidate_pairs(rbf, h, inner: bool) -> int:
     """Source-target pairs the FP32 matvec evaluates: for every cell, its points
-    times the points of its (2k+1)^2 stencil (k = 1 for cells of side r_c)."""
-    import torch
-    ncx, ncy, _ = rbf.rbf_get_grid(h)
-    cs = torch.empty(ncx * ncy + 1, dtype=torch.int32, device="cuda")
-    rbf.rbf_get_bins(h, None, cs)
-    cnt = np.diff(cs.cpu().numpy().astype(np.int64)).reshape(ncy, ncx)
-    pad = np.pad(cnt, 1)
-    win = sum(pad[1 + dy:1 + dy + ncy, 1 + dx:1 + dx + ncx] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
-    return int((cnt * win).sum())
+    times the points of its 3 x 3 stencil, on the grid that matvec walks (the
+    inner grid of the mixed form when one is set, else the cells of side r_c)."""
+    return rbf.rbf_count_candidates(h, 1 if inner else 0)
 
 
 WORKLOADS = {
@@ -359,12 +353,14 @@ def run_ours(args, ws, rank, local):
             roofline = f64_matvec_roofline(pairs, avg_s, n_mv, traffic=(name == "lattice1024" and default_cfg))
             roofline["algorithmic_bytes_per_launch"] = 32 * p.n
         else:
-            cand = candidate_pairs(rbf, h)
+            cand = candidate_pairs(rbf, h, inner=args.inner_cutoff > 0)
             peak = ISSUE_PEAK_LANE_INSTR / MATVEC_F32_INSTR_PER_CANDIDATE
             roofline = {"kernel": "k_matvec_f32v2", "bound": "alu", "achieved": cand / avg_s / 1e12,
                         "peak": peak / 1e12, "unit": "Tcandidate/s", "frac": cand / avg_s / peak,
                         "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
                         "candidates_per_launch": cand, "in_cutoff_pairs_per_launch": pairs,
+                        "grid": (f"inner, cells of {args.inner_cutoff} sigma" if args.inner_cutoff > 0
+                                 else "cells of side r_c"),
                         "peak_note": ("SM issue rate 152 x 4 x 32 lanes x 2.07 GHz = 40.3 T lane-instr/s over "
                                       f"{MATVEC_F32_INSTR_PER_CANDIDATE} lane-instr per candidate (ncu)")}
     breakdown = {nm: {"launches": prof[k][0], "ms": round(prof[k][1], 3)} for nm, k in

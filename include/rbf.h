@@ -309,6 +309,14 @@ rbf_status rbf_get_subdomains(rbf_ctx* ctx, int32_t* core_ptr_dev, int32_t* core
                               int32_t* ov_idx_dev, rbf_stream stream);
 /* Total number of (i, j) pairs with r2 <= r_c^2 (i = j included), host output. */
 rbf_status rbf_count_neighbors(rbf_ctx* ctx, int64_t* total, rbf_stream stream);
+/* Candidate pairs the FP32 matvec evaluates (the unmasked work of the
+ * cell-list method, Sec. 3.1): the sum over cells of (points in the cell) x
+ * (points in its 3 x 3 stencil), host output. grid 0: the cells of side r_c
+ * built by rbf_bin / rbf_bin_batch; grid 1: the inner grid of the mixed form
+ * (cells of side inner_cutoff * sigma), which exists after a mixed solve with
+ * inner_cutoff > 0 and until the next binning or subdomain setup
+ * (RBF_ERR_STATE otherwise). Synchronises `stream`. */
+rbf_status rbf_count_candidates(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream);
 /* Neighbour lists, CSR over targets in user order (ptr: n + 1 int64; idx:
  * `capacity` int32), each row the user indices j with r2_ij <= r_c^2,
  * ascending. INVALID_ARG if capacity is below the total. */

@@ -235,6 +235,28 @@ __global__ void k_stencil_count(const int32_t* __restrict__ cell_start, const Pr
     out[c] = (int32_t)min(s, (int64_t)0x7fffffff);
 }
 
+// Candidate pairs of a cell grid: each cell's points times the points of its
+// (2k+1)^2 stencil, summed over the cells (64-bit, one atomic per warp).
+__global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const Prob* __restrict__ prob,
+                                  const int32_t* __restrict__ pid_cell, int64_t ncell,
+                                  unsigned long long* __restrict__ total)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (c < ncell) {
+        const Prob& P = prob[pid_cell[c]];
+        const int64_t lc = c - P.cellbase, cx = lc % P.ncx, cy = lc / P.ncx;
+        const int64_t x0 = max(cx - P.k, (int64_t)0), x1 = min(cx + P.k, P.ncx - 1);
+        const int64_t y0 = max(cy - P.k, (int64_t)0), y1 = min(cy + P.k, P.ncy - 1);
+        int64_t s = 0;
+        for (int64_t yy = y0; yy <= y1; ++yy)
+            s += cell_start[P.cellbase + yy * P.ncx + x1 + 1] - cell_start[P.cellbase + yy * P.ncx + x0];
+        v = (unsigned long long)((int64_t)(cell_start[c + 1] - cell_start[c]) * s);
+    }
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
 __global__ void k_permute_to_sorted(const double* __restrict__ user, const int32_t* __restrict__ perm, int64_t n,
                                     double* __restrict__ sorted)
 {
@@ -635,6 +657,35 @@ rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double*
 {
     RBF_LAUNCH(ctx, k_inner_gather_scaled, blocks_for(std::min<int64_t>(ctx->n, 16 * kNumSMs * 256), 256), 256, 0, st,
                r_main, ctx->in.perm.p, ctx->n, scale_dev, out_inner);
+    return RBF_OK;
+}
+
+rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st)
+{
+    const int32_t* cs;
+    const Prob* pr;
+    const int32_t* pc;
+    int64_t ncell;
+    if (grid == 0) {
+        cs = ctx->cell_start.p;
+        pr = ctx->prob.p;
+        pc = ctx->pid_cell.p;
+        ncell = ctx->ncell_total;
+    } else {
+        const InnerGrid& G = ctx->in;
+        cs = G.cell_start.p;
+        pr = G.prob.p;
+        pc = G.pid_cell.p;
+        ncell = G.ncell;
+    }
+    RBF_CHECK(ensure(ctx, ctx->count_u64, 1));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->count_u64.p, 0, sizeof(unsigned long long), st));
+    if (ncell > 0)
+        RBF_LAUNCH(ctx, k_candidate_count, blocks_for(ncell, 256), 256, 0, st, cs, pr, pc, ncell, ctx->count_u64.p);
+    unsigned long long h = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&h, ctx->count_u64.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *total = (int64_t)h;
     return RBF_OK;
 }
 

@@ -635,6 +635,16 @@ rbf_status rbf_count_neighbors(rbf_ctx* ctx, int64_t* total, rbf_stream stream)
     return neighbor_lists(ctx, nullptr, nullptr, 0, total, S(stream));
 }
 
+rbf_status rbf_count_candidates(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream)
+{
+    if (!ctx || !total || (grid != 0 && grid != 1)) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_count_candidates: call rbf_bin first");
+    if (grid == 1 && !ctx->in.ready)
+        return fail(ctx, RBF_ERR_STATE, "rbf_count_candidates: no inner grid (run a mixed solve with inner_cutoff > 0)");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    return count_candidates(ctx, grid, total, S(stream));
+}
+
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;

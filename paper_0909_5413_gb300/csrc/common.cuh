@@ -144,6 +144,7 @@ struct rbf_ctx {
     EvalBins ev;                   // rbf_eval targets
     InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
     bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
+    rbf::DevArray<unsigned long long> count_u64;   // one 64-bit counter (rbf_count_candidates)
     double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)
@@ -241,6 +242,8 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
 rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st);
 // Builds ctx->in for an inner cutoff of ri_sigmas sigma (after binning and RASM setup).
 rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st);
+// Sum over the cells of grid 0 (r_c cells) or 1 (inner grid) of points x stencil points.
+rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
 // Main cell order <-> inner order for the FP32 hand-offs of the mixed form.
 rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double* scale_dev, float* out_inner,
                                cudaStream_t st);

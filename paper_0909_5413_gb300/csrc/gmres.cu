@@ -17,6 +17,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "ortho.cuh"
 #include "vecops.cuh"
 
 namespace rbf {
@@ -29,138 +30,55 @@ namespace {
 
 constexpr int kDotBlocksMax = 8 * kNumSMs;
 
-// Vector passes of one Arnoldi step, each a single stream over HBM. The vector
-// range is cut into chunks of kChunk elements; block partial sums go to
-// partial[chunk * 32 + k] and are reduced over chunks in a fixed order.
-constexpr int kChunkPerThread = 16;
-constexpr int kChunk = kDotThreads * kChunkPerThread;
+// Vector passes are cut into chunks of kChunk elements (one block each);
+// block partial sums go to partial[chunk * 32 + k] and are reduced over
+// chunks in a fixed order.
+constexpr int kChunkPerThread = kOrthoPer;
+constexpr int kChunk = kOrthoChunk;
 
-// Dots V_k . x for k < nv: block (k, chunk), k fastest so that the blocks
-// reading one chunk of x run together and find it in L2. FP64 accumulation
-// for FP64 vectors; Dot2 (then FP64) for FP32 vectors.
+// The three vector passes of one CGS2 step (kernels over chunks; the
+// per-chunk code is shared with the batched solver). Block partial sums go
+// to partial[chunk * 32 + k] and are reduced over chunks in a fixed order.
+
+// MODE 0: partial_k = V_k . x over the chunk, one block per (chunk, k), k
+// fastest so that the blocks reading one chunk of x run together and find it
+// in L2.
 template <class T>
 __global__ void __launch_bounds__(kDotThreads)
-    k_dots(const T* __restrict__ V, int64_t ldv, int nv, const T* __restrict__ x, int64_t n,
-           double* __restrict__ partial)
+    k_ortho_dots(const T* __restrict__ V, int64_t ldv, int nv, const T* __restrict__ x, int64_t n,
+                 double* __restrict__ partial)
 {
-    __shared__ double red[kDotThreads / 32];
-    __shared__ DF redf[kDotThreads / 32];
+    __shared__ OrthoRed red;
     const int k = (int)(blockIdx.x % (unsigned)nv);
     const int64_t chunk = blockIdx.x / (unsigned)nv;
-    const int64_t base = chunk * kChunk + threadIdx.x;
-    const T* v = V + k * ldv;
-    double a = 0.0;
-    if constexpr (sizeof(T) == 4) {
-        DF s{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            if (i < n) df_add_prod(s, v[i], x[i]);
-        }
-        const double t = block_sum_df(s, redf);
-        if (threadIdx.x == 0) partial[chunk * 32 + k] = t;
-        return;
-    } else {
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            if (i < n) a = fma((double)v[i], (double)x[i], a);
-        }
-    }
-    double s = block_sum(a, red);
-    if (threadIdx.x == 0) partial[chunk * 32 + k] = s;
+    ortho_dot_one<T>(V + k * ldv, x, chunk * kOrthoChunk, n, red, partial + chunk * 32 + k);
 }
 
-// x -= sum_{k < nv} coef_k V_k (x rounded to T); with NORM, partial sums of |x|^2.
-// FP32 vectors: the FP64 coefficients are split into float pairs and the
-// update is carried in double-float, then rounded once to FP32.
-template <class T, bool NORM>
-__global__ void __launch_bounds__(kDotThreads)
-    k_update(const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef, T* __restrict__ x,
-             int64_t n, double* __restrict__ partial)
+// MODE 1: x -= V coef (x rounded to T), then partial_k = V_k . x (the chunk
+// of V is read twice, the second time from L2).
+// MODE 2: x -= V coef, partial_0 = |x|^2.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kDotThreads, 2)
+    k_ortho_update(const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef,
+                   T* __restrict__ x, int64_t n, double* __restrict__ partial)
 {
-    __shared__ double cf[kMaxRestart + 1];
-    __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
-    __shared__ double red[kDotThreads / 32];
-    __shared__ DF redf[kDotThreads / 32];
-    if (threadIdx.x < (unsigned)nv) {
-        double c = coef[threadIdx.x];
-        cf[threadIdx.x] = c;
-        float h = (float)c;
-        cf_hi[threadIdx.x] = h;
-        cf_lo[threadIdx.x] = (float)(c - (double)h);
-    }
+    __shared__ OrthoCoef cf;
+    __shared__ OrthoRed red;
+    if (threadIdx.x < (unsigned)nv) ortho_coef_set(cf, (int)threadIdx.x, coef[threadIdx.x]);
     __syncthreads();
-    const int64_t chunk = blockIdx.x;
-    const int64_t base = chunk * kChunk + threadIdx.x;
-    double a = 0.0;
-    if constexpr (sizeof(T) == 4) {
-        DF xl[kChunkPerThread];
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            xl[u].hi = i < n ? (float)x[i] : 0.f;
-            xl[u].lo = 0.f;
-        }
-        for (int k = 0; k < nv; ++k) {
-            const T* v = V + k * ldv;
-            const float ch = cf_hi[k], cl = cf_lo[k];
-#pragma unroll
-            for (int u = 0; u < kChunkPerThread; ++u) {
-                int64_t i = base + (int64_t)u * kDotThreads;
-                if (i < n) {
-                    float vi = v[i];
-                    float h = ch * vi;
-                    float r = fmaf(ch, vi, -h);
-                    df_add(xl[u], -h, fmaf(-cl, vi, -r));
-                }
-            }
-        }
-        DF s{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            if (i < n) {
-                float xs = xl[u].hi + xl[u].lo;
-                x[i] = xs;
-                if (NORM) df_add_prod(s, xs, xs);
-            }
-        }
-        if (NORM) {
-            const double t = block_sum_df(s, redf);
-            if (threadIdx.x == 0) partial[chunk * 32] = t;
-        }
-        return;
+    const int64_t b = (int64_t)blockIdx.x * kOrthoChunk;
+    typename OrthoAcc<T>::type xl[kOrthoPer];
+    ortho_load_x<T>(xl, x, b, n);
+    ortho_apply<T, ortho_group<T>()>(xl, V, ldv, nv, cf, b, n);
+    T xs[kOrthoPer];
+    ortho_store_x<T>(xl, xs, x, b, n);
+    double* out = partial + (int64_t)blockIdx.x * 32;
+    if (MODE == 1) {
+        ortho_dots<T, ortho_group<T>()>(V, ldv, nv, xs, b, n, red, out);
     } else {
-        // vector index outermost, the thread's 16 elements innermost: 16 independent loads in flight
-        double xl[kChunkPerThread];
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            xl[u] = i < n ? (double)x[i] : 0.0;
-        }
-        for (int k = 0; k < nv; ++k) {
-            const T* v = V + k * ldv;
-            const double c = cf[k];
-#pragma unroll
-            for (int u = 0; u < kChunkPerThread; ++u) {
-                int64_t i = base + (int64_t)u * kDotThreads;
-                if (i < n) xl[u] = fma(-c, (double)v[i], xl[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kChunkPerThread; ++u) {
-            int64_t i = base + (int64_t)u * kDotThreads;
-            if (i < n) {
-                T xs = (T)xl[u];
-                x[i] = xs;
-                if (NORM) a = fma((double)xs, (double)xs, a);
-            }
-        }
-    }
-    if (NORM) {
-        double s = block_sum(a, red);
-        if (threadIdx.x == 0) partial[chunk * 32] = s;
+        ortho_warp_sum(ortho_thread_dot<T>(xs, xs, b, n), red, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) out[0] = ortho_block_total<T>(red, 0);
     }
 }
 
@@ -170,7 +88,18 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv
     int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= nv) return;
     double a = 0.0;
-    for (int b = lane; b < nblocks; b += 32) a += partial[(int64_t)b * 32 + k];
+    constexpr int U = 8;   // loads issued together, added in order
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * U) {
+        double p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + 32 * u;
+            p[u] = b < nblocks ? partial[(int64_t)b * 32 + k] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b0 + 32 * u < nblocks) a += p[u];
+    }
     for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
     if (lane == 0) out[k] = a;
 }
@@ -216,35 +145,14 @@ __global__ void k_cycle_init(GmresDev* g, int m, int inner)
     g->j = -1;
 }
 
-// Arnoldi step j: Hessenberg column, previous rotations, new rotation, g update.
-__global__ void k_arnoldi(GmresDev* g, int j)
+// Arnoldi step j (one warp): Hessenberg column, rotations, g, estimate.
+__global__ void k_arnoldi(GmresDev* g, int j, int passes)
 {
-    const int M = kMaxRestart;
-    for (int q = 0; q <= j; ++q) g->H[q * M + j] = g->h1[q] + g->h2[q];
-    double hn = sqrt(fmax(g->nrm2, 0.0));
-    g->H[(j + 1) * M + j] = hn;
-    for (int q = 0; q < j; ++q) {
-        double a = g->H[q * M + j], b = g->H[(q + 1) * M + j];
-        g->H[q * M + j] = g->cs[q] * a + g->sn[q] * b;
-        g->H[(q + 1) * M + j] = -g->sn[q] * a + g->cs[q] * b;
+    arnoldi_column(g, j, passes);
+    if (threadIdx.x == 0) {
+        g->done = (g->est <= g->rtol || g->breakdown) ? 1 : 0;
+        g->j = j;
     }
-    double a = g->H[j * M + j], b = g->H[(j + 1) * M + j];
-    double c, s;
-    if (b == 0.0) { c = 1.0; s = 0.0; }
-    else if (fabs(b) > fabs(a)) { double t = a / b; s = 1.0 / sqrt(1.0 + t * t); c = s * t; }
-    else { double t = b / a; c = 1.0 / sqrt(1.0 + t * t); s = c * t; }
-    g->cs[j] = c;
-    g->sn[j] = s;
-    g->H[j * M + j] = c * a + s * b;
-    g->H[(j + 1) * M + j] = 0.0;
-    g->g[j + 1] = -s * g->g[j];
-    g->g[j] = c * g->g[j];
-    g->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
-    g->breakdown = (hn == 0.0) ? 1 : 0;
-    double fn = sqrt(g->fnorm2);
-    g->est = fabs(g->g[j + 1]) / fn;
-    g->done = (g->est <= g->rtol || g->breakdown) ? 1 : 0;
-    g->j = j;
 }
 
 // y = H(0:k, 0:k)^{-1} g(0:k), upper triangular.
@@ -383,18 +291,14 @@ rbf_status launch_mdot(rbf_ctx* ctx, const T* V, int64_t ldv, int nv, T* x, int6
                        double* out, cudaStream_t st)
 {
     const int64_t nc = num_chunks(n);
-    if (MODE == 2) {
-        RBF_LAUNCH(ctx, (k_update<T, true>), (unsigned)nc, kDotThreads, 0, st, V, ldv, nv, coef, x, n,
+    if (MODE == 0)
+        RBF_LAUNCH(ctx, (k_ortho_dots<T>), (unsigned)(nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, n,
                    ctx->partial.p);
-        RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nc, 1, out);
-        return RBF_OK;
-    }
-    if (MODE == 1)
-        RBF_LAUNCH(ctx, (k_update<T, false>), (unsigned)nc, kDotThreads, 0, st, V, ldv, nv, coef, x, n,
+    else
+        RBF_LAUNCH(ctx, (k_ortho_update<T, MODE>), (unsigned)nc, kDotThreads, 0, st, V, ldv, nv, coef, x, n,
                    ctx->partial.p);
-    RBF_LAUNCH(ctx, (k_dots<T>), (unsigned)(nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, n,
-               ctx->partial.p);
-    RBF_LAUNCH(ctx, k_reduce, 1, 32 * nv, 0, st, ctx->partial.p, (int)nc, nv, out);
+    const int nout = MODE == 2 ? 1 : nv;
+    RBF_LAUNCH(ctx, k_reduce, 1, 32 * nout, 0, st, ctx->partial.p, (int)nc, nout, out);
     return RBF_OK;
 }
 
@@ -459,10 +363,14 @@ rbf_status gmres_cycle(rbf_ctx* ctx, T* V, int64_t ldv, int m, int max_steps, T*
         RBF_CHECK(Ops::amul(ctx, tmp_u, vn, st, loc));
         RBF_CHECK(prof_begin(ctx, RBF_PROF_ORTHO, st));
         RBF_CHECK((launch_mdot<0, T>(ctx, V, ldv, j + 1, vn, n, nullptr, g->h1, st)));
-        RBF_CHECK((launch_mdot<1, T>(ctx, V, ldv, j + 1, vn, n, g->h1, g->h2, st)));
-        RBF_CHECK((launch_mdot<2, T>(ctx, V, ldv, j + 1, vn, n, g->h2, &g->nrm2, st)));
+        if (gs_passes<T>() == 2) {
+            RBF_CHECK((launch_mdot<1, T>(ctx, V, ldv, j + 1, vn, n, g->h1, g->h2, st)));
+            RBF_CHECK((launch_mdot<2, T>(ctx, V, ldv, j + 1, vn, n, g->h2, &g->nrm2, st)));
+        } else {
+            RBF_CHECK((launch_mdot<2, T>(ctx, V, ldv, j + 1, vn, n, g->h1, &g->nrm2, st)));
+        }
         RBF_CHECK(prof_end(ctx, RBF_PROF_ORTHO, st));
-        RBF_LAUNCH(ctx, k_arnoldi, 1, 1, 0, st, g, j);
+        RBF_LAUNCH(ctx, k_arnoldi, 1, 32, 0, st, g, j, gs_passes<T>());
         RBF_LAUNCH(ctx, (k_scale<T>), stream_blocks(n), 256, 0, st, vn, n, &g->inv_h);
         k = j + 1;
         RBF_CHECK(read_status(ctx, st, &ss));

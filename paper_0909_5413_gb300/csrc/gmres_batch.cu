@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ortho.cuh"
 #include "vecops.cuh"
 
 namespace rbf {
@@ -26,8 +27,8 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float
 
 namespace {
 
-constexpr int kBPer = 16;                       // elements per thread (the single solver's chunking)
-constexpr int kBChunk = kDotThreads * kBPer;    // elements per chunk
+constexpr int kBPer = kOrthoPer;       // elements per thread (the single solver's chunking)
+constexpr int kBChunk = kOrthoChunk;   // elements per chunk
 
 enum BField { F_H1 = 0, F_H2 = 1, F_NRM2 = 2, F_BETA2 = 3, F_FNORM2 = 4 };
 
@@ -50,137 +51,54 @@ struct Chunks {
     int64_t nc;
 };
 
-// Dots V_k . x over one chunk (k fastest); 0 for masked problems.
+// The CGS2 vector passes over one chunk (the single solver's per-chunk code;
+// a chunk never spans two problems). Chunks of masked problems write zeros.
+// MODE 0: partial_k = V_k . x, one block per (chunk, k), k fastest.
 template <class T>
 __global__ void __launch_bounds__(kDotThreads)
     k_bdots(const T* __restrict__ V, int64_t ldv, int nv, const T* __restrict__ x, Chunks C,
             const int32_t* __restrict__ active, double* __restrict__ partial)
 {
-    __shared__ double red[kDotThreads / 32];
-    __shared__ DF redf[kDotThreads / 32];
+    __shared__ OrthoRed red;
     const int k = (int)(blockIdx.x % (unsigned)nv);
     const int64_t c = blockIdx.x / (unsigned)nv;
     if (!active[C.pid[c]]) {
         if (threadIdx.x == 0) partial[c * 32 + k] = 0.0;
         return;
     }
-    const int64_t b = C.beg[c], e = C.end[c];
-    const T* v = V + k * ldv;
-    double a = 0.0;
-    if constexpr (sizeof(T) == 4) {
-        DF s{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            if (i < e) df_add_prod(s, v[i], x[i]);
-        }
-        const double t = block_sum_df(s, redf);
-        if (threadIdx.x == 0) partial[c * 32 + k] = t;
-        return;
-    } else {
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            if (i < e) a = fma((double)v[i], (double)x[i], a);
-        }
-    }
-    double s = block_sum(a, red);
-    if (threadIdx.x == 0) partial[c * 32 + k] = s;
+    ortho_dot_one<T>(V + k * ldv, x, C.beg[c], C.end[c], red, partial + c * 32 + k);
 }
 
-// x -= sum_k coef_k V_k with the chunk's problem's coefficients (field h1 or
-// h2 of its state); with NORM, |x|^2 partial sums.
-template <class T, bool NORM>
-__global__ void __launch_bounds__(kDotThreads)
+// MODE 1: x -= V coef with the chunk's problem's coefficients (field h1 or h2
+// of its state), then partial_k = V_k . x. MODE 2: x -= V coef, partial_0 = |x|^2.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kDotThreads, 2)
     k_bupdate(const T* __restrict__ V, int64_t ldv, int nv, GmresDev* __restrict__ gm, int field, T* __restrict__ x,
               Chunks C, const int32_t* __restrict__ active, double* __restrict__ partial)
 {
-    __shared__ double cf[kMaxRestart + 1];
-    __shared__ float cf_hi[kMaxRestart + 1], cf_lo[kMaxRestart + 1];
-    __shared__ double red[kDotThreads / 32];
-    __shared__ DF redf[kDotThreads / 32];
+    __shared__ OrthoCoef cf;
+    __shared__ OrthoRed red;
     const int64_t c = blockIdx.x;
     const int pb = C.pid[c];
+    double* out = partial + c * 32;
     if (!active[pb]) {
-        if (NORM && threadIdx.x == 0) partial[c * 32] = 0.0;
+        if (threadIdx.x < (unsigned)(MODE == 2 ? 1 : nv)) out[threadIdx.x] = 0.0;
         return;
     }
-    if (threadIdx.x < (unsigned)nv) {
-        double v = field_ptr(gm[pb], field)[threadIdx.x];
-        cf[threadIdx.x] = v;
-        float h = (float)v;
-        cf_hi[threadIdx.x] = h;
-        cf_lo[threadIdx.x] = (float)(v - (double)h);
-    }
+    if (threadIdx.x < (unsigned)nv) ortho_coef_set(cf, (int)threadIdx.x, field_ptr(gm[pb], field)[threadIdx.x]);
     __syncthreads();
     const int64_t b = C.beg[c], e = C.end[c];
-    double a = 0.0;
-    if constexpr (sizeof(T) == 4) {
-        DF xl[kBPer];
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            xl[u].hi = i < e ? (float)x[i] : 0.f;
-            xl[u].lo = 0.f;
-        }
-        for (int k = 0; k < nv; ++k) {
-            const T* v = V + k * ldv;
-            const float ch = cf_hi[k], cl = cf_lo[k];
-#pragma unroll
-            for (int u = 0; u < kBPer; ++u) {
-                int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-                if (i < e) {
-                    float vi = v[i];
-                    float h = ch * vi;
-                    float r = fmaf(ch, vi, -h);
-                    df_add(xl[u], -h, fmaf(-cl, vi, -r));
-                }
-            }
-        }
-        DF s{0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            if (i < e) {
-                float xs = xl[u].hi + xl[u].lo;
-                x[i] = xs;
-                if (NORM) df_add_prod(s, xs, xs);
-            }
-        }
-        if (NORM) {
-            const double t = block_sum_df(s, redf);
-            if (threadIdx.x == 0) partial[c * 32] = t;
-        }
-        return;
+    typename OrthoAcc<T>::type xl[kOrthoPer];
+    ortho_load_x<T>(xl, x, b, e);
+    ortho_apply<T, ortho_group<T>()>(xl, V, ldv, nv, cf, b, e);
+    T xs[kOrthoPer];
+    ortho_store_x<T>(xl, xs, x, b, e);
+    if (MODE == 1) {
+        ortho_dots<T, ortho_group<T>()>(V, ldv, nv, xs, b, e, red, out);
     } else {
-        double xl[kBPer];
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            xl[u] = i < e ? (double)x[i] : 0.0;
-        }
-        for (int k = 0; k < nv; ++k) {
-            const T* v = V + k * ldv;
-            const double cc = cf[k];
-#pragma unroll
-            for (int u = 0; u < kBPer; ++u) {
-                int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-                if (i < e) xl[u] = fma(-cc, (double)v[i], xl[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kBPer; ++u) {
-            int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
-            if (i < e) {
-                T xs = (T)xl[u];
-                x[i] = xs;
-                if (NORM) a = fma((double)xs, (double)xs, a);
-            }
-        }
-    }
-    if (NORM) {
-        double s = block_sum(a, red);
-        if (threadIdx.x == 0) partial[c * 32] = s;
+        ortho_warp_sum(ortho_thread_dot<T>(xs, xs, b, e), red, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) out[0] = ortho_block_total<T>(red, 0);
     }
 }
 
@@ -218,7 +136,19 @@ __global__ void k_breduce(const double* __restrict__ partial, Chunks C, int npro
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (pb >= nprob || k >= nv || !active[pb]) return;
     double a = 0.0;
-    for (int c = C.cptr[pb] + lane; c < C.cptr[pb + 1]; c += 32) a += partial[(int64_t)c * 32 + k];
+    constexpr int U = 8;   // loads issued together, added in order
+    const int c1 = C.cptr[pb + 1];
+    for (int c0 = C.cptr[pb] + lane; c0 < c1; c0 += 32 * U) {
+        double p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + 32 * u;
+            p[u] = c < c1 ? partial[(int64_t)c * 32 + k] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c0 + 32 * u < c1) a += p[u];
+    }
     for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
     if (lane == 0) field_ptr(gm[pb], field)[k] = a;
 }
@@ -243,39 +173,20 @@ __global__ void k_bcycle_init(GmresDev* __restrict__ gm, int nprob, int m, int m
     g.j = 0;       // steps taken in this cycle
 }
 
-// Arnoldi step j of every active problem that has not stopped in this cycle.
-__global__ void k_barnoldi(GmresDev* __restrict__ gm, int nprob, int j, const int32_t* __restrict__ active)
+// Arnoldi step j of every active problem that has not stopped in this cycle
+// (one warp per problem).
+__global__ void k_barnoldi(GmresDev* __restrict__ gm, int nprob, int j, const int32_t* __restrict__ active,
+                           int passes)
 {
-    int pb = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pb = blockIdx.x;
     if (pb >= nprob || !active[pb]) return;
-    GmresDev& gg = gm[pb];
-    if (gg.done) return;
-    GmresDev* g = &gg;
-    const int M = kMaxRestart;
-    for (int q = 0; q <= j; ++q) g->H[q * M + j] = g->h1[q] + g->h2[q];
-    double hn = sqrt(fmax(g->nrm2, 0.0));
-    g->H[(j + 1) * M + j] = hn;
-    for (int q = 0; q < j; ++q) {
-        double a = g->H[q * M + j], b = g->H[(q + 1) * M + j];
-        g->H[q * M + j] = g->cs[q] * a + g->sn[q] * b;
-        g->H[(q + 1) * M + j] = -g->sn[q] * a + g->cs[q] * b;
+    GmresDev* g = &gm[pb];
+    if (g->done) return;
+    arnoldi_column(g, j, passes);
+    if (threadIdx.x == 0) {
+        g->done = (g->est <= g->rtol || g->breakdown || j + 1 >= g->budget) ? 1 : 0;
+        g->j = j + 1;
     }
-    double a = g->H[j * M + j], b = g->H[(j + 1) * M + j];
-    double c, s;
-    if (b == 0.0) { c = 1.0; s = 0.0; }
-    else if (fabs(b) > fabs(a)) { double t = a / b; s = 1.0 / sqrt(1.0 + t * t); c = s * t; }
-    else { double t = b / a; c = 1.0 / sqrt(1.0 + t * t); s = c * t; }
-    g->cs[j] = c;
-    g->sn[j] = s;
-    g->H[j * M + j] = c * a + s * b;
-    g->H[(j + 1) * M + j] = 0.0;
-    g->g[j + 1] = -s * g->g[j];
-    g->g[j] = c * g->g[j];
-    g->inv_h = hn > 0.0 ? 1.0 / hn : 0.0;
-    g->breakdown = (hn == 0.0) ? 1 : 0;
-    g->est = fabs(g->g[j + 1]) / sqrt(g->fnorm2);
-    g->done = (g->est <= g->rtol || g->breakdown || j + 1 >= g->budget) ? 1 : 0;
-    g->j = j + 1;
 }
 
 __global__ void k_bsolve_y(GmresDev* __restrict__ gm, int nprob, const int32_t* __restrict__ active)
@@ -404,18 +315,14 @@ struct BatchWork {
     template <int MODE, class T>
     rbf_status mdot(const T* V, int64_t ldv, int nv, T* x, int field_in, int field_out)
     {
-        if (MODE == 2) {
-            RBF_LAUNCH(ctx, (k_bupdate<T, true>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x, C,
+        if (MODE == 0)
+            RBF_LAUNCH(ctx, (k_bdots<T>), (unsigned)(C.nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, C,
                        active, partial);
-            RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, partial, C, nprob, 1, gm, field_out, active);
-            return RBF_OK;
-        }
-        if (MODE == 1)
-            RBF_LAUNCH(ctx, (k_bupdate<T, false>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x,
+        else
+            RBF_LAUNCH(ctx, (k_bupdate<T, MODE>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x,
                        C, active, partial);
-        RBF_LAUNCH(ctx, (k_bdots<T>), (unsigned)(C.nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, C, active,
-                   partial);
-        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nv, 0, st, partial, C, nprob, nv, gm, field_out, active);
+        const int nout = MODE == 2 ? 1 : nv;
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out, active);
         return RBF_OK;
     }
 };
@@ -462,9 +369,13 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
         RBF_CHECK(BOps<T>::minv(ctx, vj, u, st));
         RBF_CHECK(BOps<T>::amul(ctx, u, vn, st));
         RBF_CHECK((B.mdot<0, T>(V, ldv, j + 1, vn, -1, F_H1)));
-        RBF_CHECK((B.mdot<1, T>(V, ldv, j + 1, vn, F_H1, F_H2)));
-        RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H2, F_NRM2)));
-        RBF_LAUNCH(ctx, k_barnoldi, pb_blocks, 128, 0, st, B.gm, B.nprob, j, B.active);
+        if (gs_passes<T>() == 2) {
+            RBF_CHECK((B.mdot<1, T>(V, ldv, j + 1, vn, F_H1, F_H2)));
+            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H2, F_NRM2)));
+        } else {
+            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H1, F_NRM2)));
+        }
+        RBF_LAUNCH(ctx, k_barnoldi, (unsigned)B.nprob, 32, 0, st, B.gm, B.nprob, j, B.active, gs_passes<T>());
         RBF_LAUNCH(ctx, (k_bscale<T>), bstream_blocks(n), 256, 0, st, vn, n, B.pid, B.gm, 1, B.active);
     }
     RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);

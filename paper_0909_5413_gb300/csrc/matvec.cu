@@ -256,10 +256,14 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
 
 // FP32 matvec for the inner solves of the mixed form: block per (cell, T
 // targets), sources staged in shared memory as FP32 offsets from the target
-// cell's corner (scaled so the kernel is exp2(-|dX|^2)), two sources per
-// packed f32x2 step. No cutoff mask: the entries beyond r_c that this adds
-// back are below 2^-53 relative to the diagonal, far under FP32 rounding, and
-// the outer FP64 residual uses the exact truncated matrix.
+// cell's corner (scaled so the kernel is exp2(-|dX|^2)), four sources per
+// step as two packed f32x2 pairs (three 128-bit shared loads). No cutoff
+// mask: every source of the 3 x 3 stencil counts. On cells of side r_c the
+// entries this adds beyond r_c are below 2^-53 relative to the diagonal, far
+// under FP32 rounding; on the inner grid (cells of side r_i < r_c) every pair
+// within r_i counts and the pairs beyond r_i that are dropped are below
+// exp(-r_i^2 / (2 sigma^2)) each. The outer FP64 residual uses the exact
+// truncated matrix either way.
 template <int T>
 __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __restrict__ w, float* __restrict__ y)
 {
@@ -302,39 +306,45 @@ __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __r
     }
     __syncthreads();
     const int S = row_pre[nrow];
-    float2 acc2 = make_float2(0.f, 0.f);
+    float2 acc2 = make_float2(0.f, 0.f), acc2b = make_float2(0.f, 0.f);
     for (int base = 0; base < S; base += kStage) {
         const int ns = min(kStage, S - base);
         if (base > 0) __syncthreads();
         for (int idx = tid; idx < ns; idx += T) {
-            int g = base + idx;
+            const int g = base + idx;
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
-            int q = row_beg[r] + (g - row_pre[r]);
-            int cq = P.cell_s[q] - cbase;
-            SXs[idx] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
-            SYs[idx] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
+            const int q = row_beg[r] + (g - row_pre[r]);
+            const int yy = y0 + r;                           // the stencil row gives the cell's y
+            const int xq = P.cell_s[q] - cbase - yy * ncx;   // and its x
+            const float2 l = reinterpret_cast<const float2*>(P.loc)[q];
+            SXs[idx] = l.x + (float)(xq - cx) * ca;
+            SYs[idx] = l.y + (float)(yy - cy) * ca;
             SWs[idx] = w[q];
         }
-        if (tid == 0 && (ns & 1)) {   // pad to an even count with a far, zero-weight source
-            SXs[ns] = 1.0e4f;
-            SYs[ns] = 1.0e4f;
-            SWs[ns] = 0.0f;
+        if (tid < ((4 - (ns & 3)) & 3)) {   // pad to a multiple of 4 with far, zero-weight sources
+            SXs[ns + tid] = 1.0e4f;
+            SYs[ns + tid] = 1.0e4f;
+            SWs[ns + tid] = 0.0f;
         }
         __syncthreads();
-        const int ns2 = (ns + 1) >> 1;
-#pragma unroll 4
-        for (int s = 0; s < ns2; ++s) {
-            float2 sx = reinterpret_cast<const float2*>(SXs)[s];
-            float2 sy = reinterpret_cast<const float2*>(SYs)[s];
-            float2 sw = reinterpret_cast<const float2*>(SWs)[s];
-            float2 dx = f2_sub(t2, sx), dy = f2_sub(u2, sy);
-            float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
-            float2 e = make_float2(ex2_approx(-r2.x), ex2_approx(-r2.y));
-            acc2 = f2_fma(e, sw, acc2);
+        const int ns4 = (ns + 3) >> 2;
+#pragma unroll 2
+        for (int s = 0; s < ns4; ++s) {
+            const float4 sx = reinterpret_cast<const float4*>(SXs)[s];
+            const float4 sy = reinterpret_cast<const float4*>(SYs)[s];
+            const float4 sw = reinterpret_cast<const float4*>(SWs)[s];
+            const float2 dx0 = f2_sub(t2, make_float2(sx.x, sx.y)), dy0 = f2_sub(u2, make_float2(sy.x, sy.y));
+            const float2 dx1 = f2_sub(t2, make_float2(sx.z, sx.w)), dy1 = f2_sub(u2, make_float2(sy.z, sy.w));
+            const float2 r0 = f2_fma(dy0, dy0, f2_mul(dx0, dx0));
+            const float2 r1 = f2_fma(dy1, dy1, f2_mul(dx1, dx1));
+            const float2 e0 = make_float2(ex2_approx(-r0.x), ex2_approx(-r0.y));
+            const float2 e1 = make_float2(ex2_approx(-r1.x), ex2_approx(-r1.y));
+            acc2 = f2_fma(e0, make_float2(sw.x, sw.y), acc2);
+            acc2b = f2_fma(e1, make_float2(sw.z, sw.w), acc2b);
         }
     }
-    if (active) y[p] = (acc2.x + acc2.y) * knorm;
+    if (active) y[p] = ((acc2.x + acc2.y) + (acc2b.x + acc2b.y)) * knorm;
 }
 
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)

@@ -234,6 +234,8 @@ int64_t rbf_request_footprint(const rbf_request* r)
     per += mixed ? 4.0 * (m + 3) : 8.0 * (m + 1);      // Krylov basis
     per += (f32 ? 4.0 : 8.0) * n_ov;                   // subdomain inverses W_i (n_ov per core point)
     if (mixed && !f32) per += 4.0 * n_ov;              // FP32 copy made for the inner solve
+    if (mixed && r->solve.inner_cutoff > 0.0)          // inner grid: order, coordinates, re-indexed lists
+        per += 52.0 + 4.0 * n_ov / n_core;
     return (int64_t)(n * per * 1.05) + kFixedBytes;
 }
 

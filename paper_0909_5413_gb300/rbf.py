@@ -28,7 +28,8 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_device_bytes", "rbf_profile_enable", "rbf_profile_read", "rbf_debug_exp", "rbf_matvec_noalloc",
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
-            "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune"]
+            "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
+            "rbf_count_candidates"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -115,6 +116,7 @@ def load(path: str | None = None):
     L.rbf_get_subdomain_sizes.argtypes = [P, I64, I64, I64, I64]
     L.rbf_get_subdomains.argtypes = [P, P, P, P, P, P]
     L.rbf_count_neighbors.argtypes = [P, I64, P]
+    L.rbf_count_candidates.argtypes = [P, C.c_int, I64, P]
     L.rbf_get_neighbors.argtypes = [P, P, P, C.c_int64, P]
     L.rbf_status_string.argtypes = [C.c_int]
     L.rbf_status_string.restype = C.c_char_p
@@ -294,6 +296,13 @@ def rbf_get_subdomains(ctx, core_ptr, core_idx, ov_ptr, ov_idx, stream=None) -> 
 def rbf_count_neighbors(ctx, stream=None) -> int:
     t = C.c_int64()
     _check(ctx, load().rbf_count_neighbors(ctx, C.byref(t), _stream(stream)))
+    return t.value
+
+
+def rbf_count_candidates(ctx, grid: int = 0, stream=None) -> int:
+    """Candidate pairs of the FP32 matvec on grid 0 (cells of side r_c) or 1 (the mixed form's inner grid)."""
+    t = C.c_int64()
+    _check(ctx, load().rbf_count_candidates(ctx, int(grid), C.byref(t), _stream(stream)))
     return t.value
 
 

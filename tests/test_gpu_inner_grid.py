@@ -105,3 +105,34 @@ def test_inner_grid_batch_alone_equals_mix(rbf):
         st1, _, w1, _ = batch_solve(rbf, [p])
         assert st1 == 0
         np.testing.assert_array_equal(w1, wb[ptr[b]:ptr[b + 1]])
+
+
+def host_candidates(xy, c):
+    """Sum over the cells of side c (origin at the bounding box's low corner,
+    the last cell clamped) of points x points of the 3 x 3 stencil."""
+    lo, hi = xy.min(axis=0), xy.max(axis=0)
+    nc = (np.floor((hi - lo) / c) + 1).astype(np.int64)
+    cell = np.minimum(np.floor((xy - lo) / c).astype(np.int64), nc - 1)
+    cnt = np.zeros((nc[1], nc[0]), dtype=np.int64)
+    np.add.at(cnt, (cell[:, 1], cell[:, 0]), 1)
+    pad = np.pad(cnt, 1)
+    win = sum(pad[1 + dy:1 + dy + nc[1], 1 + dx:1 + dx + nc[0]] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    return int((cnt * win).sum())
+
+
+def test_candidate_counts_of_both_grids(rbf):
+    p = W.lattice_problem(120, 0.85, seed=72)
+    cfg = rbf.config_for(p, mixed=True, factor_precision=rbf.RBF_FP32, inner_cutoff=6.1)
+    ctx = rbf.Context(0)
+    ctx.bin(dev(p.xy), cfg)
+    ctx.rasm_setup(cfg)
+    assert rbf.rbf_count_candidates(ctx.handle, 0) == host_candidates(p.xy, p.cutoff)
+    with pytest.raises(rbf.RbfError):
+        rbf.rbf_count_candidates(ctx.handle, 1)
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, _ = ctx.solve(dev(p.f), w, cfg)
+    assert st == 0
+    got = rbf.rbf_count_candidates(ctx.handle, 1)
+    assert got == host_candidates(p.xy, min(6.1 * p.sigma, p.cutoff))
+    assert got < rbf.rbf_count_candidates(ctx.handle, 0)
+    ctx.close()
