@@ -76,19 +76,27 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
         pxf[a] = fx_coord(px[a], fxs, sh);
         pyf[a] = fx_coord(py[a], fxs, sh);
     }
-    // positions of the kept rows inside the overlap list (ascending)
-    if (lane == 0) {
-        int q = 0;
-        for (int a = 0; a < n; ++a)
-            if (full || core_of[ov_idx[b + a]] == (int32_t)sub) cpos[q++] = a;
+    // positions of the kept rows inside the overlap list (ascending): flags,
+    // then a ballot prefix count per group of 32
+    int nkept = 0;
+    for (int a0 = 0; a0 < n; a0 += 32) {
+        const int a = a0 + lane;
+        const bool keep = a < n && (full || core_of[ov_idx[b + a]] == (int32_t)sub);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) cpos[nkept + __popc(m & ((1u << lane) - 1u))] = a;
+        nkept += __popc(m);
     }
     __syncwarp();
     // A_i (lower triangle and diagonal): the entries of A~ itself, truncated by
     // the same FP64 pair test and valued by the same fixed-point evaluation as
-    // the FP64 matvec, so A_i = R_i A~ R_i^T holds for the operator the GPU applies
+    // the FP64 matvec, so A_i = R_i A~ R_i^T holds for the operator the GPU
+    // applies. The packed index t = i (i + 1) / 2 + j runs over the lanes.
     (void)s;
-    for (int i = 0; i < n; ++i)
-        for (int j = lane; j <= i; j += 32) {
+    {
+        const int total = n * (n + 1) / 2;
+        int i = 0, j = lane;
+        while (j > i) { j -= i + 1; ++i; }
+        for (int t = lane; t < total; t += 32) {
             double dx = __dsub_rn(px[i], px[j]), dy = __dsub_rn(py[i], py[j]);
             double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
             double v = 0.0;
@@ -98,18 +106,22 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
                 v = (F == 52 ? kernel_fx52(du, dv, M, fxtab, fxtab + kFxTab)
                              : kernel_fx(du, dv, F, M, fxtab, fxtab + kFxTab)) * knorm;
             }
-            A[tri(i, j)] = v;
+            A[t] = v;
+            j += 32;
+            while (j > i) { j -= i + 1; ++i; }
         }
+    }
     __syncwarp();
     // right-looking Cholesky, lower triangle in place; a pivot below 1e-14 of
     // the diagonal k(0) counts as not positive definite (numerically singular,
-    // e.g. two coincident points)
+    // e.g. two coincident points). The trailing update of step j runs over
+    // the packed pairs (i, k), j < k <= i, spread over the lanes.
     bool ok = true;
     const double pivot_min = 1e-14 * knorm;
     for (int j = 0; j < n; ++j) {
         double d = A[tri(j, j)];
         if (!(d > pivot_min)) { ok = false; d = 1.0; }
-        const double ljj = sqrt(d), inv = 1.0 / ljj;
+        const double inv = rsqrt(d), ljj = d * inv;
         __syncwarp();
         for (int i = j + 1 + lane; i < n; i += 32) A[tri(i, j)] = A[tri(i, j)] * inv;
         if (lane == 0) {
@@ -117,9 +129,14 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
             dinv[j] = inv;
         }
         __syncwarp();
-        for (int i = j + 1 + lane; i < n; i += 32) {
-            double lij = A[tri(i, j)];
-            for (int kk = j + 1; kk <= i; ++kk) A[tri(i, kk)] -= lij * A[tri(kk, j)];
+        const int m = n - 1 - j, total = m * (m + 1) / 2;
+        int ii = 0, kk = lane;
+        while (kk > ii) { kk -= ii + 1; ++ii; }
+        for (int t = lane; t < total; t += 32) {
+            const int i = j + 1 + ii, k = j + 1 + kk;
+            A[tri(i, k)] -= A[tri(i, j)] * A[tri(k, j)];
+            kk += 32;
+            while (kk > ii) { kk -= ii + 1; ++ii; }
         }
         __syncwarp();
     }
@@ -127,28 +144,39 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
         if (lane == 0) atomicExch(status, RBF_ERR_NOT_SPD);
         return;
     }
-    // 32 kept rows at a time: lane c computes x = A_i^{-1} e_{cpos[c]} (= row
+    // Kept rows of A_i^{-1}: column c solves L L^T x = e_{cpos[c]} (= row
     // cpos[c] of A_i^{-1}, A_i symmetric) in its own column buffer, L read by
-    // all lanes in lockstep, then the warp writes the chunk to W_i, stored
-    // column-major (W[off + a * nc + c] = x_c[a]: consecutive lanes, consecutive c)
+    // all lanes in lockstep. With at most 16 kept rows per pass, two lanes
+    // share a column (even / odd terms of each row sum, combined by a
+    // shuffle; both lanes write every entry, so each reads its own writes);
+    // the forward solve starts at the pass's first unit position (the
+    // entries above it are zero). The warp then writes the pass to W_i,
+    // stored column-major (W[off + a * nc + c] = x_c[a]).
     const int64_t off = w_off[sub];
-    double* x = X + (size_t)lane * xstride;
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-        const int c = c0 + lane;
+    const int Lc = nc <= 16 ? 2 : 1;
+    const int per_pass = 32 / Lc;
+    const int h = lane % Lc;
+    double* x = X + (size_t)(lane / Lc) * xstride;
+    for (int c0 = 0; c0 < nc; c0 += per_pass) {
+        const int c = c0 + lane / Lc;
         const bool act = c < nc;
-        const int cp = act ? cpos[c] : 0;
-        for (int i = 0; i < n; ++i) {                 // L y = e_cp
-            double v = (i == cp) ? 1.0 : 0.0;
-            for (int kk = 0; kk < i; ++kk) v -= A[tri(i, kk)] * x[kk];
-            x[i] = v * dinv[i];
+        const int cp = act ? cpos[c] : n;
+        const int cpmin = __reduce_min_sync(0xffffffffu, cp);
+        for (int i = 0; i < cpmin; ++i) x[i] = 0.0;
+        for (int i = cpmin; i < n; ++i) {            // L y = e_cp
+            double sum = 0.0;
+            for (int k = cpmin + h; k < i; k += Lc) sum = fma(A[tri(i, k)], x[k], sum);
+            if (Lc == 2) sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+            x[i] = ((i == cp ? 1.0 : 0.0) - sum) * dinv[i];
         }
-        for (int i = n - 1; i >= 0; --i) {            // L^T x = y
-            double v = x[i];
-            for (int kk = i + 1; kk < n; ++kk) v -= A[tri(kk, i)] * x[kk];
-            x[i] = v * dinv[i];
+        for (int i = n - 1; i >= 0; --i) {           // L^T x = y
+            double sum = 0.0;
+            for (int k = i + 1 + h; k < n; k += Lc) sum = fma(A[tri(k, i)], x[k], sum);
+            if (Lc == 2) sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+            x[i] = (x[i] - sum) * dinv[i];
         }
         if (act)
-            for (int a = 0; a < n; ++a) {
+            for (int a = h; a < n; a += Lc) {
                 const double v = x[a];
                 if (W64) W64[off + (int64_t)a * nc + c] = v;
                 if (W32) W32[off + (int64_t)a * nc + c] = (float)v;
