@@ -41,17 +41,17 @@ UNIT = "ms"
 
 # The FP64 matvec's kernel value is computed on the integer pipes (fixed-point
 # exp), so the FP64 pipe no longer bounds it; what does is the SM's instruction
-# issue (65 % of issue slots, ALU pipe 51 %, the rest latency). Peak from unit
+# issue (64 % of issue slots, ALU pipe 52 %, the rest latency). Peak from unit
 # counts and clocks: 152 SMs x 4 partitions x 32 lanes x 2.07 GHz = 40.3 T
 # lane-instructions/s. One ncu capture of this revision
-# (profiles/matvec_f64_lattice1024.md) measured 164.2 issued lane-instructions
+# (profiles/matvec_f64_lattice1024.md) measured 154.3 issued lane-instructions
 # per in-cutoff pair (all lanes of each issued warp instruction, idle lockstep
-# lanes included), which puts the issue ceiling at 245 G pairs/s; the roofline
+# lanes included), which puts the issue ceiling at 261 G pairs/s; the roofline
 # fraction is live pairs/s over that ceiling.
 ISSUE_PEAK_LANE_INSTR = 152 * 4 * 32 * 2.07e9
-MATVEC_F64_REV = "fixed-point-v4"
-MATVEC_F64_INSTR_PER_PAIR = {"fixed-point-v4": 164.2}
-MATVEC_F64_TRAFFIC = {"fixed-point-v4": 37_992_960}   # lattice1024, dram read + write per launch (ncu)
+MATVEC_F64_REV = "fixed-point-v5"
+MATVEC_F64_INSTR_PER_PAIR = {"fixed-point-v4": 164.2, "fixed-point-v5": 154.3}
+MATVEC_F64_TRAFFIC = {"fixed-point-v4": 37_992_960, "fixed-point-v5": 37_978_112}   # lattice1024, dram r + w (ncu)
 # The FP64 view, for comparison: 26 FP64-equivalent flops per pair (dx, dy 2; r2 3;
 # argument 1; exp 18; accumulate 2) against the FP64 ALU peak 152 x 2 DFMA/clk x 2 x 2.07 GHz.
 FLOPS_PER_PAIR_F64 = 26
@@ -78,10 +78,13 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, 
 
 
 # The FP32 matvec (inner solves of the mixed form) evaluates every staged
-# candidate pair (no cutoff mask); ncu measured 6.55 issued lane-instructions
-# per candidate (profiles/mixed_kernels_lattice1024.md), so the same issue
-# rate caps it at 6.15 T candidates/s.
-MATVEC_F32_INSTR_PER_CANDIDATE = 6.55
+# candidate pair (no cutoff mask); on the inner grid (cells of 6.1 sigma,
+# 64-target tiles) ncu measured 7.0 issued lane-instructions per candidate
+# (profiles/mixed_kernels_lattice1024.md), so the same issue rate caps it at
+# 5.75 T candidates/s. Its DRAM traffic there: 17,077,248 B per launch.
+MATVEC_F32_REV = "inner-4src-v3"
+MATVEC_F32_INSTR_PER_CANDIDATE = 7.0
+MATVEC_F32_TRAFFIC = 17_077_248
 
 
 def candidate_pairs(rbf, h, inner: bool) -> int:
@@ -355,9 +358,11 @@ def run_ours(args, ws, rank, local):
         else:
             cand = candidate_pairs(rbf, h, inner=args.inner_cutoff > 0)
             peak = ISSUE_PEAK_LANE_INSTR / MATVEC_F32_INSTR_PER_CANDIDATE
+            default_f32 = name == "lattice1024" and args.inner_cutoff == 6.1 and not args.tune
             roofline = {"kernel": "k_matvec_f32v2", "bound": "alu", "achieved": cand / avg_s / 1e12,
                         "peak": peak / 1e12, "unit": "Tcandidate/s", "frac": cand / avg_s / peak,
-                        "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
+                        "traffic": MATVEC_F32_TRAFFIC if default_f32 else None, "kernel_rev": MATVEC_F32_REV,
+                        "avg_launch_ms": avg_s * 1e3, "launches": n_mv,
                         "candidates_per_launch": cand, "in_cutoff_pairs_per_launch": pairs,
                         "grid": (f"inner, cells of {args.inner_cutoff} sigma" if args.inner_cutoff > 0
                                  else "cells of side r_c"),

@@ -257,6 +257,39 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
+// Order-preserving selection of matvec work items (cell, first target) and
+// subdomains whose problem is active: flags, an exclusive scan, a scatter.
+__global__ void k_flag_work(const int32_t* __restrict__ work, int64_t nwork, const int32_t* __restrict__ pid_cell,
+                            const int32_t* __restrict__ active, int32_t* __restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nwork) flag[i] = active[pid_cell[work[2 * i]]] ? 1 : 0;
+}
+
+__global__ void k_scatter_work(const int32_t* __restrict__ work, int64_t nwork, const int32_t* __restrict__ flag,
+                               const int32_t* __restrict__ pos, int32_t* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nwork && flag[i]) {
+        out[2 * (int64_t)pos[i]] = work[2 * i];
+        out[2 * (int64_t)pos[i] + 1] = work[2 * i + 1];
+    }
+}
+
+__global__ void k_flag_sub(const int32_t* __restrict__ pid_sub, int64_t nsub, const int32_t* __restrict__ active,
+                           int32_t* __restrict__ flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nsub) flag[i] = active[pid_sub[i]] ? 1 : 0;
+}
+
+__global__ void k_scatter_sub(int64_t nsub, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                              int32_t* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nsub && flag[i]) out[pos[i]] = (int32_t)i;
+}
+
 __global__ void k_permute_to_sorted(const double* __restrict__ user, const int32_t* __restrict__ perm, int64_t n,
                                     double* __restrict__ sorted)
 {
@@ -686,6 +719,59 @@ rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t
     RBF_CUDA(ctx, cudaMemcpyAsync(&h, ctx->count_u64.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
     *total = (int64_t)h;
+    return RBF_OK;
+}
+
+namespace {
+
+rbf_status select_work(rbf_ctx* ctx, const int32_t* work, int64_t nwork, const int32_t* pid_cell,
+                       const int32_t* active, DevArray<int32_t>& out, int64_t* nout, cudaStream_t st)
+{
+    RBF_CHECK(ensure(ctx, ctx->al.flag, std::max<int64_t>(nwork, 1)));
+    RBF_CHECK(ensure(ctx, ctx->al.pos, std::max<int64_t>(nwork, 1) + 1));
+    RBF_CHECK(ensure(ctx, out, 2 * std::max<int64_t>(nwork, 1)));
+    if (nwork == 0) {
+        *nout = 0;
+        return RBF_OK;
+    }
+    RBF_LAUNCH(ctx, k_flag_work, blocks_for(nwork, 256), 256, 0, st, work, nwork, pid_cell, active, ctx->al.flag.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, ctx->al.flag.p, ctx->al.pos.p, nwork, st));
+    RBF_LAUNCH(ctx, k_scatter_work, blocks_for(nwork, 256), 256, 0, st, work, nwork, ctx->al.flag.p, ctx->al.pos.p,
+               out.p);
+    int32_t cnt = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, ctx->al.pos.p + nwork, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *nout = cnt;
+    return RBF_OK;
+}
+
+}  // namespace
+
+rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t st)
+{
+    ctx->al.on = false;
+    RBF_CHECK(select_work(ctx, ctx->mv_work.p, ctx->n_work, ctx->pid_cell.p, active, ctx->al.w64, &ctx->al.n64, st));
+    if (ctx->inner_on)
+        RBF_CHECK(select_work(ctx, ctx->in.work.p, ctx->in.n_work, ctx->in.pid_cell.p, active, ctx->al.w32,
+                              &ctx->al.n32, st));
+    else
+        RBF_CHECK(select_work(ctx, ctx->mv_work32.p, ctx->n_work32, ctx->pid_cell.p, active, ctx->al.w32,
+                              &ctx->al.n32, st));
+    const int64_t nsub = ctx->nsub;
+    RBF_CHECK(ensure(ctx, ctx->al.flag, std::max<int64_t>(nsub, 1)));
+    RBF_CHECK(ensure(ctx, ctx->al.pos, std::max<int64_t>(nsub, 1) + 1));
+    RBF_CHECK(ensure(ctx, ctx->al.sub, std::max<int64_t>(nsub, 1)));
+    int32_t cnt = 0;
+    if (nsub > 0) {
+        RBF_LAUNCH(ctx, k_flag_sub, blocks_for(nsub, 256), 256, 0, st, ctx->pid_sub.p, nsub, active, ctx->al.flag.p);
+        RBF_CHECK(exclusive_scan_i32(ctx, ctx->al.flag.p, ctx->al.pos.p, nsub, st));
+        RBF_LAUNCH(ctx, k_scatter_sub, blocks_for(nsub, 256), 256, 0, st, nsub, ctx->al.flag.p, ctx->al.pos.p,
+                   ctx->al.sub.p);
+        RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, ctx->al.pos.p + nsub, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    ctx->al.nsub = cnt;
+    ctx->al.on = true;
     return RBF_OK;
 }
 

@@ -177,11 +177,21 @@ struct rbf_ctx {
     rbf::DevArray<int32_t> bactive;    // per-problem active / zero masks
     rbf::DevArray<double> bstat;       // per-problem summary for the host
     int batch_rounds = 0;
+    int batch_compactions = 0;              // work-list compactions of the last batched solve
     const int32_t* active_mask = nullptr;   // problems the matvec / apply skip when 0 (null: none)
     cudaStream_t bstream = nullptr;         // capturable stream of the batched solver
     cudaEvent_t bevent = nullptr;
     cudaGraphExec_t bgraph = nullptr;       // captured Arnoldi cycle of the batched solver
     uint64_t bgraph_launches = 0;           // kernels in that graph
+    // Work lists of the batched solver restricted to the problems still active
+    // (built when most problems have stopped; used by the matvecs and the apply
+    // while `on`; cleared when the solve returns). Order-preserving subsets of
+    // the full lists, so every problem's sums run in the same order.
+    struct ActiveLists {
+        bool on = false;
+        rbf::DevArray<int32_t> w64, w32, sub, flag, pos;
+        int64_t n64 = 0, n32 = 0, nsub = 0;
+    } al;
 };
 
 namespace rbf {
@@ -242,6 +252,8 @@ rbf_status neighbor_lists(rbf_ctx* ctx, int64_t* ptr, int32_t* idx, int64_t capa
 rbf_status bin_targets(rbf_ctx* ctx, const double* xe, int64_t m, cudaStream_t st);
 // Builds ctx->in for an inner cutoff of ri_sigmas sigma (after binning and RASM setup).
 rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st);
+// Builds ctx->al from the per-problem mask `active` (device) and sets al.on.
+rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t st);
 // Sum over the cells of grid 0 (r_c cells) or 1 (inner grid) of points x stencil points.
 rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
 // Main cell order <-> inner order for the FP32 hand-offs of the mixed form.

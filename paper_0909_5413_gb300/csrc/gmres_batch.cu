@@ -203,18 +203,19 @@ __global__ void k_bsolve_y(GmresDev* __restrict__ gm, int nprob, const int32_t* 
 }
 
 // x *= the problem's factor (inv_beta if which = 0, inv_h if which = 1).
+// x *= inv_beta (which 0) or inv_h (which 1) of the chunk's problem, one block
+// per chunk (chunks of stopped problems and of a broken-down step skipped).
 template <class T>
-__global__ void k_bscale(T* __restrict__ x, int64_t n, const int32_t* __restrict__ pid,
-                         const GmresDev* __restrict__ gm, int which, const int32_t* __restrict__ active)
+__global__ void k_bscale(T* __restrict__ x, Chunks C, const GmresDev* __restrict__ gm, int which,
+                         const int32_t* __restrict__ active)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int pb = pid[i];
-        if (!active[pb]) continue;
-        const GmresDev& g = gm[pb];
-        if (which == 1 && g.done && g.breakdown) continue;
-        double f = which == 0 ? g.inv_beta : g.inv_h;
-        x[i] = (T)((double)x[i] * f);
-    }
+    const int64_t c = blockIdx.x;
+    const int pb = C.pid[c];
+    if (!active[pb]) return;
+    const GmresDev& g = gm[pb];
+    if (which == 1 && g.done && g.breakdown) return;
+    const double f = which == 0 ? g.inv_beta : g.inv_h;
+    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = (T)((double)x[i] * f);
 }
 
 // FP32 copy of r scaled by the problem's inv_beta (inner start of the mixed form).
@@ -376,7 +377,7 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
             RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H1, F_NRM2)));
         }
         RBF_LAUNCH(ctx, k_barnoldi, (unsigned)B.nprob, 32, 0, st, B.gm, B.nprob, j, B.active, gs_passes<T>());
-        RBF_LAUNCH(ctx, (k_bscale<T>), bstream_blocks(n), 256, 0, st, vn, n, B.pid, B.gm, 1, B.active);
+        RBF_LAUNCH(ctx, (k_bscale<T>), (unsigned)B.C.nc, 256, 0, st, vn, B.C, B.gm, 1, B.active);
     }
     RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);
     RBF_LAUNCH(ctx, (k_bcombine<T>), bstream_blocks(n), 256, 0, st, V, ldv, B.gm, B.pid, B.active, t, n);
@@ -428,6 +429,7 @@ struct MaskGuard {
     {
         ctx->active_mask = nullptr;
         ctx->inner_on = false;
+        ctx->al.on = false;
     }
 };
 
@@ -472,7 +474,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     }
     cptr[nprob] = (int32_t)cb.size();
     const int64_t nc = (int64_t)cb.size();
-    RBF_CHECK(ensure(ctx, ctx->bch, 3 * (size_t)nc + nprob + 1));
+    const size_t ctab = 3 * (size_t)nc + nprob + 1;   // one chunk table; the second half holds the compacted one
+    RBF_CHECK(ensure(ctx, ctx->bch, 2 * ctab));
     int32_t* dch = ctx->bch.p;
     RBF_CUDA(ctx, cudaMemcpyAsync(dch, cb.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st));
     RBF_CUDA(ctx, cudaMemcpyAsync(dch + nc, ce.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, st));
@@ -549,13 +552,15 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     std::vector<std::vector<double>> hist(nprob);
     std::vector<int> stagnated(nprob, 0);
     std::vector<int32_t> left(nprob, 0);
+    int compact_at = nprob / 2, compactions = 0;
     ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
     batch_graph_reset(ctx);      // buffers may have moved since the last solve
     for (;;) {
         // true FP64 residual of the active problems
         RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
-        RBF_LAUNCH(ctx, k_bresidual, (unsigned)nc, kDotThreads, 0, st, f, ctx->vec_a.p, r64, C, active, B.partial);
-        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, B.partial, C, nprob, 1, gm, F_BETA2, active);
+        RBF_LAUNCH(ctx, k_bresidual, (unsigned)B.C.nc, kDotThreads, 0, st, f, ctx->vec_a.p, r64, B.C, active,
+                   B.partial);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, B.partial, B.C, nprob, 1, gm, F_BETA2, active);
         RBF_CHECK(read_stat());
         int nact = 0;
         for (int b = 0; b < nprob; ++b) {
@@ -575,13 +580,41 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         }
         RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         if (nact == 0) break;
+        if (nact <= compact_at) {
+            // Most problems have stopped: restrict the chunk table, the matvec
+            // work lists and the subdomain list to the active problems (same
+            // order within each problem) and capture the cycle again.
+            std::vector<int32_t> kb, ke, kp, kptr(nprob + 1);
+            for (int b = 0; b < nprob; ++b) {
+                kptr[b] = (int32_t)kb.size();
+                if (!act[b]) continue;
+                for (int32_t c = cptr[b]; c < cptr[b + 1]; ++c) {
+                    kb.push_back(cb[c]);
+                    ke.push_back(ce[c]);
+                    kp.push_back(cp[c]);
+                }
+            }
+            kptr[nprob] = (int32_t)kb.size();
+            const int64_t nk = (int64_t)kb.size();
+            int32_t* dk = dch + ctab;
+            RBF_CUDA(ctx, cudaMemcpyAsync(dk, kb.data(), sizeof(int32_t) * nk, cudaMemcpyHostToDevice, st));
+            RBF_CUDA(ctx, cudaMemcpyAsync(dk + nk, ke.data(), sizeof(int32_t) * nk, cudaMemcpyHostToDevice, st));
+            RBF_CUDA(ctx, cudaMemcpyAsync(dk + 2 * nk, kp.data(), sizeof(int32_t) * nk, cudaMemcpyHostToDevice, st));
+            RBF_CUDA(ctx, cudaMemcpyAsync(dk + 3 * nk, kptr.data(), sizeof(int32_t) * (nprob + 1),
+                                          cudaMemcpyHostToDevice, st));
+            B.C = Chunks{dk, dk + nk, dk + 2 * nk, dk + 3 * nk, nk};
+            RBF_CHECK(build_active_lists(ctx, active, st));
+            batch_graph_reset(ctx);
+            compact_at = nact / 2;
+            ++compactions;
+        }
         for (int b = 0; b < nprob; ++b) left[b] = std::max(0, max_iters - iters[b]);
         RBF_CUDA(ctx, cudaMemcpyAsync(budget, left.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         // one cycle of every active problem
         RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active,
                    budget);
         if (!mixed) {
-            RBF_LAUNCH(ctx, k_bscale<double>, bstream_blocks(n), 256, 0, st, V64, n, ctx->pid.p, gm, 0, active);
+            RBF_LAUNCH(ctx, k_bscale<double>, (unsigned)B.C.nc, 256, 0, st, V64, B.C, gm, 0, active);
             RBF_CHECK(run_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
         } else {
             RBF_LAUNCH(ctx, k_bto_f32_scaled, bstream_blocks(n), 256, 0, st, r64, n, ctx->pid.p, gm, active,
@@ -618,6 +651,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         }
     }
     ctx->batch_rounds = rounds;
+    ctx->batch_compactions = compactions;
     if (result != RBF_OK) fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve_batch: some problems missed rtol %.1e", p->rtol);
     return result;
 }

@@ -425,6 +425,11 @@ rbf_status matvec_prepare(rbf_ctx* ctx)
 
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
+    if (ctx->al.on) {   // batched solve: only the work items of active problems
+        MvParams P = mv_params(ctx);
+        P.work = ctx->al.w64.p;
+        return dispatch_f64(ctx, P, ctx->al.n64, w, y, st);
+    }
     return dispatch_f64(ctx, mv_params(ctx), ctx->n_work, w, y, st);
 }
 
@@ -473,6 +478,10 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y,
         P.stage = round_stage(G.stage_max, kMv32StageMax);
         tile = G.tile;
         nwork = G.n_work;
+    }
+    if (ctx->al.on) {   // batched solve: only the work items of active problems
+        P.work = ctx->al.w32.p;
+        nwork = ctx->al.n32;
     }
     if (nwork > 0) {
         switch (tile) {

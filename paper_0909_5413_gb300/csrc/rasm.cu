@@ -190,13 +190,14 @@ __global__ void __launch_bounds__(256)
     k_rasm_apply(const int32_t* __restrict__ ov_ptr, const int32_t* __restrict__ ov_idx,
                  const int32_t* __restrict__ core_ptr, const int32_t* __restrict__ core_idx,
                  const int64_t* __restrict__ w_off, const TW* __restrict__ W, int64_t nsub,
-                 const int32_t* __restrict__ pid_sub, const int32_t* __restrict__ active, const TV* __restrict__ r,
-                 TV* __restrict__ z)
+                 const int32_t* __restrict__ sub_list, const int32_t* __restrict__ pid_sub,
+                 const int32_t* __restrict__ active, const TV* __restrict__ r, TV* __restrict__ z)
 {
     __shared__ TV rg_all[8][kMaxSub];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t sub = (int64_t)blockIdx.x * 8 + warp;
-    if (sub >= nsub) return;
+    const int64_t idx = (int64_t)blockIdx.x * 8 + warp;
+    if (idx >= nsub) return;
+    const int64_t sub = sub_list ? (int64_t)sub_list[idx] : idx;   // sub_list: the active problems' subdomains
     if (active && !active[pid_sub[sub]]) return;   // masked problem (warp-uniform)
     TV* rg = rg_all[warp];
     const int b = ov_ptr[sub];
@@ -387,22 +388,24 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
 rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
+    const int64_t nsub = ctx->al.on ? ctx->al.nsub : ctx->nsub;
+    const int32_t* sub_list = ctx->al.on ? ctx->al.sub.p : nullptr;
     // Eq. asm: the GEMV writes every overlap row to the scratch list, then a gather
     const bool add = ctx->rasm_additive;
     const int32_t* rows_ptr = add ? ctx->ov_ptr.p : ctx->core_ptr.p;
     const int32_t* rows_idx = add ? ctx->asm_iota.p : ctx->core_idx.p;
     if (ctx->rasm_precision == RBF_FP64) {
         double* out = add ? ctx->asm_u64.p : z;
-        RBF_LAUNCH(ctx, (k_rasm_apply<double, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W64.p, ctx->nsub, ctx->pid_sub.p,
+        RBF_LAUNCH(ctx, (k_rasm_apply<double, double>), blocks_for(nsub, 8), 256, 0, st, ctx->ov_ptr.p,
+                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W64.p, nsub, sub_list, ctx->pid_sub.p,
                    ctx->active_mask, r, out);
         if (add)
             RBF_LAUNCH(ctx, k_asm_gather<double>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p,
                        ctx->asm_tidx.p, (const double*)out, ctx->n, ctx->pid.p, ctx->active_mask, z);
     } else {
         double* out = add ? ctx->asm_u64.p : z;
-        RBF_LAUNCH(ctx, (k_rasm_apply<float, double>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W32.p, ctx->nsub, ctx->pid_sub.p,
+        RBF_LAUNCH(ctx, (k_rasm_apply<float, double>), blocks_for(nsub, 8), 256, 0, st, ctx->ov_ptr.p,
+                   ctx->ov_idx.p, rows_ptr, rows_idx, ctx->w_off.p, ctx->W32.p, nsub, sub_list, ctx->pid_sub.p,
                    ctx->active_mask, r, out);
         if (add)
             RBF_LAUNCH(ctx, k_asm_gather<double>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p,
@@ -414,17 +417,19 @@ rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStrea
 rbf_status rasm_apply_sorted_f32(rbf_ctx* ctx, const float* r, float* z, cudaStream_t st)
 {
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_APPLY, st));
+    const int64_t nsub = ctx->al.on ? ctx->al.nsub : ctx->nsub;
+    const int32_t* sub_list = ctx->al.on ? ctx->al.sub.p : nullptr;
     if (ctx->inner_on) {   // vectors in the inner grid's order: the lists re-indexed into it
-        RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p,
-                   ctx->in.ov_idx.p, ctx->core_ptr.p, ctx->in.core_idx.p, ctx->w_off.p, ctx->W32.p, ctx->nsub,
+        RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(nsub, 8), 256, 0, st, ctx->ov_ptr.p,
+                   ctx->in.ov_idx.p, ctx->core_ptr.p, ctx->in.core_idx.p, ctx->w_off.p, ctx->W32.p, nsub, sub_list,
                    ctx->pid_sub.p, ctx->active_mask, r, z);
         return prof_end(ctx, RBF_PROF_RASM_APPLY, st);
     }
     const bool add = ctx->rasm_additive;
     float* out = add ? ctx->asm_u32.p : z;
-    RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(ctx->nsub, 8), 256, 0, st, ctx->ov_ptr.p, ctx->ov_idx.p,
+    RBF_LAUNCH(ctx, (k_rasm_apply<float, float>), blocks_for(nsub, 8), 256, 0, st, ctx->ov_ptr.p, ctx->ov_idx.p,
                add ? ctx->ov_ptr.p : ctx->core_ptr.p, add ? ctx->asm_iota.p : ctx->core_idx.p, ctx->w_off.p,
-               ctx->W32.p, ctx->nsub, ctx->pid_sub.p, ctx->active_mask, r, out);
+               ctx->W32.p, nsub, sub_list, ctx->pid_sub.p, ctx->active_mask, r, out);
     if (add)
         RBF_LAUNCH(ctx, k_asm_gather<float>, blocks_for(ctx->n, 256), 256, 0, st, ctx->asm_tptr.p, ctx->asm_tidx.p,
                    (const float*)out, ctx->n, ctx->pid.p, ctx->active_mask, z);
