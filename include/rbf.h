@@ -338,6 +338,9 @@ enum {
 /* enable != 0: record a CUDA event pair on the launching stream around every
  * launch of the classes above (a fixed cost of two event records each). */
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable);
+/* Classes recorded while profiling is enabled: bit k selects class k
+ * (default: all). A class left out costs no event records. */
+rbf_status rbf_profile_classes(rbf_ctx* ctx, unsigned mask);
 /* Synchronises the recorded events and returns, for kernel class `kernel`,
  * the number of recorded launches and their summed device time; clears that
  * class's record. */

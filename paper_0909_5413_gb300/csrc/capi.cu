@@ -78,7 +78,7 @@ constexpr int64_t kMaxProfPairs = 1 << 16;
 
 rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st)
 {
-    if (!ctx->prof) return RBF_OK;
+    if (!ctx->prof || !((ctx->prof_mask >> id) & 1u)) return RBF_OK;
     rbf_prof_slot& s = ctx->prof_slots[id];
     if (s.used >= kMaxProfPairs) return RBF_OK;
     while ((int64_t)s.ev.size() < 2 * (s.used + 1)) {
@@ -92,7 +92,7 @@ rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st)
 
 rbf_status prof_end(rbf_ctx* ctx, int id, cudaStream_t st)
 {
-    if (!ctx->prof) return RBF_OK;
+    if (!ctx->prof || !((ctx->prof_mask >> id) & 1u)) return RBF_OK;
     rbf_prof_slot& s = ctx->prof_slots[id];
     if (s.used >= kMaxProfPairs) return RBF_OK;
     RBF_CUDA(ctx, cudaEventRecord(s.ev[2 * s.used + 1], st));
@@ -649,6 +649,13 @@ rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;
     ctx->prof = enable != 0;
+    return RBF_OK;
+}
+
+rbf_status rbf_profile_classes(rbf_ctx* ctx, unsigned mask)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    ctx->prof_mask = mask;
     return RBF_OK;
 }
 

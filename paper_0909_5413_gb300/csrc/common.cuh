@@ -105,6 +105,7 @@ struct rbf_prof_slot {
 struct rbf_ctx {
     int device = 0;
     bool prof = false;
+    unsigned prof_mask = ~0u;     // classes recorded while prof is on (bit k: class k)
     rbf_prof_slot prof_slots[RBF_PROF_COUNT];
     rbf::ExpConsts expc;
     std::string err;

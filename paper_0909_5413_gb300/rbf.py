@@ -29,7 +29,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
-            "rbf_count_candidates"]
+            "rbf_count_candidates", "rbf_profile_classes"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -117,6 +117,7 @@ def load(path: str | None = None):
     L.rbf_get_subdomains.argtypes = [P, P, P, P, P, P]
     L.rbf_count_neighbors.argtypes = [P, I64, P]
     L.rbf_count_candidates.argtypes = [P, C.c_int, I64, P]
+    L.rbf_profile_classes.argtypes = [P, C.c_uint]
     L.rbf_get_neighbors.argtypes = [P, P, P, C.c_int64, P]
     L.rbf_status_string.argtypes = [C.c_int]
     L.rbf_status_string.restype = C.c_char_p
@@ -320,6 +321,11 @@ def rbf_device_bytes(ctx) -> int:
 
 def rbf_profile_enable(ctx, enable: bool = True) -> None:
     _check(ctx, load().rbf_profile_enable(ctx, int(enable)))
+
+
+def rbf_profile_classes(ctx, mask: int) -> None:
+    """Kernel classes recorded while profiling is on (bit k = class k)."""
+    _check(ctx, load().rbf_profile_classes(ctx, int(mask) & 0xFFFFFFFF))
 
 
 def rbf_profile_read(ctx, kernel: int) -> tuple[int, float]:
