@@ -140,6 +140,17 @@ def dist_init(args):
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of the ranks' values (the slowest replica sets the time);
+    the value itself when there is one rank (dist is None)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(name: str, p, mode: str) -> dict:
     return {"workload": name, "description": WORKLOADS[name][1], "n_points": p.n,
             "h_over_sigma": round(p.h / p.sigma, 6), "cutoff_sigmas": 8.6,
@@ -344,11 +355,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     prof_all = {k: rbf.rbf_profile_read(h, k) for k in range(6)}
     rbf.rbf_profile_enable(h, False)
-    ms = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times), dist, "cuda")
     info = infos[-1]
     ok = all(s == 0 for s in stats) and info["relres"] <= 1e-13
 
@@ -610,11 +617,7 @@ def run_batch(args, ws, rank, local):
     times, (st, infos) = timed(lambda: step(mode), args.steps)
     clk = clocks.stop()
     launches = ctx.launches - launches0
-    ms = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(times), dist, "cuda")
     summ = batch_summary(probs, infos)
     w_host = w.cpu().numpy()
     iters = [i.iters for i in infos]
