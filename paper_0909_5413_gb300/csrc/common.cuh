@@ -14,7 +14,7 @@
 
 namespace rbf {
 
-constexpr int kMaxRestart = 32;   // GMRES(m): m <= 32 (the CGS2 kernels keep V_k[i] in registers)
+constexpr int kMaxRestart = 32;   // GMRES(m): m <= 32 (coefficients and partial sums use 32-wide slots)
 constexpr int kMaxSub = 192;      // overlap list cap (subdomain matrix dimension)
 constexpr int kNumSMs = 152;      // GB300
 

@@ -36,7 +36,7 @@ constexpr int kDotBlocksMax = 8 * kNumSMs;
 constexpr int kChunkPerThread = kOrthoPer;
 constexpr int kChunk = kOrthoChunk;
 
-// The three vector passes of one CGS2 step (kernels over chunks; the
+// The vector passes of one Gram-Schmidt step (kernels over chunks; the
 // per-chunk code is shared with the batched solver). Block partial sums go
 // to partial[chunk * 32 + k] and are reduced over chunks in a fixed order.
 

@@ -51,7 +51,7 @@ struct Chunks {
     int64_t nc;
 };
 
-// The CGS2 vector passes over one chunk (the single solver's per-chunk code;
+// The Gram-Schmidt vector passes over one chunk (the single solver's per-chunk code;
 // a chunk never spans two problems). Chunks of masked problems write zeros.
 // MODE 0: partial_k = V_k . x, one block per (chunk, k), k fastest.
 template <class T>

@@ -1,5 +1,5 @@
-// ortho.cuh -- per-chunk device code of the classical Gram-Schmidt passes with
-// reorthogonalisation (CGS2) used by the Arnoldi process of GMRES (Sec. 2.2),
+// ortho.cuh -- per-chunk device code of the classical Gram-Schmidt passes (with
+// one reorthogonalisation for FP64 bases) used by the Arnoldi process of GMRES (Sec. 2.2),
 // shared by the single-problem and the batched solvers so that both sum in
 // the same order.
 //
