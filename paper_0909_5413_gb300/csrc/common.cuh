@@ -146,6 +146,7 @@ struct rbf_ctx {
     InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
     bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
     rbf::DevArray<unsigned long long> count_u64;   // one 64-bit counter (rbf_count_candidates)
+    rbf::DevArray<int> flag_dev;                   // one flag (zero initial guess test of the solvers)
     double exp2048_c[3] = {0, 0, 0};
 
     // ---- subdomains (rbf_rasm_setup)

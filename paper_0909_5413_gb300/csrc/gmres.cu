@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kDotThreads)
     for (int u = 0; u < kChunkPerThread; ++u) {
         const int64_t i = base + (int64_t)u * kDotThreads;
         if (i < n) {
-            const double v = f[i] - t[i];
+            const double v = t ? f[i] - t[i] : f[i];   // t null: A w with w = 0
             r[i] = v;
             a = fma(v, v, a);
         }
@@ -390,13 +390,15 @@ rbf_status gmres_cycle(rbf_ctx* ctx, T* V, int64_t ldv, int m, int max_steps, T*
 }
 
 // True FP64 residual r = f - A w into r64, |r|^2 into g->beta2; returns |r| / |f|.
-rbf_status true_residual(rbf_ctx* ctx, const double* f, const double* w, double* t, double* r64, cudaStream_t st,
+rbf_status true_residual(rbf_ctx* ctx, const double* f, const double* w, bool w_zero, double* t, double* r64,
+                         cudaStream_t st,
                          double fnorm, double* relres)
 {
     GmresDev* g = ctx->gm.p;
-    RBF_CHECK(matvec_sorted_f64(ctx, w, t, st));
+    if (!w_zero) RBF_CHECK(matvec_sorted_f64(ctx, w, t, st));   // w = 0: r = f exactly, no product
     const int64_t nc = num_chunks(ctx->n);
-    RBF_LAUNCH(ctx, k_residual, (unsigned)nc, kDotThreads, 0, st, f, t, r64, ctx->n, ctx->partial.p);
+    RBF_LAUNCH(ctx, k_residual, (unsigned)nc, kDotThreads, 0, st, f, w_zero ? nullptr : t, r64, ctx->n,
+               ctx->partial.p);
     RBF_LAUNCH(ctx, k_reduce, 1, 32, 0, st, ctx->partial.p, (int)nc, 1, &g->beta2);
     RBF_CUDA(ctx, cudaMemcpyAsync(&ctx->gm_host->beta2, &g->beta2, sizeof(double), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
@@ -423,10 +425,16 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
     std::memset(ctx->gm_host, 0, sizeof(GmresDev));
     ctx->gm_host->rtol = mixed ? (p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5) : p->rtol;
     RBF_CUDA(ctx, cudaMemcpyAsync(g, ctx->gm_host, sizeof(GmresDev), cudaMemcpyHostToDevice, st));
-    // |f|^2
+    // |f|^2, and whether the initial guess is zero (then r0 = f without a product)
     RBF_CHECK((launch_mdot<0, double>(ctx, f, 0, 1, const_cast<double*>(f), n, nullptr, &g->fnorm2, st)));
+    RBF_CHECK(ensure(ctx, ctx->flag_dev, 1));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->flag_dev.p, 0, sizeof(int), st));
+    RBF_LAUNCH(ctx, k_any_nonzero, stream_blocks(n), 256, 0, st, w, n, ctx->flag_dev.p);
+    int w_nonzero = 1;
     RBF_CUDA(ctx, cudaMemcpyAsync(&ctx->gm_host->fnorm2, &g->fnorm2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&w_nonzero, ctx->flag_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    bool w_zero = w_nonzero == 0;
     const double fnorm = std::sqrt(ctx->gm_host->fnorm2);
     if (!std::isfinite(fnorm)) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_solve: f is not finite");
     if (fnorm == 0.0) {
@@ -445,8 +453,9 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
         RBF_CHECK(ensure(ctx, ctx->V, (size_t)(m + 1) * n));
         double* V = ctx->V.p;
         for (;;) {
-            RBF_CHECK(true_residual(ctx, f, w, ctx->vec_a.p, V, st, fnorm, &relres));
-            ++matvecs;
+            RBF_CHECK(true_residual(ctx, f, w, w_zero, ctx->vec_a.p, V, st, fnorm, &relres));
+            if (!w_zero) ++matvecs;
+            w_zero = false;
             if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
             if (relres <= p->rtol) { result = RBF_OK; break; }
             if (it >= max_iters) break;
@@ -496,8 +505,9 @@ rbf_status gmres_solve(rbf_ctx* ctx, const double* f, double* w, const rbf_solve
         // therefore starts from the FP64 residual, which is the refinement step.
         constexpr int kMaxInnerCycles = 1;
         for (;;) {
-            RBF_CHECK(true_residual(ctx, f, w, ctx->vec_a.p, r64, st, fnorm, &relres));
-            ++matvecs;
+            RBF_CHECK(true_residual(ctx, f, w, w_zero, ctx->vec_a.p, r64, st, fnorm, &relres));
+            if (!w_zero) ++matvecs;
+            w_zero = false;
             if (!std::isfinite(relres)) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve: residual is not finite");
             if (relres <= p->rtol) { result = RBF_OK; break; }
             if (it >= max_iters || refine >= max_refine) break;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kDotThreads)
     for (int u = 0; u < kBPer; ++u) {
         int64_t i = b + threadIdx.x + (int64_t)u * kDotThreads;
         if (i < e) {
-            double v = f[i] - t[i];
+            double v = t ? f[i] - t[i] : f[i];   // t null: A w with w = 0
             r[i] = v;
             a = fma(v, v, a);
         }
@@ -555,17 +555,25 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     int compact_at = nprob / 2, compactions = 0;
     ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
     batch_graph_reset(ctx);      // buffers may have moved since the last solve
+    // a zero initial guess (every problem) gives r0 = f without a product
+    RBF_CHECK(ensure(ctx, ctx->flag_dev, 1));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->flag_dev.p, 0, sizeof(int), st));
+    RBF_LAUNCH(ctx, k_any_nonzero, bstream_blocks(n), 256, 0, st, w, n, ctx->flag_dev.p);
+    int w_nonzero = 1;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&w_nonzero, ctx->flag_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    bool w_zero = w_nonzero == 0;
     for (;;) {
         // true FP64 residual of the active problems
-        RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
-        RBF_LAUNCH(ctx, k_bresidual, (unsigned)B.C.nc, kDotThreads, 0, st, f, ctx->vec_a.p, r64, B.C, active,
-                   B.partial);
+        if (!w_zero) RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
+        RBF_LAUNCH(ctx, k_bresidual, (unsigned)B.C.nc, kDotThreads, 0, st, f, w_zero ? nullptr : ctx->vec_a.p, r64,
+                   B.C, active, B.partial);
         RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, B.partial, B.C, nprob, 1, gm, F_BETA2, active);
         RBF_CHECK(read_stat());
         int nact = 0;
         for (int b = 0; b < nprob; ++b) {
             if (!act[b]) continue;
-            ++fmv[b];
+            if (!w_zero) ++fmv[b];
             relres[b] = std::sqrt(stat[4 * b + 0]) / fnorm[b];
             if (!std::isfinite(relres[b])) return fail(ctx, RBF_ERR_NOT_CONVERGED, "rbf_solve_batch: residual of "
                                                        "problem %d is not finite", b);
@@ -579,6 +587,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             }
         }
         RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
+        w_zero = false;
         if (nact == 0) break;
         if (nact <= compact_at) {
             // Most problems have stopped: restrict the chunk table, the matvec

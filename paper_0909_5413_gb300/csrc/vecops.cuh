@@ -19,6 +19,20 @@ inline bool stagnating(std::vector<double>& hist, double relres)
 
 constexpr int kDotThreads = 256;
 
+namespace {
+
+// flag = 1 if some x[i] is not +-0 (NaN included): the solvers' zero initial
+// guess test (r0 = f without a product when w0 = 0).
+__global__ void k_any_nonzero(const double* __restrict__ x, int64_t n, int* __restrict__ flag)
+{
+    bool nz = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        nz |= !(x[i] == 0.0);
+    if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1;
+}
+
+}  // namespace
+
 // Double-float accumulator for FP32 data (Ogita, Rump and Oishi, "Accurate sum
 // and dot product", SIAM J. Sci. Comput. 26(6), 2005: TwoProduct by FMA,
 // TwoSum, and the Dot2 recurrence): a sum of exact FP32 products carried as an

@@ -206,3 +206,18 @@ def test_batch_honours_max_iters_mid_cycle(rbf):
         c1.close()
         assert info1.iters == cap
         np.testing.assert_array_equal(host(w1), host(wb))
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_tail_after_compaction_matches_alone(rbf, mixed):
+    """Seven quick problems and one slow one: once the quick ones stop, the
+    batch restricts its work lists to the slow problem and captures its cycle
+    again; every problem still gives the same bits alone and in the batch."""
+    probs = [W.lattice_problem(8 + k, 1.0, seed=300 + k, rhs="four_gaussians") for k in range(7)]
+    probs.append(W.lattice_problem(40, 0.75, seed=310, rhs="four_gaussians"))
+    st, infos, (wb,), ptr = solve_batch(rbf, probs, mixed)
+    assert st == 0, [i.as_dict() for i in infos]
+    assert infos[-1].iters > max(i.iters for i in infos[:-1])   # the tail runs alone
+    for b in (0, 3, 7):
+        _, _, (wa,), _ = solve_batch(rbf, [probs[b]], mixed)
+        np.testing.assert_array_equal(wa, wb[ptr[b]:ptr[b + 1]])
