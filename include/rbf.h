@@ -95,7 +95,7 @@ typedef struct {
     int refinements;      /* outer FP64 refinement steps (mixed), 0 otherwise */
     double relres;        /* final true relative residual, FP64 matvec */
     double relres_est;    /* last GMRES residual estimate |g_{j+1}| / ||f|| */
-    int matvecs;          /* FP64 matvecs + FP32 matvecs */
+    int matvecs;          /* FP64 matvecs + FP32 matvecs applied (none for r0 when w0 = 0) */
     int applies;          /* preconditioner applications */
     int status;           /* rbf_status of this solve / problem */
     int stagnated;        /* 1: stopped because the true residual stopped decreasing */
@@ -134,7 +134,9 @@ rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_
 
 /* Solve A~ w = f by right-preconditioned restarted GMRES with RASM (Sec. 2.2,
  * Sec. 3.1). w_dev holds the initial guess on entry (zeros for none) and the
- * solution on return, so a later call continues from it. info (host,
+ * solution on return, so a later call continues from it. An all-zero guess
+ * is detected and its residual taken as f itself (no product; the same bits
+ * as forming A 0). info (host,
  * optional) is filled. Synchronises `stream`. Returns NOT_CONVERGED (with the
  * best w) if rtol is not met within max_iters, or as soon as the true
  * residual stagnates: less than 10 % reduction over three consecutive restart
