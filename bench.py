@@ -79,12 +79,12 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic: bool, 
 
 # The FP32 matvec (inner solves of the mixed form) evaluates every staged
 # candidate pair (no cutoff mask); on the inner grid (cells of 6.1 sigma,
-# 64-target tiles) ncu measured 7.0 issued lane-instructions per candidate
+# 64-target tiles) ncu measured 6.44 issued lane-instructions per candidate
 # (profiles/mixed_kernels_lattice1024.md), so the same issue rate caps it at
-# 5.75 T candidates/s. Its DRAM traffic there: 17,077,248 B per launch.
-MATVEC_F32_REV = "inner-4src-v3"
-MATVEC_F32_INSTR_PER_CANDIDATE = 7.0
-MATVEC_F32_TRAFFIC = 17_077_248
+# 6.26 T candidates/s. Its DRAM traffic there: 17,079,040 B per launch.
+MATVEC_F32_REV = "inner-4src-v4"
+MATVEC_F32_INSTR_PER_CANDIDATE = 6.44
+MATVEC_F32_TRAFFIC = 17_079_040
 
 
 def candidate_pairs(rbf, h, inner: bool) -> int:

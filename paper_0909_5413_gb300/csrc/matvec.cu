@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __r
         }
         __syncthreads();
         const int ns4 = (ns + 3) >> 2;
-#pragma unroll 2
+#pragma unroll 8
         for (int s = 0; s < ns4; ++s) {
             const float4 sx = reinterpret_cast<const float4*>(SXs)[s];
             const float4 sy = reinterpret_cast<const float4*>(SYs)[s];
