@@ -44,3 +44,25 @@ def test_roofline_constants_are_per_revision():
 def test_every_workload_has_a_description():
     for name, (_, desc) in bench.WORKLOADS.items():
         assert isinstance(desc, str) and len(desc) > 10, name
+
+
+@pytest.mark.timeout(600)
+def test_reference_arm_json_line_on_the_small_lattice():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one JSON
+    line with the contract's keys; it needs no GPU."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "lattice64", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["higher_is_better"] is False
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "lattice64"
