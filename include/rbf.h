@@ -167,18 +167,20 @@ rbf_status rbf_eval(rbf_ctx* ctx, const double* xe_dev, int64_t m, const double*
 
 /* y = A~ w in FP64, like rbf_matvec(..., RBF_FP64, ...), without allocating.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot let a library allocate device memory -- code running while a CUDA
- * graph is captured, real-time loops that must avoid the allocator's implicit
- * synchronisation, or applications whose device memory belongs to another
- * framework's pool. Its two cell-order work vectors live in one file-scope
- * __device__ array sized for n <= 1,048,576 points (16 MiB, held by every GPU
- * that loads the library until the process exits); it calls no cudaMalloc,
- * cudaFree or other allocating routine and records no profiler events.
- * Errors: INVALID_ARG if the binned point count exceeds 1,048,576, STATE
- * without rbf_bin. The first call on a device looks up the array's device
- * address with that device current: make it before any stream capture. All
- * calls on a device share the array, so calls that overlap on the GPU race;
- * the array keeps the last call's contents (nothing relies on it being zero). */
+ * cannot let a library allocate device memory -- real-time loops that must
+ * avoid the allocator's implicit synchronisation, or applications whose device
+ * memory belongs to another framework's pool with a fixed budget. Its two
+ * cell-order work vectors live in one file-scope __device__ array sized for
+ * n <= 1,048,576 points (16 MiB, held by every GPU that loads the library
+ * until the process exits); it calls no cudaMalloc, cudaFree or other
+ * allocating routine and records no profiler events. Errors: INVALID_ARG if
+ * the binned point count exceeds 1,048,576, STATE without rbf_bin or while a
+ * batched solve runs on the context. The first call in each CUDA context (the
+ * runtime's primary context of the device, for ordinary callers) looks up the
+ * array's device address with that context current: make it before any stream
+ * capture. All calls in one context share the array, so calls that overlap on
+ * the GPU (different streams) race; the array keeps the last call's contents
+ * (nothing relies on it being zero). */
 rbf_status rbf_matvec_noalloc(rbf_ctx* ctx, const double* w_dev, double* y_dev, rbf_stream stream);
 
 /* ---- batches of independent problems in one context ----
@@ -319,6 +321,12 @@ rbf_status rbf_count_neighbors(rbf_ctx* ctx, int64_t* total, rbf_stream stream);
  * inner_cutoff > 0 and until the next binning or subdomain setup
  * (RBF_ERR_STATE otherwise). Synchronises `stream`. */
 rbf_status rbf_count_candidates(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream);
+/* Pairs (i, j), i = j included, within a grid's cutoff by the FP64 pair test
+ * of Sec. 2.3, host output: grid 0 counts r2 <= r_c^2 (the truncated matrix's
+ * nonzeros, as rbf_count_neighbors); grid 1 counts r2 <= (inner_cutoff
+ * sigma)^2, the entries the mixed form's FP32 inner operator keeps (STATE
+ * without an inner grid, as rbf_count_candidates). Synchronises `stream`. */
+rbf_status rbf_count_pairs(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream);
 /* Neighbour lists, CSR over targets in user order (ptr: n + 1 int64; idx:
  * `capacity` int32), each row the user indices j with r2_ij <= r_c^2,
  * ascending. INVALID_ARG if capacity is below the total. */
@@ -368,6 +376,13 @@ const char* rbf_last_error(rbf_ctx* ctx);
 uint64_t rbf_launch_count(rbf_ctx* ctx);
 /* Device bytes the context currently holds. */
 int64_t rbf_device_bytes(rbf_ctx* ctx);
+/* Cap on the device bytes the context may hold (0 = no cap, the default): an
+ * allocation that would take rbf_device_bytes() above it fails with
+ * RBF_ERR_OOM before cudaMalloc is called, as a real shortage would. For a
+ * host that shares the GPU under a fixed budget, and for tests that drive
+ * the library into its out-of-memory paths without exhausting the device.
+ * INVALID_ARG for a negative value. */
+rbf_status rbf_set_memory_limit(rbf_ctx* ctx, int64_t bytes);
 
 #ifdef __cplusplus
 }

@@ -257,6 +257,32 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
+// Pairs (i, j), i = j included, of a cell grid with r2_ij <= R^2 by the FP64
+// pair test (R = r_c on the main grid, the cell side on the inner grid, whose
+// cells are as wide as its cutoff), summed as 64-bit (one atomic per warp).
+__global__ void k_pair_count(const double* __restrict__ xy_s, const int32_t* __restrict__ cell_s,
+                             const int32_t* __restrict__ cell_start, int64_t n, const Prob* __restrict__ prob,
+                             const int32_t* __restrict__ pid, int inner, unsigned long long* __restrict__ total)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (p < n) {
+        const Prob& P = prob[pid[p]];
+        const double R2 = inner ? P.c * P.c : P.rc2;
+        const int64_t lc = cell_s[p] - P.cellbase, cx = lc % P.ncx, cy = lc / P.ncx;
+        const int64_t x0 = max(cx - P.k, (int64_t)0), x1 = min(cx + P.k, P.ncx - 1);
+        const int64_t y0 = max(cy - P.k, (int64_t)0), y1 = min(cy + P.k, P.ncy - 1);
+        const double xi = xy_s[2 * p], yi = xy_s[2 * p + 1];
+        for (int64_t yy = y0; yy <= y1; ++yy) {
+            const int32_t b = cell_start[P.cellbase + yy * P.ncx + x0], e = cell_start[P.cellbase + yy * P.ncx + x1 + 1];
+            for (int32_t q = b; q < e; ++q)
+                v += pair_r2(xi, yi, xy_s[2 * (int64_t)q], xy_s[2 * (int64_t)q + 1]) <= R2 ? 1u : 0u;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
 // Order-preserving selection of matvec work items (cell, first target) and
 // subdomains whose problem is active: flags, an exclusive scan, a scatter.
 __global__ void k_flag_work(const int32_t* __restrict__ work, int64_t nwork, const int32_t* __restrict__ pid_cell,
@@ -715,6 +741,22 @@ rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->count_u64.p, 0, sizeof(unsigned long long), st));
     if (ncell > 0)
         RBF_LAUNCH(ctx, k_candidate_count, blocks_for(ncell, 256), 256, 0, st, cs, pr, pc, ncell, ctx->count_u64.p);
+    unsigned long long h = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&h, ctx->count_u64.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *total = (int64_t)h;
+    return RBF_OK;
+}
+
+rbf_status count_pairs(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st)
+{
+    const bool inner = grid == 1;
+    const InnerGrid& G = ctx->in;
+    RBF_CHECK(ensure(ctx, ctx->count_u64, 1));
+    RBF_CUDA(ctx, cudaMemsetAsync(ctx->count_u64.p, 0, sizeof(unsigned long long), st));
+    RBF_LAUNCH(ctx, k_pair_count, blocks_for(ctx->n, 128), 128, 0, st, inner ? G.xy_s.p : ctx->xy_s.p,
+               inner ? G.cell_s.p : ctx->cell_s.p, inner ? G.cell_start.p : ctx->cell_start.p, ctx->n,
+               inner ? G.prob.p : ctx->prob.p, ctx->pid.p, inner ? 1 : 0, ctx->count_u64.p);
     unsigned long long h = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&h, ctx->count_u64.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));

@@ -54,6 +54,9 @@ rbf_status ensure(rbf_ctx* ctx, DevArray<T>& a, size_t count)
     a.count = 0;
     void* p = nullptr;
     size_t bytes = count * sizeof(T);
+    if (ctx->mem_limit > 0 && ctx->dev_bytes + (int64_t)bytes > ctx->mem_limit)
+        return fail(ctx, RBF_ERR_OOM, "allocation of %zu bytes exceeds the context's memory limit (%lld of %lld held)",
+                    bytes, (long long)ctx->dev_bytes, (long long)ctx->mem_limit);
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -238,6 +241,14 @@ const char* rbf_last_error(rbf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null
 uint64_t rbf_launch_count(rbf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int64_t rbf_device_bytes(rbf_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+rbf_status rbf_set_memory_limit(rbf_ctx* ctx, int64_t bytes)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (bytes < 0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_memory_limit: negative limit");
+    ctx->mem_limit = bytes;
+    return RBF_OK;
+}
 
 rbf_status rbf_create(rbf_ctx** out, int device)
 {
@@ -643,6 +654,16 @@ rbf_status rbf_count_candidates(rbf_ctx* ctx, int grid, int64_t* total, rbf_stre
         return fail(ctx, RBF_ERR_STATE, "rbf_count_candidates: no inner grid (run a mixed solve with inner_cutoff > 0)");
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     return count_candidates(ctx, grid, total, S(stream));
+}
+
+rbf_status rbf_count_pairs(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream)
+{
+    if (!ctx || !total || (grid != 0 && grid != 1)) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_count_pairs: call rbf_bin first");
+    if (grid == 1 && !ctx->in.ready)
+        return fail(ctx, RBF_ERR_STATE, "rbf_count_pairs: no inner grid (run a mixed solve with inner_cutoff > 0)");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    return count_pairs(ctx, grid, total, S(stream));
 }
 
 rbf_status rbf_profile_enable(rbf_ctx* ctx, int enable)

@@ -111,6 +111,7 @@ struct rbf_ctx {
     std::string err;
     uint64_t launches = 0;
     int64_t dev_bytes = 0;
+    int64_t mem_limit = 0;        // rbf_set_memory_limit: cap on dev_bytes (0 = none)
     std::vector<std::pair<void*, size_t>> owned;   // every live allocation
 
     // ---- problems (one for rbf_bin, several for rbf_bin_batch)
@@ -258,6 +259,8 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st);
 rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t st);
 // Sum over the cells of grid 0 (r_c cells) or 1 (inner grid) of points x stencil points.
 rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
+// Pairs within the grid's cutoff (r_c on grid 0, the inner cutoff on grid 1), FP64 pair test.
+rbf_status count_pairs(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
 // Main cell order <-> inner order for the FP32 hand-offs of the mixed form.
 rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double* scale_dev, float* out_inner,
                                cudaStream_t st);

@@ -29,7 +29,8 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_bin_batch", "rbf_rasm_setup_batch", "rbf_solve_batch", "rbf_server_create", "rbf_server_destroy",
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
-            "rbf_count_candidates", "rbf_profile_classes"]
+            "rbf_count_candidates", "rbf_profile_classes", "rbf_set_memory_limit",
+            "rbf_count_pairs"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -117,6 +118,7 @@ def load(path: str | None = None):
     L.rbf_get_subdomains.argtypes = [P, P, P, P, P, P]
     L.rbf_count_neighbors.argtypes = [P, I64, P]
     L.rbf_count_candidates.argtypes = [P, C.c_int, I64, P]
+    L.rbf_count_pairs.argtypes = [P, C.c_int, I64, P]
     L.rbf_profile_classes.argtypes = [P, C.c_uint]
     L.rbf_get_neighbors.argtypes = [P, P, P, C.c_int64, P]
     L.rbf_status_string.argtypes = [C.c_int]
@@ -127,6 +129,7 @@ def load(path: str | None = None):
     L.rbf_launch_count.restype = C.c_uint64
     L.rbf_device_bytes.argtypes = [P]
     L.rbf_device_bytes.restype = C.c_int64
+    L.rbf_set_memory_limit.argtypes = [P, C.c_int64]
     L.rbf_profile_enable.argtypes = [P, C.c_int]
     L.rbf_profile_read.argtypes = [P, C.c_int, I64, D]
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
@@ -307,6 +310,13 @@ def rbf_count_candidates(ctx, grid: int = 0, stream=None) -> int:
     return t.value
 
 
+def rbf_count_pairs(ctx, grid: int = 0, stream=None) -> int:
+    """Pairs within r_c (grid 0) or within the mixed form's inner cutoff (grid 1)."""
+    t = C.c_int64()
+    _check(ctx, load().rbf_count_pairs(ctx, int(grid), C.byref(t), _stream(stream)))
+    return t.value
+
+
 def rbf_get_neighbors(ctx, ptr_dev, idx_dev, capacity: int, stream=None) -> None:
     _check(ctx, load().rbf_get_neighbors(ctx, _ptr(ptr_dev), _ptr(idx_dev), int(capacity), _stream(stream)))
 
@@ -317,6 +327,11 @@ def rbf_launch_count(ctx) -> int:
 
 def rbf_device_bytes(ctx) -> int:
     return int(load().rbf_device_bytes(ctx))
+
+
+def rbf_set_memory_limit(ctx, nbytes: int) -> None:
+    """Cap on the device bytes the context may hold (0 = none)."""
+    _check(ctx, load().rbf_set_memory_limit(ctx, int(nbytes)))
 
 
 def rbf_profile_enable(ctx, enable: bool = True) -> None:

@@ -1,6 +1,6 @@
 """bench.py's roofline objects on CPU: the fields the JSON line must carry,
-frac = achieved / peak, and ceilings that follow from the issue rate and the
-per-revision instruction counts."""
+frac = achieved / peak, and ceilings that follow from unit counts and clocks
+alone (no per-revision instruction counts)."""
 import os
 import sys
 
@@ -12,33 +12,55 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_issue_peak_from_unit_counts():
+def test_peaks_from_unit_counts():
     assert bench.ISSUE_PEAK_LANE_INSTR == pytest.approx(152 * 4 * 32 * 2.07e9)
+    assert bench.FP64_DFMA_PEAK_PAIRS == pytest.approx(152 * 2 * 2.07e9)      # 629.3 G pairs/s
+    assert bench.MUFU_PEAK_PAIRS == pytest.approx(152 * 16 * 2.07e9)          # 5.03 T pairs/s
 
 
 def test_f64_roofline_object():
     pairs, avg_s = 375_552_506, 2.27e-3
-    r = bench.f64_matvec_roofline(pairs, avg_s, 185, traffic=True)
+    r = bench.f64_matvec_roofline(pairs, avg_s, 185, 37_978_112)
     for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert key in r
     assert r["bound"] == "alu" and r["unit"] == "Gpair/s"
     assert r["achieved"] == pytest.approx(pairs / avg_s / 1e9)
-    instr = bench.MATVEC_F64_INSTR_PER_PAIR[bench.MATVEC_F64_REV]
-    assert r["peak"] == pytest.approx(bench.ISSUE_PEAK_LANE_INSTR / instr / 1e9)
+    assert r["peak"] == pytest.approx(629.28, rel=1e-4)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.MATVEC_F64_TRAFFIC[bench.MATVEC_F64_REV]
-    assert r["kernel_rev"] == bench.MATVEC_F64_REV
-    # traffic is only claimed for the workload the counters were taken on
-    assert bench.f64_matvec_roofline(pairs, avg_s, 185, traffic=False)["traffic"] is None
+    ib = r["issue_bound"]
+    assert ib["peak"] == pytest.approx(bench.ISSUE_PEAK_LANE_INSTR / bench.F64_ISSUE_BUDGET_PER_PAIR / 1e9)
+    assert ib["frac"] == pytest.approx(r["achieved"] / ib["peak"])
+    assert r["traffic"] == 37_978_112
+    assert bench.f64_matvec_roofline(pairs, avg_s, 185, None)["traffic"] is None
 
 
-def test_roofline_constants_are_per_revision():
-    assert bench.MATVEC_F64_REV in bench.MATVEC_F64_INSTR_PER_PAIR
+def test_f32_roofline_counts_in_cutoff_pairs_not_candidates():
+    pairs, cand, avg_s = 191_000_000, 542_600_000, 127e-6
+    r = bench.f32_matvec_roofline(pairs, cand, avg_s, 180, None, "inner")
+    assert r["unit"] == "Tpair/s" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(pairs / avg_s / 1e12)
+    assert r["frac"] == pytest.approx(pairs / avg_s / bench.MUFU_PEAK_PAIRS)
+    assert r["candidates_per_pair"] == pytest.approx(cand / pairs)
+
+
+def test_roofline_constants():
     assert bench.MATVEC_F64_REV in bench.MATVEC_F64_TRAFFIC
     # algorithmic bytes of the FP64 matvec are 32 B per point; the measured traffic sits above them
     assert bench.MATVEC_F64_TRAFFIC[bench.MATVEC_F64_REV] >= 32 * 1024 * 1024
-    assert 4.0 < bench.MATVEC_F32_INSTR_PER_CANDIDATE < 10.0
-    assert bench.MATVEC_F32_TRAFFIC > 0
+    assert 60.0 < bench.F64_ISSUE_BUDGET_PER_PAIR < 160.0
+
+
+def test_lattice_window_is_a_block_of_the_lattice():
+    p = bench.W.lattice_problem(40, 0.8, seed=3)
+    xy, f, x0, y0, (i0, j0, w) = bench.lattice_window(p, 16, seed=5)
+    assert w == 16 and i0 % 4 == 0 and j0 % 4 == 0
+    full = p.xy.reshape(40, 40, 2)
+    np = bench.np
+    assert np.array_equal(xy.reshape(16, 16, 2), full[j0:j0 + 16, i0:i0 + 16])
+    assert np.array_equal(f, p.f.reshape(40, 40)[j0:j0 + 16, i0:i0 + 16].ravel())
+    # the window's box origin lies on the full lattice's box edges
+    assert x0 == pytest.approx(p.x0 + i0 * p.h) and y0 == pytest.approx(p.x0 + j0 * p.h)
+    assert bench.lattice_window(p, 100, seed=1)[4] == (0, 0, 40)
 
 
 def test_every_workload_has_a_description():
@@ -66,3 +88,5 @@ def test_reference_arm_json_line_on_the_small_lattice():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "lattice64"
+    # ms_per_step is the wall time of the step's sample, which fits in the run
+    assert 0.0 < line["ms_per_step"] < 600e3

@@ -221,3 +221,45 @@ def test_batch_tail_after_compaction_matches_alone(rbf, mixed):
     for b in (0, 3, 7):
         _, _, (wa,), _ = solve_batch(rbf, [probs[b]], mixed)
         np.testing.assert_array_equal(wa, wb[ptr[b]:ptr[b + 1]])
+
+
+def config4_slice():
+    """A seeded slice of the 4096-problem batch workload (the same (n_side, h/sigma)
+    draws and per-problem seeds as the full batch): its largest problem (128 x 128
+    = 16,384 points) and eleven others drawn at random, all at h/sigma >= 0.7."""
+    sizes = W.batch_problem_sizes(4096, 256, 16384, W.DEFAULT_SEED)
+    big = int(np.argmax([s[0] for s in sizes]))
+    rng = np.random.default_rng(77)
+    pick = [big]
+    for k in rng.permutation(len(sizes)):
+        if len(pick) == 12:
+            break
+        if int(k) != big and sizes[k][1] >= 0.7:
+            pick.append(int(k))
+    return [W.lattice_problem(sizes[k][0], sizes[k][1], seed=W.DEFAULT_SEED + 1 + k, rhs="four_gaussians")
+            for k in pick]
+
+
+def test_config4_slice_matches_oracle_per_problem(rbf):
+    """Mixed batched solve (FP32 inner on the 6.1 sigma grid, FP64 outer) of the
+    slice: every problem reaches a true relative residual <= 1e-13, recomputed
+    by the oracle's FP64 matvec, and its w agrees with the oracle's own FP64
+    solve of that problem alone to within the conditioning of the system."""
+    probs = config4_slice()
+    assert max(p.n for p in probs) == 128 * 128
+    ctx, xy, f, ptr = setup(rbf, probs, factor_precision=1)
+    sp = rbf.RbfSolveParams(1e-13, 30, 3000, 1, 3000, 1e-5, 6.1)
+    w = torch.zeros(ptr[-1], dtype=torch.float64, device="cuda")
+    st, infos = rbf.rbf_solve_batch(ctx.handle, dev(f), w, sp, len(probs), check=False)
+    w = host(w)
+    ctx.close()
+    assert st == 0, [i.as_dict() for i in infos]
+    for b, p in enumerate(probs):
+        wb = w[ptr[b]:ptr[b + 1]]
+        r = p.f - O.matvec_cutoff(p.xy, wb, p.sigma, p.cutoff)
+        assert np.linalg.norm(r) / np.linalg.norm(p.f) <= 1e-13, (b, infos[b].as_dict())
+        pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+        wo, oi = pr.solve(p.f, max_iters=3000)
+        assert oi.relres <= 1e-13
+        # two solutions of one SPD system, each to 1e-13: |dw| / |w| <= cond * 2e-13
+        assert rel(wb, wo) <= 1e-5, (b, p.n, p.h / p.sigma)

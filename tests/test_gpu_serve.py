@@ -1,9 +1,11 @@
 """Serving loop: requests of different sizes submitted together run
 concurrently on their own slots, each result is bit-identical to the same
-request solved alone, and admission respects the device-memory budget."""
+request solved alone and meets the tolerance against the CPU oracle, and
+admission respects the device-memory budget."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_0909_5413_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -25,6 +27,12 @@ def requests(rbf, sizes, seed=300):
         cfg = rbf.config_for(p, mixed=mixed, factor_precision=rbf.RBF_FP32 if mixed else rbf.RBF_FP64)
         out.append((p, cfg))
     return out
+
+
+def oracle_relres(p, w):
+    """True relative residual of w by the oracle's FP64 truncated matvec."""
+    r = p.f - O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff)
+    return float(np.linalg.norm(r) / np.linalg.norm(p.f))
 
 
 def alone(rbf, p, cfg):
@@ -54,6 +62,14 @@ def test_serve_results_identical_alone_and_in_the_mix(rbf):
         st, wa = alone(rbf, p, cfg)
         assert st == 0
         np.testing.assert_array_equal(w, wa)
+        # against the oracle: its own FP64 matvec gives the residual, and its own
+        # solve of the request agrees to within the conditioning of the system
+        assert oracle_relres(p, w) <= 1e-13
+        if p.n <= 128 * 128:
+            pr = O.Problem(p.xy, p.sigma, p.cutoff, p.x0, p.x0, p.core_size, p.overlap)
+            wo, oi = pr.solve(p.f, max_iters=3000)
+            assert oi.relres <= 1e-13
+            assert np.linalg.norm(w - wo) / np.linalg.norm(wo) <= 1e-5
         assert r.t_submit <= r.t_admit <= r.t_done
         spans.append((r.t_admit, r.t_done))
     # requests submitted together overlap on the device
@@ -86,6 +102,7 @@ def test_serve_admission_respects_memory_budget(rbf):
         assert r.status == 0
         _, wa = alone(rbf, p, cfg)
         np.testing.assert_array_equal(w, wa)
+        assert oracle_relres(p, w) <= 1e-13
 
 
 def test_serve_rejects_request_over_budget(rbf):
