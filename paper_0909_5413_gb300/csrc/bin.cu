@@ -96,6 +96,10 @@ __global__ void k_bbox(const double* __restrict__ xy, int64_t n, const int32_t* 
         }
         cur = b;
         double x = xy[2 * i], y = xy[2 * i + 1];
+        // A NaN (whose sign arithmetic may not keep) would slip through the
+        // ordered-key minima; key 0, which no finite or infinite value maps
+        // to, makes the problem's x_min NaN instead, and the host rejects it.
+        if (!(isfinite(x) && isfinite(y))) k[0] = 0ull;
         k[0] = min(k[0], okey(x));
         k[1] = min(k[1], okey(y));
         k[2] = min(k[2], okey(-x));

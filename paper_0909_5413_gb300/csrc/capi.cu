@@ -82,6 +82,18 @@ constexpr int64_t kMaxProfPairs = 1 << 16;
 rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st)
 {
     if (!ctx->prof || !((ctx->prof_mask >> id) & 1u)) return RBF_OK;
+    if (ctx->capturing) {   // an event record node of the captured cycle
+        rbf_graph_prof g{id, ctx->prof_step, nullptr, nullptr};
+        RBF_CUDA(ctx, cudaEventCreate(&g.a));
+        cudaError_t e = cudaEventCreate(&g.b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(g.a);
+            return cuda_fail(ctx, e, "cudaEventCreate");
+        }
+        ctx->bgraph_prof.push_back(g);
+        RBF_CUDA(ctx, cudaEventRecordWithFlags(g.a, st, cudaEventRecordExternal));
+        return RBF_OK;
+    }
     rbf_prof_slot& s = ctx->prof_slots[id];
     if (s.used >= kMaxProfPairs) return RBF_OK;
     while ((int64_t)s.ev.size() < 2 * (s.used + 1)) {
@@ -96,10 +108,30 @@ rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st)
 rbf_status prof_end(rbf_ctx* ctx, int id, cudaStream_t st)
 {
     if (!ctx->prof || !((ctx->prof_mask >> id) & 1u)) return RBF_OK;
+    if (ctx->capturing) {
+        for (size_t i = ctx->bgraph_prof.size(); i-- > 0;)
+            if (ctx->bgraph_prof[i].cls == id) {
+                RBF_CUDA(ctx, cudaEventRecordWithFlags(ctx->bgraph_prof[i].b, st, cudaEventRecordExternal));
+                return RBF_OK;
+            }
+        return fail(ctx, RBF_ERR_STATE, "profiler: end of a launch that was not begun");
+    }
     rbf_prof_slot& s = ctx->prof_slots[id];
     if (s.used >= kMaxProfPairs) return RBF_OK;
     RBF_CUDA(ctx, cudaEventRecord(s.ev[2 * s.used + 1], st));
     s.used++;
+    return RBF_OK;
+}
+
+rbf_status prof_harvest_graph(rbf_ctx* ctx, int steps_run)
+{
+    for (const rbf_graph_prof& g : ctx->bgraph_prof) {
+        if (g.step >= steps_run) continue;   // every problem had stopped: the launch did no work
+        float ms = 0.f;
+        RBF_CUDA(ctx, cudaEventElapsedTime(&ms, g.a, g.b));
+        ctx->prof_slots[g.cls].graph_ms += ms;
+        ctx->prof_slots[g.cls].graph_launches += 1;
+    }
     return RBF_OK;
 }
 
@@ -692,9 +724,11 @@ rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double*
         RBF_CUDA(ctx, cudaEventElapsedTime(&ms, s.ev[2 * i], s.ev[2 * i + 1]));
         tot += ms;
     }
-    if (launches) *launches = s.used;
-    if (total_ms) *total_ms = tot;
+    if (launches) *launches = s.used + s.graph_launches;
+    if (total_ms) *total_ms = tot + s.graph_ms;
     s.used = 0;
+    s.graph_ms = 0.0;
+    s.graph_launches = 0;
     return RBF_OK;
 }
 

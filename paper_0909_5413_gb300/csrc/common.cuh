@@ -100,6 +100,16 @@ struct EvalBins {
 struct rbf_prof_slot {
     std::vector<cudaEvent_t> ev;   // pairs (start, stop)
     int64_t used = 0;
+    double graph_ms = 0.0;         // launches inside replayed graphs, harvested after each replay
+    int64_t graph_launches = 0;
+};
+
+// An event pair recorded by a captured Arnoldi cycle around one launch of a
+// profiled class: `step` is the Arnoldi step of the launch (-1 after the steps).
+struct rbf_graph_prof {
+    int cls;
+    int step;
+    cudaEvent_t a, b;
 };
 
 struct rbf_ctx {
@@ -186,6 +196,10 @@ struct rbf_ctx {
     cudaEvent_t bevent = nullptr;
     cudaGraphExec_t bgraph = nullptr;       // captured Arnoldi cycle of the batched solver
     uint64_t bgraph_launches = 0;           // kernels in that graph
+    bool capturing = false;                 // launches are being captured into bgraph
+    int prof_step = -1;                     // Arnoldi step of the launches being issued (-1: none)
+    unsigned bgraph_prof_mask = 0;          // profiler classes the captured graph records
+    std::vector<rbf_graph_prof> bgraph_prof;   // its event pairs
     // Work lists of the batched solver restricted to the problems still active
     // (built when most problems have stopped; used by the matvecs and the apply
     // while `on`; cleared when the solve returns). Order-preserving subsets of
@@ -238,6 +252,10 @@ inline unsigned blocks_for(int64_t n, int threads)
 // Profiler hooks: event pair around one launch (or launch sequence) of class id.
 rbf_status prof_begin(rbf_ctx* ctx, int id, cudaStream_t st);
 rbf_status prof_end(rbf_ctx* ctx, int id, cudaStream_t st);
+// After a replay of the captured cycle has completed: add the durations of its
+// recorded launches of steps < steps_run (and of those after the steps) to the
+// profiler's totals; the launches of later steps found every problem stopped.
+rbf_status prof_harvest_graph(rbf_ctx* ctx, int steps_run);
 
 // ---- scan.cu
 // out[0] = 0, out[i+1] = in[0] + ... + in[i] for i < n (int32 or int64 in, int64 or int32 out)

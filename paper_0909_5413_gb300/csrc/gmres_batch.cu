@@ -8,9 +8,12 @@
 // boundary; block partial sums of a chunk are reduced per problem in a fixed
 // order (deterministic: a problem's result does not depend on the other
 // problems of the batch). Converged problems are masked: their kernels return
-// at once. An Arnoldi cycle runs with no host synchronisation (each problem's
-// stop flag lives on the device), so the cycle is captured once as a CUDA
-// graph and replayed; the host reads the problems' residuals once per cycle.
+// at once; within a cycle, a problem that meets its estimate (or its step
+// budget) leaves the step mask, and the rest of the cycle's steps skip it. An
+// Arnoldi cycle runs with no host synchronisation (each problem's stop flag
+// lives on the device), so the cycle is captured once as a CUDA graph and
+// replayed; the host reads the problems' residuals once per cycle. A single
+// problem (rbf_solve) is a batch of one.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -154,11 +157,17 @@ __global__ void k_breduce(const double* __restrict__ partial, Chunks C, int npro
 }
 
 // Start of a cycle of every active problem (mode 1: reference norm = |r|).
+// run[b] (the step mask of the Arnoldi kernels) starts as active and not done.
 __global__ void k_bcycle_init(GmresDev* __restrict__ gm, int nprob, int m, int mode,
-                              const int32_t* __restrict__ active, const int32_t* __restrict__ budget)
+                              const int32_t* __restrict__ active, const int32_t* __restrict__ budget,
+                              int32_t* __restrict__ run)
 {
     int pb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pb >= nprob || !active[pb]) return;
+    if (pb >= nprob) return;
+    if (!active[pb]) {
+        run[pb] = 0;
+        return;
+    }
     GmresDev& g = gm[pb];
     g.budget = budget[pb];   // steps left before max_iters (the cycle stops there, as the single solver's)
     if (mode == 1) g.fnorm2 = g.beta2;
@@ -168,25 +177,10 @@ __global__ void k_bcycle_init(GmresDev* __restrict__ gm, int nprob, int m, int m
     g.g[0] = beta;
     g.inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
     g.est = fn > 0.0 ? beta / fn : 0.0;
-    g.done = (g.est <= g.rtol) ? 1 : 0;
+    g.done = (g.est <= g.rtol || g.budget <= 0) ? 1 : 0;
     g.breakdown = 0;
     g.j = 0;       // steps taken in this cycle
-}
-
-// Arnoldi step j of every active problem that has not stopped in this cycle
-// (one warp per problem).
-__global__ void k_barnoldi(GmresDev* __restrict__ gm, int nprob, int j, const int32_t* __restrict__ active,
-                           int passes)
-{
-    const int pb = blockIdx.x;
-    if (pb >= nprob || !active[pb]) return;
-    GmresDev* g = &gm[pb];
-    if (g->done) return;
-    arnoldi_column(g, j, passes);
-    if (threadIdx.x == 0) {
-        g->done = (g->est <= g->rtol || g->breakdown || j + 1 >= g->budget) ? 1 : 0;
-        g->j = j + 1;
-    }
+    run[pb] = g.done ? 0 : 1;
 }
 
 __global__ void k_bsolve_y(GmresDev* __restrict__ gm, int nprob, const int32_t* __restrict__ active)
@@ -215,6 +209,36 @@ __global__ void k_bscale(T* __restrict__ x, Chunks C, const GmresDev* __restrict
     const GmresDev& g = gm[pb];
     if (which == 1 && g.done && g.breakdown) return;
     const double f = which == 0 ? g.inv_beta : g.inv_h;
+    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = (T)((double)x[i] * f);
+}
+
+// End of Arnoldi step j, one block per chunk: v_{j+1} /= |v_{j+1}| for the
+// problems still running (1 / |v| from the norm of the last Gram-Schmidt pass,
+// as the Arnoldi column computes it), and, in the block of each problem's
+// first chunk, the Arnoldi column itself (Hessenberg column, rotations,
+// estimate) and the stop test, which takes a stopped problem out of the step
+// mask. A block of the same problem that already sees the problem stopped
+// skips its scaling: v_{j+1} of a stopped problem is never used.
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_bscale_norm(T* __restrict__ x, Chunks C, GmresDev* __restrict__ gm, int nprob, int j, int32_t* __restrict__ run,
+                  int passes)
+{
+    const int64_t c = blockIdx.x;
+    const int pb = C.pid[c];
+    if (!run[pb]) return;
+    GmresDev* g = &gm[pb];
+    const double hn = sqrt(fmax(g->nrm2, 0.0));
+    const double f = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (c == C.cptr[pb] && threadIdx.x < 32) {
+        arnoldi_column(g, j, passes);
+        if (threadIdx.x == 0) {
+            const int done = (g->est <= g->rtol || g->breakdown || j + 1 >= g->budget) ? 1 : 0;
+            g->done = done;
+            g->j = j + 1;
+            if (done) run[pb] = 0;
+        }
+    }
     for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = (T)((double)x[i] * f);
 }
 
@@ -288,6 +312,12 @@ __global__ void k_bpack(const GmresDev* __restrict__ gm, int nprob, double* __re
     out[4 * pb + 3] = gm[pb].est;
 }
 
+__global__ void k_w64_to_w32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 __global__ void k_bzero_inactive_w(double* __restrict__ w, const int32_t* __restrict__ pid,
                                    const int32_t* __restrict__ zero, int64_t n)
 {
@@ -308,22 +338,24 @@ struct BatchWork {
     Chunks C;
     int nprob;
     GmresDev* gm;
-    const int32_t* active;
+    const int32_t* active;   // problems of this cycle
+    int32_t* run;            // problems still stepping in this cycle (the Arnoldi kernels' mask)
     double* partial;
     const int32_t* pid;
     int64_t n;
 
+    // The Gram-Schmidt passes of one step, over the problems still running.
     template <int MODE, class T>
-    rbf_status mdot(const T* V, int64_t ldv, int nv, T* x, int field_in, int field_out)
+    rbf_status mdot(const T* V, int64_t ldv, int nv, T* x, int field_in, int field_out, const int32_t* mask)
     {
         if (MODE == 0)
             RBF_LAUNCH(ctx, (k_bdots<T>), (unsigned)(C.nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, C,
-                       active, partial);
+                       mask, partial);
         else
             RBF_LAUNCH(ctx, (k_bupdate<T, MODE>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x,
-                       C, active, partial);
+                       C, mask, partial);
         const int nout = MODE == 2 ? 1 : nv;
-        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out, active);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out, mask);
         return RBF_OK;
     }
 };
@@ -367,18 +399,25 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
     for (int j = 0; j < m; ++j) {
         T* vj = V + (int64_t)j * ldv;
         T* vn = V + (int64_t)(j + 1) * ldv;
+        // the operators of the step skip the problems that have stopped in this cycle
+        ctx->prof_step = j;
+        ctx->active_mask = B.run;
         RBF_CHECK(BOps<T>::minv(ctx, vj, u, st));
         RBF_CHECK(BOps<T>::amul(ctx, u, vn, st));
-        RBF_CHECK((B.mdot<0, T>(V, ldv, j + 1, vn, -1, F_H1)));
+        ctx->active_mask = B.active;
+        RBF_CHECK(prof_begin(ctx, RBF_PROF_ORTHO, st));
+        RBF_CHECK((B.mdot<0, T>(V, ldv, j + 1, vn, -1, F_H1, B.run)));
         if (gs_passes<T>() == 2) {
-            RBF_CHECK((B.mdot<1, T>(V, ldv, j + 1, vn, F_H1, F_H2)));
-            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H2, F_NRM2)));
+            RBF_CHECK((B.mdot<1, T>(V, ldv, j + 1, vn, F_H1, F_H2, B.run)));
+            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H2, F_NRM2, B.run)));
         } else {
-            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H1, F_NRM2)));
+            RBF_CHECK((B.mdot<2, T>(V, ldv, j + 1, vn, F_H1, F_NRM2, B.run)));
         }
-        RBF_LAUNCH(ctx, k_barnoldi, (unsigned)B.nprob, 32, 0, st, B.gm, B.nprob, j, B.active, gs_passes<T>());
-        RBF_LAUNCH(ctx, (k_bscale<T>), (unsigned)B.C.nc, 256, 0, st, vn, B.C, B.gm, 1, B.active);
+        RBF_CHECK(prof_end(ctx, RBF_PROF_ORTHO, st));
+        RBF_LAUNCH(ctx, (k_bscale_norm<T>), (unsigned)B.C.nc, 256, 0, st, vn, B.C, B.gm, B.nprob, j, B.run,
+                   gs_passes<T>());
     }
+    ctx->prof_step = -1;
     RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);
     RBF_LAUNCH(ctx, (k_bcombine<T>), bstream_blocks(n), 256, 0, st, V, ldv, B.gm, B.pid, B.active, t, n);
     RBF_CHECK(BOps<T>::minv(ctx, t, u, st));
@@ -394,15 +433,20 @@ template <class T>
 rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double* w)
 {
     rbf_ctx* ctx = B.ctx;
+    // profiled classes are recorded by event nodes inside the graph: a change of
+    // the profiler's state takes a new capture
+    const unsigned pmask = ctx->prof ? ctx->prof_mask : 0u;
+    if (ctx->bgraph && pmask != ctx->bgraph_prof_mask) batch_graph_reset(ctx);
     if (!ctx->bgraph) {
-        const bool prof = ctx->prof;
         const uint64_t l0 = ctx->launches;
-        ctx->prof = false;   // no event records inside the graph
+        ctx->capturing = true;
+        ctx->bgraph_prof_mask = pmask;
         RBF_CUDA(ctx, cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
         rbf_status s = batch_cycle<T>(B, V, ldv, m, u, t, w);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(B.st, &g);
-        ctx->prof = prof;
+        ctx->capturing = false;
+        ctx->prof_step = -1;
         if (s != RBF_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             if (s != RBF_OK) return s;
@@ -440,6 +484,12 @@ void batch_graph_reset(rbf_ctx* ctx)
     if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
     ctx->bgraph = nullptr;
     ctx->bgraph_launches = 0;
+    for (const rbf_graph_prof& g : ctx->bgraph_prof) {
+        cudaEventDestroy(g.a);
+        cudaEventDestroy(g.b);
+    }
+    ctx->bgraph_prof.clear();
+    ctx->bgraph_prof_mask = 0;
 }
 
 rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf_solve_params* p,
@@ -485,7 +535,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     Chunks C{dch, dch + nc, dch + 2 * nc, dch + 3 * nc, nc};
 
     RBF_CHECK(ensure(ctx, ctx->gmb, nprob));
-    RBF_CHECK(ensure(ctx, ctx->bactive, 3 * (size_t)nprob));
+    RBF_CHECK(ensure(ctx, ctx->bactive, 4 * (size_t)nprob));
     RBF_CHECK(ensure(ctx, ctx->bstat, 4 * (size_t)nprob));
     RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(nc, 1) * 32));
     RBF_CHECK(ensure(ctx, ctx->vec_a, n));
@@ -494,15 +544,16 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     int32_t* active = ctx->bactive.p;
     int32_t* zero_mask = ctx->bactive.p + nprob;
     int32_t* budget = ctx->bactive.p + 2 * nprob;   // steps left per problem
+    int32_t* run = ctx->bactive.p + 3 * nprob;      // problems still stepping in the current cycle
     RBF_CUDA(ctx, cudaMemsetAsync(gm, 0, sizeof(GmresDev) * nprob, st));
     const double rt = mixed ? (p->inner_rtol > 0.0 ? p->inner_rtol : 1e-5) : p->rtol;
     RBF_LAUNCH(ctx, k_binit, blocks_for(nprob, 128), 128, 0, st, gm, nprob, rt);
     std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
     RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
 
-    BatchWork B{ctx, st, C, nprob, gm, active, ctx->partial.p, ctx->pid.p, n};
+    BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, ctx->pid.p, n};
     // |f_b|^2
-    RBF_CHECK((B.mdot<0, double>(f, 0, 1, const_cast<double*>(f), -1, F_FNORM2)));
+    RBF_CHECK((B.mdot<0, double>(f, 0, 1, const_cast<double*>(f), -1, F_FNORM2, active)));
     std::vector<double> stat(4 * (size_t)nprob);
     auto read_stat = [&]() -> rbf_status {
         RBF_LAUNCH(ctx, k_bpack, blocks_for(nprob, 128), 128, 0, st, gm, nprob, ctx->bstat.p);
@@ -534,8 +585,13 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         RBF_CHECK(ensure(ctx, ctx->V, (size_t)(m + 1) * ldv));
         V64 = ctx->V.p;
     } else {
-        if (ctx->rasm_precision == RBF_FP64 || !ctx->W32.p) return fail(ctx, RBF_ERR_STATE,
-            "rbf_solve_batch: the mixed form needs rbf_rasm_setup_batch with precision RBF_FP32");
+        if (ctx->rasm_precision == RBF_FP64) {
+            // FP64 subdomain inverses: the inner solves use an FP32 copy of them
+            RBF_CHECK(ensure(ctx, ctx->W32, ctx->W64.count));
+            RBF_LAUNCH(ctx, k_w64_to_w32, bstream_blocks((int64_t)ctx->W64.count), 256, 0, st, ctx->W64.p,
+                       (int64_t)ctx->W64.count, ctx->W32.p);
+            if (ctx->rasm_additive) RBF_CHECK(ensure(ctx, ctx->asm_u32, ctx->asm_u64.count));
+        }
         RBF_CHECK(ensure(ctx, ctx->V, (size_t)((m + 3) * ldv + 1) / 2 + 1));
         Vf = (float*)ctx->V.p;
         // the inner grid (shorter cutoff, own order) for the FP32 inner solves
@@ -621,7 +677,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         RBF_CUDA(ctx, cudaMemcpyAsync(budget, left.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
         // one cycle of every active problem
         RBF_LAUNCH(ctx, k_bcycle_init, blocks_for(nprob, 128), 128, 0, st, gm, nprob, m, mixed ? 1 : 0, active,
-                   budget);
+                   budget, run);
         if (!mixed) {
             RBF_LAUNCH(ctx, k_bscale<double>, (unsigned)B.C.nc, 256, 0, st, V64, B.C, gm, 0, active);
             RBF_CHECK(run_cycle<double>(B, V64, ldv, m, ctx->vec_b.p, ctx->vec_a.p, w));
@@ -631,6 +687,12 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             RBF_CHECK(run_cycle<float>(B, Vf, ldv, m, uf, tf, w));
         }
         RBF_CHECK(read_stat());
+        if (!ctx->bgraph_prof.empty()) {
+            int steps_run = 0;
+            for (int b = 0; b < nprob; ++b)
+                if (act[b]) steps_run = std::max(steps_run, (int)stat[4 * b + 2]);
+            RBF_CHECK(prof_harvest_graph(ctx, steps_run));
+        }
         for (int b = 0; b < nprob; ++b) {
             if (!act[b]) continue;
             iters[b] += (int)stat[4 * b + 2];
