@@ -487,6 +487,21 @@ def run_ours(args, ws, rank, local):
     breakdown = {nm: {"launches": prof_all[k][0], "ms": round(prof_all[k][1], 3)} for nm, k in
                  (("matvec_f64", 0), ("matvec_f32", 1), ("rasm_apply", 2), ("orthogonalisation", 3),
                   ("rasm_setup", 4), ("binning", 5))}
+    tc, f64 = rbf.rbf_rasm_factor_counts(h)
+    factors = {"precision": "fp32 tensor cores" if mode == "mixed" else "fp64", "tensor_core_subdomains": tc,
+               "fp64_subdomains": f64}
+
+    # the mixed form with subdomain inverses computed in FP64 (stored FP32), for
+    # the inner-step cost of the tensor-core inverses
+    if mode == "mixed" and not args.no_extra:
+        c3 = cfg_for("mixed")
+        c3.factor_precision = rbf.RBF_FP32_FROM_FP64
+        flush.zero_()
+        step(c3)
+        ts, (st3, i3) = timed_steps(lambda: step(c3), 1, flush, barrier)
+        factors["fp64_computed_inverses"] = {"ms_per_step": ts[0], "iters": i3.iters, "relres": i3.relres,
+                                             "status": st3}
+        factors["inner_step_ratio_tc_over_fp64"] = info["iters"] / max(i3.iters, 1)
 
     # the other precision on the same inputs, for the "mixed vs FP64" comparison
     extra = None
@@ -543,7 +558,7 @@ def run_ours(args, ws, rank, local):
                "config": {**workload_config(name, p, mode, args.inner_cutoff), "tuned": tuned},
                "value_is": f"{mode} solve (bin + RASM setup + GMRES) to relres 1e-13, mean of the timed steps",
                "ok": ok, "solve": info, "step_ms": [round(t, 3) for t in times], "roofline": roofline,
-               "roofline_f64_matvec": roof64, "breakdown_ms": breakdown,
+               "roofline_f64_matvec": roof64, "breakdown_ms": breakdown, "rasm_factors": factors,
                "breakdown_note": "one extra step after the timed region with every kernel class recorded",
                "other_precision": extra, "serve": serve, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clk}

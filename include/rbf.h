@@ -46,7 +46,18 @@ typedef enum {
     RBF_ERR_STATE = 8                 /* call out of order (e.g. apply before setup) */
 } rbf_status;
 
-enum { RBF_FP64 = 0, RBF_FP32 = 1 };
+/* Precisions. For rbf_matvec: RBF_FP64 or RBF_FP32. For the subdomain
+ * inverses of rbf_rasm_setup (rbf_rasm_params.precision):
+ *   RBF_FP64           computed and stored in FP64 (Cholesky, Sec. 2.2);
+ *   RBF_FP32           computed in FP32 on the tensor cores and stored in FP32,
+ *                      for the inner solves of the mixed form: the block sweep
+ *                      (Gauss-Jordan without pivoting on the SPD A_i, 8 x 8
+ *                      blocks) with every product a TF32 MMA split into three
+ *                      (FP32 accuracy) and FP32 accumulation; a subdomain of
+ *                      more than 48 overlap points, or with an FP32 pivot that
+ *                      is not positive, is computed in FP64 instead;
+ *   RBF_FP32_FROM_FP64 computed in FP64 (as RBF_FP64), stored in FP32. */
+enum { RBF_FP64 = 0, RBF_FP32 = 1, RBF_FP32_FROM_FP64 = 2 };
 
 typedef struct rbf_ctx rbf_ctx;
 typedef void* rbf_stream;
@@ -69,7 +80,7 @@ typedef struct {
     double core_size;     /* B > 0 */
     double overlap;       /* delta >= 0 */
     int max_sub_points;   /* cap on an overlap list, 1..192 (0 = 192) */
-    int precision;        /* storage of the subdomain inverses: RBF_FP64 or RBF_FP32 */
+    int precision;        /* subdomain inverses: RBF_FP64, RBF_FP32 (tensor cores) or RBF_FP32_FROM_FP64 */
     int additive;         /* 0: restricted (Eq. rasm, default); 1: plain additive Schwarz (Eq. asm), for
                            * comparison: every overlap entry of A_i^{-1} r_i is added back (full n x n
                            * inverses, about n_overlap / n_core times the memory) */
@@ -127,6 +138,11 @@ rbf_status rbf_matvec(rbf_ctx* ctx, const double* w_dev, double* y_dev, int prec
  * `stream`. Errors: SUBDOMAIN_TOO_LARGE if an overlap list exceeds
  * max_sub_points, NOT_SPD on a pivot <= 0, STATE without rbf_bin. */
 rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* params, rbf_stream stream);
+
+/* Subdomains whose inverse the last rbf_rasm_setup computed on the tensor
+ * cores (RBF_FP32) and in FP64 (every other one: all of them for RBF_FP64 and
+ * RBF_FP32_FROM_FP64), host outputs (either may be NULL). STATE before setup. */
+rbf_status rbf_rasm_factor_counts(rbf_ctx* ctx, int64_t* tensor_core, int64_t* fp64);
 
 /* z = M^{-1} r = sum_i ~R_i^T A_i^{-1} R_i r (Eq. rasm), n FP64 in user
  * order. Errors: STATE without rbf_rasm_setup. */

@@ -446,8 +446,9 @@ static rbf_status rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params, 
     if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_rasm_setup: call rbf_bin first");
     if (!params) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: null parameters");
     const int precision = params[0].precision;
-    if (precision != RBF_FP64 && precision != RBF_FP32)
-        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_rasm_setup: precision must be RBF_FP64 or RBF_FP32");
+    if (precision != RBF_FP64 && precision != RBF_FP32 && precision != RBF_FP32_FROM_FP64)
+        return fail(ctx, RBF_ERR_INVALID_ARG,
+                    "rbf_rasm_setup: precision must be RBF_FP64, RBF_FP32 or RBF_FP32_FROM_FP64");
     int cap = 0;
     int64_t nsub = 0;
     for (int64_t b = 0; b < ctx->nprob; ++b) {
@@ -516,6 +517,15 @@ rbf_status rbf_rasm_setup(rbf_ctx* ctx, const rbf_rasm_params* p, rbf_stream str
 rbf_status rbf_rasm_setup_batch(rbf_ctx* ctx, const rbf_rasm_params* params_host, rbf_stream stream)
 {
     return rasm_setup_batch(ctx, params_host, S(stream));
+}
+
+rbf_status rbf_rasm_factor_counts(rbf_ctx* ctx, int64_t* tensor_core, int64_t* fp64)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->rasm_ready) return fail(ctx, RBF_ERR_STATE, "rbf_rasm_factor_counts: call rbf_rasm_setup first");
+    if (tensor_core) *tensor_core = ctx->factor_tc;
+    if (fp64) *fp64 = ctx->factor_fp64;
+    return RBF_OK;
 }
 
 rbf_status rbf_rasm_apply(rbf_ctx* ctx, const double* r_dev, double* z_dev, rbf_stream stream)

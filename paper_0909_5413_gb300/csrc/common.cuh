@@ -175,6 +175,8 @@ struct rbf_ctx {
     rbf::DevArray<double> asm_u64;
     rbf::DevArray<float> asm_u32;
     rbf::DevArray<int> status_dev;
+    rbf::DevArray<int32_t> tc_fb;   // tensor-core setup: [0] count, then the subdomains left to FP64
+    int64_t factor_tc = 0, factor_fp64 = 0;   // subdomains factored by each path at the last setup
 
     // ---- solver workspace
     rbf::DevArray<double> V, vec_a, vec_b, vec_c, vec_d, vec_e, partial;
@@ -309,6 +311,10 @@ void batch_graph_reset(rbf_ctx* ctx);
 rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st);
 rbf_status asm_lists(rbf_ctx* ctx, cudaStream_t st);   // overlap entries per point (Eq. asm only)
 rbf_status rasm_apply_sorted(rbf_ctx* ctx, const double* r, double* z, cudaStream_t st);
+// ---- rasm_tc.cu: FP32 inverses on the tensor cores (RBF_FP32); the subdomains
+// it cannot take are written to fb_list and counted in *fb_host
+rbf_status rasm_factor_tc(rbf_ctx* ctx, int32_t* fb_list, unsigned int* fb_count_dev, int64_t* fb_host,
+                          cudaStream_t st);
 
 // ---- gmres.cu
 rbf_status gmres_solve(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,

@@ -35,6 +35,7 @@ constexpr int kBChunk = kOrthoChunk;   // elements per chunk
 
 enum BField { F_H1 = 0, F_H2 = 1, F_NRM2 = 2, F_BETA2 = 3, F_FNORM2 = 4 };
 
+
 __device__ __forceinline__ double* field_ptr(GmresDev& g, int field)
 {
     switch (field) {
@@ -209,7 +210,10 @@ __global__ void k_bscale(T* __restrict__ x, Chunks C, const GmresDev* __restrict
     const GmresDev& g = gm[pb];
     if (which == 1 && g.done && g.breakdown) return;
     const double f = which == 0 ? g.inv_beta : g.inv_h;
-    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = (T)((double)x[i] * f);
+    // FP32 bases are scaled in FP32 (the factor rounded once): the FP64 pipe of
+    // GB300 would make a per-element FP64 product the cost of the pass
+    const T fT = (T)f;
+    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = x[i] * fT;
 }
 
 // End of Arnoldi step j, one block per chunk: v_{j+1} /= |v_{j+1}| for the
@@ -239,7 +243,10 @@ __global__ void __launch_bounds__(256)
             if (done) run[pb] = 0;
         }
     }
-    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = (T)((double)x[i] * f);
+    // FP32 bases are scaled in FP32 (the factor rounded once): the FP64 pipe of
+    // GB300 would make a per-element FP64 product the cost of the pass
+    const T fT = (T)f;
+    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) x[i] = x[i] * fT;
 }
 
 // FP32 copy of r scaled by the problem's inv_beta (inner start of the mixed form).
@@ -254,30 +261,41 @@ __global__ void k_bto_f32_scaled(const double* __restrict__ r, int64_t n, const 
     }
 }
 
-// t = sum_{q < k_b} y_q V_q with the problem's own step count and y.
+// t = sum_{q < k_b} y_q V_q with the problem's own step count and y, one
+// block per chunk: the chunk's problem's coefficients are staged once in
+// shared memory (with their float split for FP32 bases), and every element
+// sums its q terms in order.
 template <class T>
-__global__ void k_bcombine(const T* __restrict__ V, int64_t ldv, const GmresDev* __restrict__ gm,
-                           const int32_t* __restrict__ pid, const int32_t* __restrict__ active, T* __restrict__ t,
-                           int64_t n)
+__global__ void __launch_bounds__(256)
+    k_bcombine(const T* __restrict__ V, int64_t ldv, const GmresDev* __restrict__ gm, Chunks C,
+               const int32_t* __restrict__ active, T* __restrict__ t)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int pb = pid[i];
-        if (!active[pb]) continue;
-        const GmresDev& g = gm[pb];
-        const int k = g.j;
+    __shared__ double ys[kMaxRestart];
+    __shared__ float yh[kMaxRestart], yl[kMaxRestart];
+    const int64_t c = blockIdx.x;
+    const int pb = C.pid[c];
+    if (!active[pb]) return;
+    const GmresDev& g = gm[pb];
+    const int k = g.j;
+    if (threadIdx.x < (unsigned)k) {
+        const double v = g.y[threadIdx.x];
+        ys[threadIdx.x] = v;
+        yh[threadIdx.x] = (float)v;
+        yl[threadIdx.x] = (float)(v - (double)(float)v);
+    }
+    __syncthreads();
+    for (int64_t i = C.beg[c] + threadIdx.x; i < C.end[c]; i += blockDim.x) {
         if constexpr (sizeof(T) == 4) {
             DF a{0.f, 0.f};
             for (int q = 0; q < k; ++q) {
-                double c = g.y[q];
-                float ch = (float)c, cl = (float)(c - (double)ch);
-                float vi = V[q * ldv + i];
-                float h = ch * vi;
-                df_add(a, h, fmaf(cl, vi, fmaf(ch, vi, -h)));
+                const float vi = V[q * ldv + i];
+                const float h = yh[q] * vi;
+                df_add(a, h, fmaf(yl[q], vi, fmaf(yh[q], vi, -h)));
             }
             t[i] = a.hi + a.lo;
         } else {
             double a = 0.0;
-            for (int q = 0; q < k; ++q) a = fma(g.y[q], (double)V[q * ldv + i], a);
+            for (int q = 0; q < k; ++q) a = fma(ys[q], (double)V[q * ldv + i], a);
             t[i] = (T)a;
         }
     }
@@ -419,7 +437,7 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
     }
     ctx->prof_step = -1;
     RBF_LAUNCH(ctx, k_bsolve_y, pb_blocks, 128, 0, st, B.gm, B.nprob, B.active);
-    RBF_LAUNCH(ctx, (k_bcombine<T>), bstream_blocks(n), 256, 0, st, V, ldv, B.gm, B.pid, B.active, t, n);
+    RBF_LAUNCH(ctx, (k_bcombine<T>), (unsigned)B.C.nc, 256, 0, st, V, ldv, B.gm, B.C, B.active, t);
     RBF_CHECK(BOps<T>::minv(ctx, t, u, st));
     RBF_LAUNCH(ctx, (k_baxpy<T>), bstream_blocks(n), 256, 0, st, w, u, B.pid, B.active,
                (sizeof(T) == 4 && ctx->inner_on) ? (const int32_t*)ctx->in.perm.p : nullptr, n);

@@ -43,12 +43,13 @@ __global__ void __launch_bounds__(kSetupWarps * 32)
                  const int32_t* __restrict__ core_ptr, const int64_t* __restrict__ w_off, int64_t nsub, int nmax,
                  int wpb, const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub, int full,
                  const unsigned long long* __restrict__ fxtab, double* __restrict__ W64, float* __restrict__ W32,
-                 int* __restrict__ status)
+                 int* __restrict__ status, const int32_t* __restrict__ sub_list)
 {
     extern __shared__ double sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t sub = (int64_t)blockIdx.x * wpb + warp;
-    if (warp >= wpb || sub >= nsub) return;
+    const int64_t idx = (int64_t)blockIdx.x * wpb + warp;
+    if (warp >= wpb || idx >= nsub) return;
+    const int64_t sub = sub_list ? (int64_t)sub_list[idx] : idx;   // sub_list: the subdomains to factor
     const Prob& pr = prob[pid_sub[sub]];
     const double rc2 = pr.rc2, s = pr.s, knorm = pr.knorm;
     const int xstride = nmax | 1;
@@ -198,7 +199,9 @@ __global__ void __launch_bounds__(256)
     const int64_t idx = (int64_t)blockIdx.x * 8 + warp;
     if (idx >= nsub) return;
     const int64_t sub = sub_list ? (int64_t)sub_list[idx] : idx;   // sub_list: the active problems' subdomains
-    if (active && !active[pid_sub[sub]]) return;   // masked problem (warp-uniform)
+    // the problem's mask is read here but tested only once the first loads of W
+    // and of the overlap list are in flight (its latency then overlaps theirs)
+    const int32_t* mask = active ? active + pid_sub[sub] : nullptr;
     TV* rg = rg_all[warp];
     const int b = ov_ptr[sub];
     const int n = ov_ptr[sub + 1] - b;
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(256)
         int ia[kG];
 #pragma unroll
         for (int t = 0; t < kG; ++t) ia[t] = lane + 32 * t < n ? ov_idx[b + lane + 32 * t] : -1;
+        if (mask && !*mask) return;   // masked problem (warp-uniform); nothing has been written
         TV rv[kG];
 #pragma unroll
         for (int t = 0; t < kG; ++t) rv[t] = ia[t] >= 0 ? r[ia[t]] : (TV)0;
@@ -335,7 +339,7 @@ rbf_status asm_lists(rbf_ctx* ctx, cudaStream_t st)
                ctx->asm_fill.p, ctx->asm_tidx.p);
     RBF_LAUNCH(ctx, k_asm_sort, blocks_for(n, 256), 256, 0, st, ctx->asm_tptr.p, n, ctx->asm_tidx.p);
     RBF_CHECK(ensure(ctx, ctx->asm_u64, tot));
-    if (ctx->rasm_precision == RBF_FP32) RBF_CHECK(ensure(ctx, ctx->asm_u32, tot));
+    if (ctx->rasm_precision != RBF_FP64) RBF_CHECK(ensure(ctx, ctx->asm_u32, tot));
     return RBF_OK;
 }
 
@@ -363,19 +367,42 @@ rbf_status rasm_factor(rbf_ctx* ctx, cudaStream_t st)
         W32 = ctx->W32.p;
     }
     const int nmax = ctx->max_ov;
+    ctx->factor_tc = 0;
+    ctx->factor_fp64 = 0;
     if (nmax == 0) return RBF_OK;
     const size_t per = setup_doubles(nmax) * sizeof(double);
-    if (per > kSetupSmemMax)
-        return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
-                    "rbf_rasm_setup: a %d-point overlap list needs %zu KB of shared memory", nmax, per / 1024);
     // as many warps per block as fit in kSetupSmemMax of shared memory (at most kSetupWarps)
-    int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, kSetupSmemMax / per));
-    size_t smem = per * wpb;
-    RBF_CUDA(ctx, cudaFuncSetAttribute(k_rasm_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int wpb = (int)std::min<size_t>(kSetupWarps, std::max<size_t>(1, kSetupSmemMax / per));
+    const size_t smem = per * wpb;
+    const bool fits = per <= kSetupSmemMax;
+    if (fits)
+        RBF_CUDA(ctx, cudaFuncSetAttribute(k_rasm_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RBF_CHECK(prof_begin(ctx, RBF_PROF_RASM_SETUP, st));
-    RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nsub, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
-               ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, wpb, ctx->prob.p,
-               ctx->pid_sub.p, full, ctx->fxtab.p, W64, W32, ctx->status_dev.p);
+    if (ctx->rasm_precision == RBF_FP32) {
+        // FP32 inverses on the tensor cores; the subdomains they leave are factored in FP64
+        RBF_CHECK(ensure(ctx, ctx->tc_fb, (size_t)nsub + 1));
+        int64_t nfb = 0;
+        RBF_CHECK(rasm_factor_tc(ctx, ctx->tc_fb.p + 1, (unsigned int*)ctx->tc_fb.p, &nfb, st));
+        ctx->factor_tc = nsub - nfb;
+        ctx->factor_fp64 = nfb;
+        if (nfb > 0) {
+            if (!fits)
+                return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
+                            "rbf_rasm_setup: a %d-point overlap list needs %zu KB of shared memory", nmax, per / 1024);
+            RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nfb, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p,
+                       ctx->ov_ptr.p, ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nfb, nmax, wpb,
+                       ctx->prob.p, ctx->pid_sub.p, full, ctx->fxtab.p, (double*)nullptr, W32, ctx->status_dev.p,
+                       (const int32_t*)(ctx->tc_fb.p + 1));
+        }
+    } else {
+        if (!fits)
+            return fail(ctx, RBF_ERR_SUBDOMAIN_TOO_LARGE,
+                        "rbf_rasm_setup: a %d-point overlap list needs %zu KB of shared memory", nmax, per / 1024);
+        ctx->factor_fp64 = nsub;
+        RBF_LAUNCH(ctx, k_rasm_setup, blocks_for(nsub, wpb), kSetupWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
+                   ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, nmax, wpb, ctx->prob.p,
+                   ctx->pid_sub.p, full, ctx->fxtab.p, W64, W32, ctx->status_dev.p, (const int32_t*)nullptr);
+    }
     RBF_CHECK(prof_end(ctx, RBF_PROF_RASM_SETUP, st));
     int status = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&status, ctx->status_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -226,7 +226,7 @@ int64_t rbf_request_footprint(const rbf_request* r)
     }
     const int m = (r->solve.restart > 0 && r->solve.restart <= 32) ? r->solve.restart : 30;
     const bool mixed = r->solve.mixed != 0;
-    const bool f32 = r->rasm.precision == RBF_FP32;
+    const bool f32 = r->rasm.precision != RBF_FP64;
     double per = 32.0;                                 // staging xy, f, w
     per += 60.0;                                       // sorted points, permutations, cell ids, FP32 offsets
     per += 8.0 + 4.0 * n_ov / n_core;                  // core and overlap lists

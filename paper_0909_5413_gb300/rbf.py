@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "librbf.so")
 
 RBF_FP64 = 0
 RBF_FP32 = 1
+RBF_FP32_FROM_FP64 = 2
 
 STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_INVALID_ARG", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA", 4: "RBF_ERR_NOT_SPD",
                 5: "RBF_ERR_SUBDOMAIN_TOO_LARGE", 6: "RBF_ERR_NOT_CONVERGED", 7: "RBF_ERR_TIMEOUT",
@@ -30,7 +31,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
             "rbf_count_candidates", "rbf_profile_classes", "rbf_set_memory_limit",
-            "rbf_count_pairs"]
+            "rbf_count_pairs", "rbf_rasm_factor_counts"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -109,6 +110,7 @@ def load(path: str | None = None):
     L.rbf_matvec.argtypes = [P, P, P, C.c_int, P]
     L.rbf_rasm_setup.argtypes = [P, C.POINTER(RbfRasmParams), P]
     L.rbf_rasm_apply.argtypes = [P, P, P, P]
+    L.rbf_rasm_factor_counts.argtypes = [P, I64, I64]
     L.rbf_solve.argtypes = [P, P, P, C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
     L.rbf_interpolate_host.argtypes = [P, P, P, P, C.c_int64, C.POINTER(RbfParams), C.POINTER(RbfRasmParams),
                                        C.POINTER(RbfSolveParams), C.POINTER(RbfSolveInfo), P]
@@ -228,6 +230,13 @@ def rbf_matvec_noalloc(ctx, w_dev, y_dev, stream=None) -> None:
 
 def rbf_rasm_setup(ctx, params: RbfRasmParams, stream=None) -> None:
     _check(ctx, load().rbf_rasm_setup(ctx, C.byref(params), _stream(stream)))
+
+
+def rbf_rasm_factor_counts(ctx) -> tuple[int, int]:
+    """(subdomains inverted on the tensor cores, subdomains inverted in FP64) at the last setup."""
+    tc, f64 = C.c_int64(), C.c_int64()
+    _check(ctx, load().rbf_rasm_factor_counts(ctx, C.byref(tc), C.byref(f64)))
+    return tc.value, f64.value
 
 
 def rbf_rasm_apply(ctx, r_dev, z_dev, stream=None) -> None:
