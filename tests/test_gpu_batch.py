@@ -225,10 +225,11 @@ def test_batch_tail_after_compaction_matches_alone(rbf, mixed):
 
 def config4_slice():
     """A seeded slice of the 4096-problem batch workload (the same (n_side, h/sigma)
-    draws and per-problem seeds as the full batch): its largest problem (128 x 128
-    = 16,384 points) and eleven others drawn at random, all at h/sigma >= 0.7."""
+    draws and per-problem seeds as the full batch): its largest problem at
+    h/sigma >= 0.7 (128 x 128 = 16,384 points) and eleven others drawn at random,
+    all at h/sigma >= 0.7 (below it the 4 x 4-point subdomains stall GMRES)."""
     sizes = W.batch_problem_sizes(4096, 256, 16384, W.DEFAULT_SEED)
-    big = int(np.argmax([s[0] for s in sizes]))
+    big = int(np.argmax([s[0] if s[1] >= 0.7 else 0 for s in sizes]))
     rng = np.random.default_rng(77)
     pick = [big]
     for k in rng.permutation(len(sizes)):
