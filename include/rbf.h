@@ -378,6 +378,17 @@ rbf_status rbf_profile_read(rbf_ctx* ctx, int kernel, int64_t* launches, double*
  * without the normalisation factor). STATE before rbf_bin. */
 rbf_status rbf_debug_kernel_pairs(rbf_ctx* ctx, const double* pairs_dev, double* out_dev, int64_t n,
                                   rbf_stream stream);
+/* The FP32 operator of the mixed form's inner solves, y = A_i w, on the grid
+ * of the inner cutoff (inner_cutoff sigma; built if needed, as the solver
+ * builds it): every pair of the 3 x 3 cell stencil, FP32 on cell-local
+ * offsets, no cutoff mask. w_dev, y_dev: n FP64 in user order (rounded to FP32
+ * on the way in). variant 0: the symmetric kernel the solver uses (each
+ * neighbouring cell pair once, column sums gathered in a fixed order; STATE
+ * if a cell holds more than 128 points); variant 1: the stencil kernel (every
+ * target against its 3 x 3 cells). For accuracy checks of the two against
+ * each other and against the FP64 truncated matvec. */
+rbf_status rbf_debug_inner_matvec(rbf_ctx* ctx, double inner_cutoff, const double* w_dev, double* y_dev, int variant,
+                                  rbf_stream stream);
 /* out[i] = exp(-t[i]) for n FP64 values on the device: variant 0 is the
  * library's table-driven exp with 64 entries (subdomain setup), variant 2 the
  * 2048-entry one of the FP64 matvec, variant 1 CUDA's exp(); for accuracy

@@ -261,6 +261,13 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
+// Points per cell.
+__global__ void k_cell_sizes(const int32_t* __restrict__ cell_start, int64_t ncell, int32_t* __restrict__ out)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) out[c] = cell_start[c + 1] - cell_start[c];
+}
+
 // Pairs (i, j), i = j included, of a cell grid with r2_ij <= R^2 by the FP64
 // pair test (R = r_c on the main grid, the cell side on the inner grid, whose
 // cells are as wide as its cutoff), summed as 64-bit (one atomic per warp).
@@ -414,6 +421,21 @@ __global__ void k_inner_gather_scaled(const double* __restrict__ r, const int32_
     const double f = *scale;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
         out[q] = (float)(r[perm[q]] * f);
+}
+
+// Inner order <-> main cell order without scaling (diagnostics of the inner operator).
+__global__ void k_inner_from_main(const double* __restrict__ r, const int32_t* __restrict__ perm, int64_t n,
+                                  float* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = (float)r[perm[q]];
+}
+
+__global__ void k_main_from_inner(const float* __restrict__ v, const int32_t* __restrict__ perm, int64_t n,
+                                  double* __restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[perm[q]] = (double)v[q];
 }
 
 __global__ void k_widen_i32_i64(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
@@ -697,6 +719,11 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
     int32_t smax = 0;
     RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &smax, st));
     G.stage_max = smax;
+    // the symmetric FP32 kernel takes cells of at most 128 points (four targets per lane)
+    RBF_LAUNCH(ctx, k_cell_sizes, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, G.wcnt.p);
+    int32_t cmax = 0;
+    RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &cmax, st));
+    G.sym = cmax <= 128;
     // subdomain lists in inner positions
     if (ctx->rasm_ready) {
         int32_t tot[2] = {0, 0};
@@ -720,6 +747,29 @@ rbf_status inner_gather_scaled(rbf_ctx* ctx, const double* r_main, const double*
 {
     RBF_LAUNCH(ctx, k_inner_gather_scaled, blocks_for(std::min<int64_t>(ctx->n, 16 * kNumSMs * 256), 256), 256, 0, st,
                r_main, ctx->in.perm.p, ctx->n, scale_dev, out_inner);
+    return RBF_OK;
+}
+
+rbf_status inner_matvec_debug(rbf_ctx* ctx, double ri_sigmas, const double* w_main, double* y_main, int variant,
+                              cudaStream_t st)
+{
+    if (!ctx->in.ready || ctx->in.ri_sigmas != ri_sigmas) RBF_CHECK(bin_inner(ctx, ri_sigmas, st));
+    if (variant == 0 && !ctx->in.sym)
+        return fail(ctx, RBF_ERR_STATE, "rbf_debug_inner_matvec: an inner cell holds more than 128 points");
+    const int64_t n = ctx->n;
+    RBF_CHECK(ensure(ctx, ctx->vec_c, (size_t)n));   // two FP32 vectors
+    float* wf = (float*)ctx->vec_c.p;
+    float* yf = wf + n;
+    RBF_LAUNCH(ctx, k_inner_from_main, blocks_for(n, 256), 256, 0, st, w_main, ctx->in.perm.p, n, wf);
+    const bool on = ctx->inner_on;
+    const int mode = ctx->sym_mode;
+    ctx->inner_on = true;
+    ctx->sym_mode = variant;
+    const rbf_status s = matvec_f32_raw(ctx, nullptr, wf, yf, st);
+    ctx->inner_on = on;
+    ctx->sym_mode = mode;
+    RBF_CHECK(s);
+    RBF_LAUNCH(ctx, k_main_from_inner, blocks_for(n, 256), 256, 0, st, yf, ctx->in.perm.p, n, y_main);
     return RBF_OK;
 }
 

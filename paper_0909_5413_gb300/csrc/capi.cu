@@ -698,6 +698,21 @@ rbf_status rbf_count_candidates(rbf_ctx* ctx, int grid, int64_t* total, rbf_stre
     return count_candidates(ctx, grid, total, S(stream));
 }
 
+rbf_status rbf_debug_inner_matvec(rbf_ctx* ctx, double inner_cutoff, const double* w_dev, double* y_dev, int variant,
+                                  rbf_stream stream)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    if (!ctx->binned) return fail(ctx, RBF_ERR_STATE, "rbf_debug_inner_matvec: call rbf_bin first");
+    if (!w_dev || !y_dev || !(inner_cutoff > 0.0) || (variant != 0 && variant != 1))
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_debug_inner_matvec: bad argument");
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CHECK(ensure(ctx, ctx->vec_a, ctx->n));
+    RBF_CHECK(ensure(ctx, ctx->vec_b, ctx->n));
+    RBF_CHECK(permute_to_sorted(ctx, w_dev, ctx->vec_a.p, S(stream)));
+    RBF_CHECK(inner_matvec_debug(ctx, inner_cutoff, ctx->vec_a.p, ctx->vec_b.p, variant, S(stream)));
+    return permute_to_user(ctx, ctx->vec_b.p, y_dev, S(stream));
+}
+
 rbf_status rbf_count_pairs(rbf_ctx* ctx, int grid, int64_t* total, rbf_stream stream)
 {
     if (!ctx || !total || (grid != 0 && grid != 1)) return RBF_ERR_INVALID_ARG;

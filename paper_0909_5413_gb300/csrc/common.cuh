@@ -77,6 +77,7 @@ struct Prob {
 // subdomain lists re-indexed into that order.
 struct InnerGrid {
     bool ready = false;
+    bool sym = false;          // every cell holds at most 128 points: the symmetric FP32 kernel applies
     double ri_sigmas = 0.0;
     int tile = 64;
     int stage_max = 0;
@@ -156,6 +157,8 @@ struct rbf_ctx {
     EvalBins ev;                   // rbf_eval targets
     InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
     bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
+    int sym_mode = 0;              // inner FP32 operator: 0 symmetric kernel when the grid allows, 1 stencil kernel
+    rbf::DevArray<float> sym_slots;   // symmetric FP32 kernel: row slot and four column slots per point
     rbf::DevArray<unsigned long long> count_u64;   // one 64-bit counter (rbf_count_candidates)
     rbf::DevArray<int> flag_dev;                   // one flag (zero initial guess test of the solvers)
     double exp2048_c[3] = {0, 0, 0};
@@ -279,6 +282,9 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st);
 rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t st);
 // Sum over the cells of grid 0 (r_c cells) or 1 (inner grid) of points x stencil points.
 rbf_status count_candidates(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
+// The FP32 inner operator on main cell-ordered FP64 vectors (variant 0: symmetric kernel, 1: stencil kernel).
+rbf_status inner_matvec_debug(rbf_ctx* ctx, double ri_sigmas, const double* w_main, double* y_main, int variant,
+                              cudaStream_t st);
 // Pairs within the grid's cutoff (r_c on grid 0, the inner cutoff on grid 1), FP64 pair test.
 rbf_status count_pairs(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st);
 // Main cell order <-> inner order for the FP32 hand-offs of the mixed form.

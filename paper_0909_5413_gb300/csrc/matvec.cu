@@ -347,6 +347,186 @@ __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __r
     if (active) y[p] = ((acc2.x + acc2.y) + (acc2b.x + acc2b.y)) * knorm;
 }
 
+// Symmetric FP32 matvec on the inner grid: every unordered pair of
+// neighbouring cells is visited once. One warp per cell C (at most
+// kSymMaxCell points, up to four targets per lane) takes C itself (row sums
+// only: all pairs inside C) and its four forward neighbours D = C + d,
+// d in {(1,0), (-1,1), (0,1), (1,1)}: each kernel value k_ij (i in C, j in D)
+// feeds the row sum of i (registers) and the column sum of j, which is
+// reduced over the warp's targets through a shared transpose (lane j adds the
+// 32 rows in order) and written to point j's slot for direction d. The
+// gather then adds, per point, its row slot and the column slots of its
+// existing backward neighbours in a fixed order: deterministic, with half
+// the exp2 evaluations of the stencil sweep. Sources are staged as FP32
+// offsets from C's corner (scaled so that the kernel is exp2(-|dX|^2)), in
+// chunks of 32 padded with far, zero-weight sources.
+constexpr int kSymWarps = 4;
+constexpr int kSymMaxCell = 128;
+constexpr int kSymStage = kSymMaxCell + 32;
+constexpr int kSymTld = 36;   // row stride of the transpose buffer (16-byte rows, conflict-free columns)
+
+struct SymWarp {
+    float sx[kSymStage], sy[kSymStage], sw[kSymStage];
+    float T[32 * kSymTld];
+};
+
+template <int TPL, bool COL>
+__device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx)[TPL], const float2 (&ty)[TPL],
+                                         const float (&wt)[TPL], float2 (&acc)[TPL], float2 (&acc2)[TPL], int dn,
+                                         float* __restrict__ colout)
+{
+    const int dnp = (dn + 31) & ~31;
+    for (int c0 = 0; c0 < dnp; c0 += 32) {
+        float col[32];
+        if (COL) {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) col[s] = 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < 32; s += 4) {
+            const float4 X = *reinterpret_cast<const float4*>(&S.sx[c0 + s]);
+            const float4 Y = *reinterpret_cast<const float4*>(&S.sy[c0 + s]);
+            const float4 Wv = *reinterpret_cast<const float4*>(&S.sw[c0 + s]);
+#pragma unroll
+            for (int t = 0; t < TPL; ++t) {
+                const float2 dx0 = f2_sub(tx[t], make_float2(X.x, X.y)), dy0 = f2_sub(ty[t], make_float2(Y.x, Y.y));
+                const float2 dx1 = f2_sub(tx[t], make_float2(X.z, X.w)), dy1 = f2_sub(ty[t], make_float2(Y.z, Y.w));
+                const float2 r0 = f2_fma(dy0, dy0, f2_mul(dx0, dx0));
+                const float2 r1 = f2_fma(dy1, dy1, f2_mul(dx1, dx1));
+                const float2 e0 = make_float2(ex2_approx(-r0.x), ex2_approx(-r0.y));
+                const float2 e1 = make_float2(ex2_approx(-r1.x), ex2_approx(-r1.y));
+                acc[t] = f2_fma(e0, make_float2(Wv.x, Wv.y), acc[t]);
+                acc2[t] = f2_fma(e1, make_float2(Wv.z, Wv.w), acc2[t]);
+                if (COL) {
+                    const float2 w2 = make_float2(wt[t], wt[t]);
+                    const float2 c01 = f2_fma(e0, w2, make_float2(col[s], col[s + 1]));
+                    const float2 c23 = f2_fma(e1, w2, make_float2(col[s + 2], col[s + 3]));
+                    col[s] = c01.x;
+                    col[s + 1] = c01.y;
+                    col[s + 2] = c23.x;
+                    col[s + 3] = c23.y;
+                }
+            }
+        }
+        if (COL) {
+            float4* row = reinterpret_cast<float4*>(&S.T[lane * kSymTld]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) row[k] = make_float4(col[4 * k], col[4 * k + 1], col[4 * k + 2], col[4 * k + 3]);
+            __syncwarp();
+            float sum = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) sum += S.T[r * kSymTld + lane];
+            __syncwarp();
+            if (c0 + lane < dn) colout[c0 + lane] = sum;
+        }
+    }
+}
+
+template <int TPL>
+__device__ __forceinline__ void sym_cell(const MvParams& P, SymWarp& S, int lane, int cell, int cb, int cnt,
+                                         const Prob& pr, const float* __restrict__ w, float* __restrict__ rowslot,
+                                         float* __restrict__ colslot, int64_t n)
+{
+    const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, cbase = (int)pr.cellbase;
+    const float ca = pr.ca;
+    const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
+    float2 tx[TPL], ty[TPL], acc[TPL], acc2[TPL];
+    float wt[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int q = lane + 32 * t;
+        const bool ok = q < cnt;
+        const float2 l = ok ? reinterpret_cast<const float2*>(P.loc)[cb + q] : make_float2(-1.0e4f, -1.0e4f);
+        tx[t] = make_float2(l.x, l.x);
+        ty[t] = make_float2(l.y, l.y);
+        wt[t] = ok ? w[cb + q] : 0.f;
+        acc[t] = make_float2(0.f, 0.f);
+        acc2[t] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < 5; ++pass) {
+        const int dx = (pass == 1 || pass == 4) ? 1 : (pass == 2 ? -1 : 0);
+        const int dy = pass >= 2 ? 1 : 0;
+        const int nx = cx + dx, ny = cy + dy;
+        if (nx < 0 || nx >= ncx || ny >= ncy) continue;
+        const int dcell = cbase + ny * ncx + nx;
+        const int db = P.cell_start[dcell], dn = P.cell_start[dcell + 1] - db;
+        if (dn == 0) continue;
+        const int dnp = (dn + 31) & ~31;
+        for (int s = lane; s < dnp; s += 32) {
+            if (s < dn) {
+                const float2 l = reinterpret_cast<const float2*>(P.loc)[db + s];
+                S.sx[s] = l.x + (float)dx * ca;
+                S.sy[s] = l.y + (float)dy * ca;
+                S.sw[s] = w[db + s];
+            } else {
+                S.sx[s] = 1.0e4f;
+                S.sy[s] = 1.0e4f;
+                S.sw[s] = 0.f;
+            }
+        }
+        __syncwarp();
+        if (pass == 0) sym_pass<TPL, false>(S, lane, tx, ty, wt, acc, acc2, dn, nullptr);
+        else sym_pass<TPL, true>(S, lane, tx, ty, wt, acc, acc2, dn, colslot + (int64_t)(pass - 1) * n + db);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int q = lane + 32 * t;
+        if (q < cnt) rowslot[cb + q] = (acc[t].x + acc[t].y) + (acc2[t].x + acc2[t].y);
+    }
+}
+
+// One warp per cell: the cell's first work item (a cell of more points than
+// the work tile has further items, which return).
+__global__ void __launch_bounds__(kSymWarps * 32)
+    k_matvec_f32_sym(MvParams P, int64_t nwork, const float* __restrict__ w, float* __restrict__ rowslot,
+                     float* __restrict__ colslot, int64_t n)
+{
+    __shared__ __align__(16) SymWarp sm_all[kSymWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kSymWarps + warp;
+    if (item >= nwork) return;
+    const int cell = P.work[2 * item], first = P.work[2 * item + 1];
+    if (first != 0) return;
+    const int pcell = P.pid_cell[cell];
+    if (P.active && !P.active[pcell]) return;
+    const Prob& pr = P.prob[pcell];
+    const int cb = P.cell_start[cell], cnt = P.cell_start[cell + 1] - cb;
+    SymWarp& S = sm_all[warp];
+    switch ((cnt + 31) >> 5) {   // warp-uniform; the binning guarantees cnt <= kSymMaxCell
+    case 1: sym_cell<1>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
+    case 2: sym_cell<2>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
+    case 3: sym_cell<3>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
+    default: sym_cell<4>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
+    }
+}
+
+// y_p = row slot + the column slots of p's backward neighbours C = cell(p) - d
+// that exist and hold points, in the order of d, times the normalisation.
+__global__ void k_sym_gather(const float* __restrict__ rowslot, const float* __restrict__ colslot, int64_t n,
+                             const int32_t* __restrict__ cell_s, const int32_t* __restrict__ cell_start,
+                             const Prob* __restrict__ prob, const int32_t* __restrict__ pid,
+                             const int32_t* __restrict__ active, float* __restrict__ y)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int pb = pid[p];
+    if (active && !active[pb]) return;
+    const Prob& pr = prob[pb];
+    const int ncx = (int)pr.ncx, cbase = (int)pr.cellbase;
+    const int lc = cell_s[p] - cbase, cx = lc % ncx, cy = lc / ncx;
+    float s = rowslot[p];
+    const int bx[4] = {cx - 1, cx + 1, cx, cx - 1}, by[4] = {cy, cy - 1, cy - 1, cy - 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (bx[q] < 0 || bx[q] >= ncx || by[q] < 0) continue;
+        const int c = cbase + by[q] * ncx + bx[q];
+        if (cell_start[c + 1] > cell_start[c]) s += colslot[(int64_t)q * n + p];
+    }
+    y[p] = s * (float)pr.knorm;
+}
+
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -483,7 +663,17 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y,
         P.work = ctx->al.w32.p;
         nwork = ctx->al.n32;
     }
-    if (nwork > 0) {
+    if (nwork > 0 && ctx->inner_on && ctx->in.sym && ctx->sym_mode != 1) {
+        // each neighbouring pair of inner cells once, then the fixed-order gather
+        const int64_t n = ctx->n;
+        RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
+        float* rowslot = ctx->sym_slots.p;
+        float* colslot = rowslot + n;
+        RBF_LAUNCH(ctx, k_matvec_f32_sym, blocks_for(nwork, kSymWarps), kSymWarps * 32, 0, st, P, nwork, w, rowslot,
+                   colslot, n);
+        RBF_LAUNCH(ctx, k_sym_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, P.cell_s, P.cell_start,
+                   P.prob, ctx->pid.p, P.active, y);
+    } else if (nwork > 0) {
         switch (tile) {
         case 32: RBF_CHECK(launch_f32<32>(ctx, P, nwork, w, y, st)); break;
         case 64: RBF_CHECK(launch_f32<64>(ctx, P, nwork, w, y, st)); break;

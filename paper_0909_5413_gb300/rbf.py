@@ -31,7 +31,8 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_server_submit", "rbf_server_wait", "rbf_server_get_stats", "rbf_server_clock",
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
             "rbf_count_candidates", "rbf_profile_classes", "rbf_set_memory_limit",
-            "rbf_count_pairs", "rbf_rasm_factor_counts"]
+            "rbf_count_pairs", "rbf_rasm_factor_counts",
+            "rbf_debug_inner_matvec"]
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -137,6 +138,7 @@ def load(path: str | None = None):
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
     L.rbf_matvec_noalloc.argtypes = [P, P, P, P]
     L.rbf_debug_kernel_pairs.argtypes = [P, P, P, C.c_int64, P]
+    L.rbf_debug_inner_matvec.argtypes = [P, C.c_double, P, P, C.c_int, P]
     L.rbf_eval.argtypes = [P, P, C.c_int64, P, P, P]
     L.rbf_tune.argtypes = [P, P, C.c_int64, C.POINTER(RbfParams), C.c_double, C.c_double, C.POINTER(RbfParams),
                            C.POINTER(C.c_double), P]
@@ -360,6 +362,12 @@ def rbf_profile_read(ctx, kernel: int) -> tuple[int, float]:
 
 def rbf_debug_exp(ctx, t_dev, out_dev, variant: int = 0, stream=None) -> None:
     _check(ctx, load().rbf_debug_exp(ctx, _ptr(t_dev), _ptr(out_dev), t_dev.numel(), int(variant), _stream(stream)))
+
+
+def rbf_debug_inner_matvec(ctx, inner_cutoff: float, w_dev, y_dev, variant: int = 0, stream=None) -> None:
+    """The mixed form's FP32 inner operator (variant 0 symmetric kernel, 1 stencil kernel)."""
+    _check(ctx, load().rbf_debug_inner_matvec(ctx, float(inner_cutoff), _ptr(w_dev), _ptr(y_dev), int(variant),
+                                              _stream(stream)))
 
 
 def rbf_debug_kernel_pairs(ctx, pairs_dev, out_dev, stream=None) -> None:

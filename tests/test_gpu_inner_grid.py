@@ -136,3 +136,54 @@ def test_candidate_counts_of_both_grids(rbf):
     assert got == host_candidates(p.xy, min(6.1 * p.sigma, p.cutoff))
     assert got < rbf.rbf_count_candidates(ctx.handle, 0)
     ctx.close()
+
+
+def inner_apply(rbf, p, w, variant, ri=6.1):
+    ctx = rbf.Context(0)
+    rbf.rbf_bin(ctx.handle, dev(p.xy), p.n, rbf.RbfParams(p.sigma, p.cutoff, 0.0, 0))
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    rbf.rbf_debug_inner_matvec(ctx.handle, ri, dev(w), y, variant)
+    out = host(y)
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("n_side,ratio", [(96, 0.8), (130, 0.6), (64, 1.0), (37, 0.9)])
+def test_symmetric_inner_operator(rbf, n_side, ratio):
+    """The symmetric FP32 kernel (each neighbouring cell pair once) against the
+    stencil kernel (every target against its 3 x 3 cells), and both against the
+    oracle's FP64 matvec truncated at the inner cutoff: the pairs of the stencil
+    beyond r_i, which the FP32 operator keeps, are each below e^-18.6."""
+    p = W.lattice_problem(n_side, ratio, seed=400 + n_side)
+    w = np.random.default_rng(9).standard_normal(p.n)
+    ys = inner_apply(rbf, p, w, 0)
+    yt = inner_apply(rbf, p, w, 1)
+    scale = np.max(np.abs(yt))
+    assert np.max(np.abs(ys - yt)) <= 1e-5 * scale
+    ri = 6.1 * p.sigma
+    ref = O.matvec_cutoff(p.xy, w.astype(np.float32).astype(np.float64), p.sigma, ri, c=ri)
+    assert np.max(np.abs(ys - ref)) <= 2e-5 * np.max(np.abs(ref))
+
+
+def test_symmetric_inner_operator_random_points_and_dense_cells(rbf):
+    """Uneven cells (uniform random points, including empty cells); and a
+    clump whose inner cell exceeds 128 points, which the symmetric kernel
+    refuses (the solver then keeps the stencil kernel)."""
+    rng = np.random.default_rng(10)
+    xy = np.ascontiguousarray(rng.uniform(-1.0, 1.0, size=(6000, 2)))
+    from dataclasses import replace
+    base = W.lattice_problem(8, 0.8, seed=1)
+    p = replace(base, xy=xy, f=np.zeros(6000), sigma=0.02, cutoff=0.172)
+    w = rng.standard_normal(p.n)
+    ys, yt = inner_apply(rbf, p, w, 0), inner_apply(rbf, p, w, 1)
+    assert np.max(np.abs(ys - yt)) <= 1e-5 * np.max(np.abs(yt))
+    clump = np.ascontiguousarray(np.vstack([rng.uniform(0.0, 0.05, size=(300, 2)), xy[:500]]))
+    q = replace(p, xy=clump, f=np.zeros(clump.shape[0]))
+    ctx = rbf.Context(0)
+    rbf.rbf_bin(ctx.handle, dev(q.xy), q.n, rbf.RbfParams(q.sigma, q.cutoff, 0.0, 0))
+    y = torch.empty(q.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(rbf.RbfError) as e:
+        rbf.rbf_debug_inner_matvec(ctx.handle, 6.1, dev(rng.standard_normal(q.n)), y, 0)
+    assert e.value.status == 8
+    rbf.rbf_debug_inner_matvec(ctx.handle, 6.1, dev(rng.standard_normal(q.n)), y, 1)
+    ctx.close()
