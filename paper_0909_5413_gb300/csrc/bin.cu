@@ -724,6 +724,8 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
     int32_t cmax = 0;
     RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &cmax, st));
     G.sym = cmax <= 128;
+    // its slots are allocated here, outside the solver's graph capture
+    if (G.sym) RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
     // subdomain lists in inner positions
     if (ctx->rasm_ready) {
         int32_t tot[2] = {0, 0};

@@ -49,6 +49,8 @@ rbf_status ensure(rbf_ctx* ctx, DevArray<T>& a, size_t count)
 {
     if (count == 0) count = 1;
     if (a.p && a.count >= count) return RBF_OK;
+    if (ctx->capturing)   // a cudaMalloc would invalidate the solver's graph capture
+        return fail(ctx, RBF_ERR_STATE, "device allocation requested while the solver captures its cycle");
     release(ctx, a.p);
     a.p = nullptr;
     a.count = 0;

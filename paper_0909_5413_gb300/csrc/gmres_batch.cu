@@ -467,6 +467,7 @@ rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double*
         ctx->prof_step = -1;
         if (s != RBF_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
+            cudaGetLastError();   // a failed capture leaves its error behind for the next launch check
             if (s != RBF_OK) return s;
             return cuda_fail(ctx, e, "rbf_solve_batch: graph capture");
         }

@@ -666,7 +666,8 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y,
     if (nwork > 0 && ctx->inner_on && ctx->in.sym && ctx->sym_mode != 1) {
         // each neighbouring pair of inner cells once, then the fixed-order gather
         const int64_t n = ctx->n;
-        RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
+        if (ctx->sym_slots.count < (size_t)(5 * n))   // allocated with the inner grid (never inside a capture)
+            return fail(ctx, RBF_ERR_STATE, "symmetric FP32 matvec: slots not allocated");
         float* rowslot = ctx->sym_slots.p;
         float* colslot = rowslot + n;
         RBF_LAUNCH(ctx, k_matvec_f32_sym, blocks_for(nwork, kSymWarps), kSymWarps * 32, 0, st, P, nwork, w, rowslot,
