@@ -261,6 +261,26 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
+// Size class t (ceil(points / 32) == t) flags of the cells, and the scatter of
+// the flagged cells as (cell, 0) items.
+__global__ void k_flag_class(const int32_t* __restrict__ cell_start, int64_t ncell, int t, int32_t* __restrict__ flag)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int cnt = cell_start[c + 1] - cell_start[c];
+    flag[c] = (cnt > 0 && (cnt + 31) / 32 == t) ? 1 : 0;
+}
+
+__global__ void k_scatter_cells(int64_t ncell, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                int32_t* __restrict__ out)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell && flag[c]) {
+        out[2 * (int64_t)pos[c]] = (int32_t)c;
+        out[2 * (int64_t)pos[c] + 1] = 0;
+    }
+}
+
 // Points per cell.
 __global__ void k_cell_sizes(const int32_t* __restrict__ cell_start, int64_t ncell, int32_t* __restrict__ out)
 {
@@ -724,8 +744,26 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
     int32_t cmax = 0;
     RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &cmax, st));
     G.sym = cmax <= 128;
-    // its slots are allocated here, outside the solver's graph capture
-    if (G.sym) RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
+    if (G.sym) {
+        // its slots are allocated here, outside the solver's graph capture
+        RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
+        // its cell lists by size class (order kept within a class)
+        RBF_CHECK(ensure(ctx, G.symw, 2 * (size_t)std::max<int64_t>(ncell, 1)));
+        RBF_CHECK(ensure(ctx, G.tmp, std::max<int64_t>(2 * (ncell + 1), 2 * kNumSMs + 1)));
+        int32_t* flag = G.tmp.p;
+        int32_t* pos = G.tmp.p + (ncell + 1);
+        G.symoff[0] = 0;
+        for (int t = 1; t <= 4; ++t) {
+            RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, t, flag);
+            RBF_CHECK(exclusive_scan_i32(ctx, flag, pos, ncell, st));
+            RBF_LAUNCH(ctx, k_scatter_cells, blocks_for(ncell, 256), 256, 0, st, ncell, flag, pos,
+                       G.symw.p + 2 * G.symoff[t - 1]);
+            int32_t cnt = 0;
+            RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, pos + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            RBF_CUDA(ctx, cudaStreamSynchronize(st));
+            G.symoff[t] = G.symoff[t - 1] + cnt;
+        }
+    }
     // subdomain lists in inner positions
     if (ctx->rasm_ready) {
         int32_t tot[2] = {0, 0};
@@ -822,6 +860,27 @@ rbf_status count_pairs(rbf_ctx* ctx, int grid, int64_t* total, cudaStream_t st)
 
 namespace {
 
+// The items of `work` whose problem is active, in order, written to out (room for nwork items).
+rbf_status select_work_into(rbf_ctx* ctx, const int32_t* work, int64_t nwork, const int32_t* pid_cell,
+                            const int32_t* active, int32_t* out, int64_t* nout, cudaStream_t st)
+{
+    RBF_CHECK(ensure(ctx, ctx->al.flag, std::max<int64_t>(nwork, 1)));
+    RBF_CHECK(ensure(ctx, ctx->al.pos, std::max<int64_t>(nwork, 1) + 1));
+    if (nwork == 0) {
+        *nout = 0;
+        return RBF_OK;
+    }
+    RBF_LAUNCH(ctx, k_flag_work, blocks_for(nwork, 256), 256, 0, st, work, nwork, pid_cell, active, ctx->al.flag.p);
+    RBF_CHECK(exclusive_scan_i32(ctx, ctx->al.flag.p, ctx->al.pos.p, nwork, st));
+    RBF_LAUNCH(ctx, k_scatter_work, blocks_for(nwork, 256), 256, 0, st, work, nwork, ctx->al.flag.p, ctx->al.pos.p,
+               out);
+    int32_t cnt = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, ctx->al.pos.p + nwork, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    *nout = cnt;
+    return RBF_OK;
+}
+
 rbf_status select_work(rbf_ctx* ctx, const int32_t* work, int64_t nwork, const int32_t* pid_cell,
                        const int32_t* active, DevArray<int32_t>& out, int64_t* nout, cudaStream_t st)
 {
@@ -855,6 +914,17 @@ rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t 
     else
         RBF_CHECK(select_work(ctx, ctx->mv_work32.p, ctx->n_work32, ctx->pid_cell.p, active, ctx->al.w32,
                               &ctx->al.n32, st));
+    if (ctx->inner_on && ctx->in.sym) {   // the symmetric kernel's class lists, each filtered in order
+        const InnerGrid& G = ctx->in;
+        RBF_CHECK(ensure(ctx, ctx->al.symw, 2 * (size_t)std::max<int64_t>(G.symoff[4], 1)));
+        ctx->al.symoff[0] = 0;
+        for (int t = 1; t <= 4; ++t) {
+            int64_t got = 0;
+            RBF_CHECK(select_work_into(ctx, G.symw.p + 2 * G.symoff[t - 1], G.symoff[t] - G.symoff[t - 1],
+                                       G.pid_cell.p, active, ctx->al.symw.p + 2 * ctx->al.symoff[t - 1], &got, st));
+            ctx->al.symoff[t] = ctx->al.symoff[t - 1] + got;
+        }
+    }
     const int64_t nsub = ctx->nsub;
     RBF_CHECK(ensure(ctx, ctx->al.flag, std::max<int64_t>(nsub, 1)));
     RBF_CHECK(ensure(ctx, ctx->al.pos, std::max<int64_t>(nsub, 1) + 1));

@@ -78,6 +78,8 @@ struct Prob {
 struct InnerGrid {
     bool ready = false;
     bool sym = false;          // every cell holds at most 128 points: the symmetric FP32 kernel applies
+    rbf::DevArray<int32_t> symw;   // its (cell, 0) items, non-empty cells by size class ceil(points / 32)
+    int64_t symoff[5] = {0, 0, 0, 0, 0};   // class t holds items [symoff[t-1], symoff[t])
     double ri_sigmas = 0.0;
     int tile = 64;
     int stage_max = 0;
@@ -211,8 +213,9 @@ struct rbf_ctx {
     // the full lists, so every problem's sums run in the same order.
     struct ActiveLists {
         bool on = false;
-        rbf::DevArray<int32_t> w64, w32, sub, flag, pos;
+        rbf::DevArray<int32_t> w64, w32, sub, flag, pos, symw;
         int64_t n64 = 0, n32 = 0, nsub = 0;
+        int64_t symoff[5] = {0, 0, 0, 0, 0};
     } al;
 };
 

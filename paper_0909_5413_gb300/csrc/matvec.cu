@@ -373,7 +373,7 @@ struct SymWarp {
 template <int TPL, bool COL>
 __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx)[TPL], const float2 (&ty)[TPL],
                                          const float (&wt)[TPL], float2 (&acc)[TPL], float2 (&acc2)[TPL], int dn,
-                                         float* __restrict__ colout)
+                                         float* __restrict__ colout, float knorm)
 {
     const int dnp = (dn + 31) & ~31;
     for (int c0 = 0; c0 < dnp; c0 += 32) {
@@ -417,7 +417,7 @@ __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx
 #pragma unroll 8
             for (int r = 0; r < 32; ++r) sum += S.T[r * kSymTld + lane];
             __syncwarp();
-            if (c0 + lane < dn) colout[c0 + lane] = sum;
+            if (c0 + lane < dn) colout[c0 + lane] = sum * knorm;
         }
     }
 }
@@ -428,7 +428,7 @@ __device__ __forceinline__ void sym_cell(const MvParams& P, SymWarp& S, int lane
                                          float* __restrict__ colslot, int64_t n)
 {
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, cbase = (int)pr.cellbase;
-    const float ca = pr.ca;
+    const float ca = pr.ca, knorm = (float)pr.knorm;
     const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
     float2 tx[TPL], ty[TPL], acc[TPL], acc2[TPL];
     float wt[TPL];
@@ -442,6 +442,21 @@ __device__ __forceinline__ void sym_cell(const MvParams& P, SymWarp& S, int lane
         wt[t] = ok ? w[cb + q] : 0.f;
         acc[t] = make_float2(0.f, 0.f);
         acc2[t] = make_float2(0.f, 0.f);
+    }
+    // slots of the backward directions whose source cell is missing (off the
+    // grid or empty) get zeros, so that the gather is a plain fixed-order sum
+    {
+        const int bx[4] = {cx - 1, cx + 1, cx, cx - 1}, by[4] = {cy, cy - 1, cy - 1, cy - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bool missing = bx[q] < 0 || bx[q] >= ncx || by[q] < 0;
+            if (!missing) {
+                const int c = cbase + by[q] * ncx + bx[q];
+                missing = P.cell_start[c + 1] == P.cell_start[c];
+            }
+            if (missing)
+                for (int t = lane; t < cnt; t += 32) colslot[(int64_t)q * n + cb + t] = 0.f;
+        }
     }
 #pragma unroll 1
     for (int pass = 0; pass < 5; ++pass) {
@@ -466,65 +481,47 @@ __device__ __forceinline__ void sym_cell(const MvParams& P, SymWarp& S, int lane
             }
         }
         __syncwarp();
-        if (pass == 0) sym_pass<TPL, false>(S, lane, tx, ty, wt, acc, acc2, dn, nullptr);
-        else sym_pass<TPL, true>(S, lane, tx, ty, wt, acc, acc2, dn, colslot + (int64_t)(pass - 1) * n + db);
+        if (pass == 0) sym_pass<TPL, false>(S, lane, tx, ty, wt, acc, acc2, dn, nullptr, knorm);
+        else sym_pass<TPL, true>(S, lane, tx, ty, wt, acc, acc2, dn, colslot + (int64_t)(pass - 1) * n + db, knorm);
         __syncwarp();
     }
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
         const int q = lane + 32 * t;
-        if (q < cnt) rowslot[cb + q] = (acc[t].x + acc[t].y) + (acc2[t].x + acc2[t].y);
+        if (q < cnt) rowslot[cb + q] = ((acc[t].x + acc[t].y) + (acc2[t].x + acc2[t].y)) * knorm;
     }
 }
 
-// One warp per cell: the cell's first work item (a cell of more points than
-// the work tile has further items, which return).
-__global__ void __launch_bounds__(kSymWarps * 32)
-    k_matvec_f32_sym(MvParams P, int64_t nwork, const float* __restrict__ w, float* __restrict__ rowslot,
-                     float* __restrict__ colslot, int64_t n)
+// One warp per cell of one size class (TPL targets per lane, 32 (TPL - 1) <
+// points <= 32 TPL): the list holds (cell, 0) items of that class, and each
+// class has a kernel of its own register budget.
+template <int TPL>
+__global__ void __launch_bounds__(kSymWarps * 32, TPL == 1 ? 6 : (TPL == 2 ? 5 : 4))
+    k_matvec_f32_sym(MvParams P, const int32_t* __restrict__ cells, int64_t ncells, const float* __restrict__ w,
+                     float* __restrict__ rowslot, float* __restrict__ colslot, int64_t n)
 {
     __shared__ __align__(16) SymWarp sm_all[kSymWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kSymWarps + warp;
-    if (item >= nwork) return;
-    const int cell = P.work[2 * item], first = P.work[2 * item + 1];
-    if (first != 0) return;
+    if (item >= ncells) return;
+    const int cell = cells[2 * item];
     const int pcell = P.pid_cell[cell];
     if (P.active && !P.active[pcell]) return;
     const Prob& pr = P.prob[pcell];
     const int cb = P.cell_start[cell], cnt = P.cell_start[cell + 1] - cb;
-    SymWarp& S = sm_all[warp];
-    switch ((cnt + 31) >> 5) {   // warp-uniform; the binning guarantees cnt <= kSymMaxCell
-    case 1: sym_cell<1>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
-    case 2: sym_cell<2>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
-    case 3: sym_cell<3>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
-    default: sym_cell<4>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n); break;
-    }
+    sym_cell<TPL>(P, sm_all[warp], lane, cell, cb, cnt, pr, w, rowslot, colslot, n);
 }
 
-// y_p = row slot + the column slots of p's backward neighbours C = cell(p) - d
-// that exist and hold points, in the order of d, times the normalisation.
+// y_p = row slot + the four column slots in the order of d (a missing
+// backward neighbour's slot holds zero); the slots already carry the
+// normalisation. Points of masked problems are left alone.
 __global__ void k_sym_gather(const float* __restrict__ rowslot, const float* __restrict__ colslot, int64_t n,
-                             const int32_t* __restrict__ cell_s, const int32_t* __restrict__ cell_start,
-                             const Prob* __restrict__ prob, const int32_t* __restrict__ pid,
-                             const int32_t* __restrict__ active, float* __restrict__ y)
+                             const int32_t* __restrict__ pid, const int32_t* __restrict__ active, float* __restrict__ y)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int pb = pid[p];
-    if (active && !active[pb]) return;
-    const Prob& pr = prob[pb];
-    const int ncx = (int)pr.ncx, cbase = (int)pr.cellbase;
-    const int lc = cell_s[p] - cbase, cx = lc % ncx, cy = lc / ncx;
-    float s = rowslot[p];
-    const int bx[4] = {cx - 1, cx + 1, cx, cx - 1}, by[4] = {cy, cy - 1, cy - 1, cy - 1};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (bx[q] < 0 || bx[q] >= ncx || by[q] < 0) continue;
-        const int c = cbase + by[q] * ncx + bx[q];
-        if (cell_start[c + 1] > cell_start[c]) s += colslot[(int64_t)q * n + p];
-    }
-    y[p] = s * (float)pr.knorm;
+    if (active && !active[pid[p]]) return;
+    y[p] = (((rowslot[p] + colslot[p]) + colslot[n + p]) + colslot[2 * n + p]) + colslot[3 * n + p];
 }
 
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
@@ -670,10 +667,22 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y,
             return fail(ctx, RBF_ERR_STATE, "symmetric FP32 matvec: slots not allocated");
         float* rowslot = ctx->sym_slots.p;
         float* colslot = rowslot + n;
-        RBF_LAUNCH(ctx, k_matvec_f32_sym, blocks_for(nwork, kSymWarps), kSymWarps * 32, 0, st, P, nwork, w, rowslot,
-                   colslot, n);
-        RBF_LAUNCH(ctx, k_sym_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, P.cell_s, P.cell_start,
-                   P.prob, ctx->pid.p, P.active, y);
+        const InnerGrid& G = ctx->in;
+        const int32_t* lists = ctx->al.on ? ctx->al.symw.p : G.symw.p;
+        const int64_t* off = ctx->al.on ? ctx->al.symoff : G.symoff;
+        for (int t = 1; t <= 4; ++t) {
+            const int64_t cnt = off[t] - off[t - 1];
+            if (cnt == 0) continue;
+            const int32_t* cl = lists + 2 * off[t - 1];
+            const unsigned nb = blocks_for(cnt, kSymWarps);
+            switch (t) {
+            case 1: RBF_LAUNCH(ctx, k_matvec_f32_sym<1>, nb, kSymWarps * 32, 0, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            case 2: RBF_LAUNCH(ctx, k_matvec_f32_sym<2>, nb, kSymWarps * 32, 0, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            case 3: RBF_LAUNCH(ctx, k_matvec_f32_sym<3>, nb, kSymWarps * 32, 0, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            default: RBF_LAUNCH(ctx, k_matvec_f32_sym<4>, nb, kSymWarps * 32, 0, st, P, cl, cnt, w, rowslot, colslot, n);
+            }
+        }
+        RBF_LAUNCH(ctx, k_sym_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active, y);
     } else if (nwork > 0) {
         switch (tile) {
         case 32: RBF_CHECK(launch_f32<32>(ctx, P, nwork, w, y, st)); break;
