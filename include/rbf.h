@@ -403,6 +403,30 @@ const char* rbf_last_error(rbf_ctx* ctx);
 uint64_t rbf_launch_count(rbf_ctx* ctx);
 /* Device bytes the context currently holds. */
 int64_t rbf_device_bytes(rbf_ctx* ctx);
+/* Context options (no counterpart in the paper). */
+enum {
+    /* 1 (default): a batched mixed solve on the inner grid runs each Arnoldi
+     * step as one persistent cooperative launch (apply, matvec, Gram-Schmidt,
+     * Arnoldi column and scaling for every running problem, with grid-wide
+     * barriers between the phases; the results are bit for bit those of the
+     * separate kernels); 0: separate kernels. Not used while a kernel class
+     * of the cycle is being profiled, nor for a single problem. */
+    RBF_OPT_FUSED_STEP = 1,
+    /* 1 (default): the inner FP32 matvec of the mixed form visits each pair of
+     * neighbouring cells once (cells of at most 128 points); 0: every target
+     * against its 3 x 3 cells. */
+    RBF_OPT_SYMMETRIC_F32 = 2,
+    /* Polls of a grid-barrier wait of the fused step before it gives up: the
+     * step then ends, and the solve returns RBF_ERR_TIMEOUT (value >= 1;
+     * default 2^23, about a second). */
+    RBF_OPT_BARRIER_SPIN_LIMIT = 3,
+    /* Check of the timeout path: 1 makes every barrier of the fused step wait
+     * for one block more than the grid has, so that every wait runs out. */
+    RBF_OPT_BARRIER_EXTRA_BLOCK = 4
+};
+/* Set a context option. INVALID_ARG for an unknown option or value. */
+rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value);
+
 /* Cap on the device bytes the context may hold (0 = no cap, the default): an
  * allocation that would take rbf_device_bytes() above it fails with
  * RBF_ERR_OOM before cudaMalloc is called, as a real shortage would. For a

@@ -276,6 +276,33 @@ uint64_t rbf_launch_count(rbf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int64_t rbf_device_bytes(rbf_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
 
+rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
+{
+    if (!ctx) return RBF_ERR_INVALID_ARG;
+    switch (option) {
+    case RBF_OPT_FUSED_STEP:
+        if (value != 0 && value != 1) break;
+        ctx->fused_mode = (int)value;
+        return RBF_OK;
+    case RBF_OPT_SYMMETRIC_F32:
+        if (value != 0 && value != 1) break;
+        ctx->sym_mode = value ? 0 : 1;
+        return RBF_OK;
+    case RBF_OPT_BARRIER_SPIN_LIMIT:
+        if (value < 1) break;
+        ctx->fused_spin_limit = (unsigned long long)value;
+        return RBF_OK;
+    case RBF_OPT_BARRIER_EXTRA_BLOCK:
+        if (value != 0 && value != 1) break;
+        ctx->fused_extra_block = (int)value;
+        return RBF_OK;
+    default:
+        return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_option: unknown option %d", option);
+    }
+    return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_option: value %lld out of range for option %d", (long long)value,
+                option);
+}
+
 rbf_status rbf_set_memory_limit(rbf_ctx* ctx, int64_t bytes)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;

@@ -204,6 +204,13 @@ struct rbf_ctx {
     cudaGraphExec_t bgraph = nullptr;       // captured Arnoldi cycle of the batched solver
     uint64_t bgraph_launches = 0;           // kernels in that graph
     bool capturing = false;                 // launches are being captured into bgraph
+    // fused Arnoldi step of the batched mixed solver (fused.cu)
+    int fused_mode = 1;                     // 1: one persistent launch per step where it applies; 0: separate kernels
+    unsigned int fused_grid = 0;            // its resident grid (computed on first use)
+    unsigned long long fused_spin_limit = 1ull << 23;   // polls of a barrier wait before it gives up
+    int fused_extra_block = 0;              // check of the timeout path: barriers wait for one block too many
+    bool bgraph_off = false;                // this solve launches its cycles directly (no capture)
+    rbf::DevArray<int> fused_sync;          // barrier state (4 ints), then the solve's status word
     int prof_step = -1;                     // Arnoldi step of the launches being issued (-1: none)
     unsigned bgraph_prof_mask = 0;          // profiler classes the captured graph records
     std::vector<rbf_graph_prof> bgraph_prof;   // its event pairs
@@ -328,6 +335,12 @@ rbf_status rasm_factor_tc(rbf_ctx* ctx, int32_t* fb_list, unsigned int* fb_count
 // ---- gmres.cu
 rbf_status gmres_solve(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,
                        rbf_solve_info* info, cudaStream_t st);
+
+// ---- fused.cu: one persistent launch per Arnoldi step (batched mixed solve, inner grid)
+struct Chunks;
+bool fused_step_applies(rbf_ctx* ctx);
+rbf_status fused_step(rbf_ctx* ctx, float* V, int64_t ldv, int j, float* u, const Chunks& C, GmresDev* gm, int nprob,
+                      int32_t* run, double* partial, cudaStream_t st);
 
 // ---- gmres_batch.cu
 rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f_sorted, double* w_sorted, const rbf_solve_params* p,

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "ortho.cuh"
+#include "batch.cuh"
 #include "vecops.cuh"
 
 namespace rbf {
@@ -32,28 +33,6 @@ namespace {
 
 constexpr int kBPer = kOrthoPer;       // elements per thread (the single solver's chunking)
 constexpr int kBChunk = kOrthoChunk;   // elements per chunk
-
-enum BField { F_H1 = 0, F_H2 = 1, F_NRM2 = 2, F_BETA2 = 3, F_FNORM2 = 4 };
-
-
-__device__ __forceinline__ double* field_ptr(GmresDev& g, int field)
-{
-    switch (field) {
-    case F_H1: return g.h1;
-    case F_H2: return g.h2;
-    case F_NRM2: return &g.nrm2;
-    case F_BETA2: return &g.beta2;
-    default: return &g.fnorm2;
-    }
-}
-
-struct Chunks {
-    const int32_t* beg;   // first element of chunk
-    const int32_t* end;   // one past the last
-    const int32_t* pid;   // problem of the chunk
-    const int32_t* cptr;  // chunks of problem b: [cptr[b], cptr[b+1])
-    int64_t nc;
-};
 
 // The Gram-Schmidt vector passes over one chunk (the single solver's per-chunk code;
 // a chunk never spans two problems). Chunks of masked problems write zeros.
@@ -139,21 +118,7 @@ __global__ void k_breduce(const double* __restrict__ partial, Chunks C, int npro
     const int pb = blockIdx.x;
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (pb >= nprob || k >= nv || !active[pb]) return;
-    double a = 0.0;
-    constexpr int U = 8;   // loads issued together, added in order
-    const int c1 = C.cptr[pb + 1];
-    for (int c0 = C.cptr[pb] + lane; c0 < c1; c0 += 32 * U) {
-        double p[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = c0 + 32 * u;
-            p[u] = c < c1 ? partial[(int64_t)c * 32 + k] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (c0 + 32 * u < c1) a += p[u];
-    }
-    for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+    const double a = breduce_one(partial, C, pb, k, lane);
     if (lane == 0) field_ptr(gm[pb], field)[k] = a;
 }
 
@@ -359,6 +324,7 @@ struct BatchWork {
     const int32_t* active;   // problems of this cycle
     int32_t* run;            // problems still stepping in this cycle (the Arnoldi kernels' mask)
     double* partial;
+    bool fused;              // FP32 cycle: one persistent launch per Arnoldi step (fused.cu)
     const int32_t* pid;
     int64_t n;
 
@@ -414,7 +380,13 @@ rbf_status batch_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, doubl
     cudaStream_t st = B.st;
     const int64_t n = B.n;
     const unsigned pb_blocks = blocks_for(B.nprob, 128);
-    for (int j = 0; j < m; ++j) {
+    if constexpr (sizeof(T) == 4) {
+        if (B.fused) {   // one persistent launch per Arnoldi step
+            for (int j = 0; j < m; ++j)
+                RBF_CHECK(fused_step(ctx, V, ldv, j, u, B.C, B.gm, B.nprob, B.run, B.partial, st));
+        }
+    }
+    for (int j = 0; j < m && !B.fused; ++j) {
         T* vj = V + (int64_t)j * ldv;
         T* vn = V + (int64_t)(j + 1) * ldv;
         // the operators of the step skip the problems that have stopped in this cycle
@@ -455,6 +427,7 @@ rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double*
     // the profiler's state takes a new capture
     const unsigned pmask = ctx->prof ? ctx->prof_mask : 0u;
     if (ctx->bgraph && pmask != ctx->bgraph_prof_mask) batch_graph_reset(ctx);
+    if (ctx->bgraph_off) return batch_cycle<T>(B, V, ldv, m, u, t, w);   // launched directly (see below)
     if (!ctx->bgraph) {
         const uint64_t l0 = ctx->launches;
         ctx->capturing = true;
@@ -468,6 +441,12 @@ rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double*
         if (s != RBF_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();   // a failed capture leaves its error behind for the next launch check
+            if (B.fused) {
+                // a runtime that cannot capture the cooperative launch: the fused
+                // cycle is launched directly for the rest of the solve
+                ctx->bgraph_off = true;
+                return batch_cycle<T>(B, V, ldv, m, u, t, w);
+            }
             if (s != RBF_OK) return s;
             return cuda_fail(ctx, e, "rbf_solve_batch: graph capture");
         }
@@ -570,7 +549,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
     RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
 
-    BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, ctx->pid.p, n};
+    BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, false, ctx->pid.p, n};
     // |f_b|^2
     RBF_CHECK((B.mdot<0, double>(f, 0, 1, const_cast<double*>(f), -1, F_FNORM2, active)));
     std::vector<double> stat(4 * (size_t)nprob);
@@ -630,6 +609,19 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     int compact_at = nprob / 2, compactions = 0;
     ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
     batch_graph_reset(ctx);      // buffers may have moved since the last solve
+    ctx->bgraph_off = false;
+    // the fused Arnoldi step: batches of the mixed form on the symmetric inner
+    // matvec, unless a kernel class of the cycle is being profiled
+    {
+        constexpr unsigned kCycleClasses = (1u << RBF_PROF_MATVEC_F64) | (1u << RBF_PROF_MATVEC_F32) |
+                                           (1u << RBF_PROF_RASM_APPLY) | (1u << RBF_PROF_ORTHO);
+        const bool profiling = ctx->prof && (ctx->prof_mask & kCycleClasses);
+        B.fused = mixed && nprob > 1 && !profiling && fused_step_applies(ctx);
+        if (B.fused) {
+            RBF_CHECK(ensure(ctx, ctx->fused_sync, 8));
+            RBF_CUDA(ctx, cudaMemsetAsync(ctx->fused_sync.p, 0, 8 * sizeof(int), st));
+        }
+    }
     // a zero initial guess (every problem) gives r0 = f without a product
     RBF_CHECK(ensure(ctx, ctx->flag_dev, 1));
     RBF_CUDA(ctx, cudaMemsetAsync(ctx->flag_dev.p, 0, sizeof(int), st));
@@ -705,7 +697,14 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
                        ctx->inner_on ? (const int32_t*)ctx->in.perm.p : nullptr, Vf);
             RBF_CHECK(run_cycle<float>(B, Vf, ldv, m, uf, tf, w));
         }
+        int fused_status = 0;
+        if (B.fused)
+            RBF_CUDA(ctx, cudaMemcpyAsync(&fused_status, ctx->fused_sync.p + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                                          st));
         RBF_CHECK(read_stat());
+        if (fused_status != 0)
+            return fail(ctx, (rbf_status)fused_status,
+                        "rbf_solve_batch: a grid barrier of the fused Arnoldi step gave up waiting");
         if (!ctx->bgraph_prof.empty()) {
             int steps_run = 0;
             for (int b = 0; b < nprob; ++b)

@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "matvec_sym.cuh"
 
 namespace rbf {
 namespace {
@@ -31,23 +32,6 @@ constexpr int kMvStage = 1152;                 // FP64: sources staged per pass 
 constexpr int kMv32StageMax = 1536;            // FP32: the same
 constexpr int kMvMaxRows = 129;                // 2k + 1 with k <= 64
 
-struct MvParams {
-    const double* xy;          // cell-ordered source coordinates (x, y)
-    const float* loc;          // FP32 scaled offsets from the point's cell corner (x, y)
-    const int32_t* cell_s;     // global cell id of each cell-ordered point
-    const int32_t* cell_start;
-    const int32_t* work;       // (cell, first target) per block
-    // targets (the sources themselves for A~ w; other points for s(x))
-    const double* txy;
-    const float* tloc;
-    const int32_t* tcell_start;
-    const unsigned long long* fxtab;   // T1, T2 of fixexp.cuh
-    const Prob* prob;          // per-problem grid and kernel constants
-    const int32_t* pid_cell;   // problem of each cell
-    const int32_t* active;     // per-problem mask (null: every problem)
-    int stage;                 // sources staged per pass (a multiple of 32)
-};
-
 // Stage size for the largest stencil of a binning: rounded up to 32, capped.
 inline int round_stage(int stage_max, int cap)
 {
@@ -56,36 +40,6 @@ inline int round_stage(int stage_max, int cap)
 }
 
 inline int stage_for(const rbf_ctx* ctx, int cap) { return round_stage(ctx->stage_max, cap); }
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Packed FP32 pairs (two lanes of work per instruction on sm_100-class SMs).
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
-    return *reinterpret_cast<float2*>(&d);
-}
-
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
-    return *reinterpret_cast<float2*>(&d);
-}
-
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c)
-{
-    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b),
-                          Cc = *reinterpret_cast<unsigned long long*>(&c);
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(A), "l"(B), "l"(Cc));
-    return *reinterpret_cast<float2*>(&d);
-}
 
 // Dynamic shared memory of the FP64 kernel for tile T and stage S: tables, staged
 // FP64 and fixed-point coordinates, weights, partial sums, FP32 offsets, masks.
@@ -347,151 +301,6 @@ __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __r
     if (active) y[p] = ((acc2.x + acc2.y) + (acc2b.x + acc2b.y)) * knorm;
 }
 
-// Symmetric FP32 matvec on the inner grid: every unordered pair of
-// neighbouring cells is visited once. One warp per cell C (at most
-// kSymMaxCell points, up to four targets per lane) takes C itself (row sums
-// only: all pairs inside C) and its four forward neighbours D = C + d,
-// d in {(1,0), (-1,1), (0,1), (1,1)}: each kernel value k_ij (i in C, j in D)
-// feeds the row sum of i (registers) and the column sum of j, which is
-// reduced over the warp's targets through a shared transpose (lane j adds the
-// 32 rows in order) and written to point j's slot for direction d. The
-// gather then adds, per point, its row slot and the column slots of its
-// existing backward neighbours in a fixed order: deterministic, with half
-// the exp2 evaluations of the stencil sweep. Sources are staged as FP32
-// offsets from C's corner (scaled so that the kernel is exp2(-|dX|^2)), in
-// chunks of 32 padded with far, zero-weight sources.
-constexpr int kSymWarps = 4;
-constexpr int kSymMaxCell = 128;
-constexpr int kSymStage = kSymMaxCell + 32;
-constexpr int kSymTld = 36;   // row stride of the transpose buffer (16-byte rows, conflict-free columns)
-
-struct SymWarp {
-    float sx[kSymStage], sy[kSymStage], sw[kSymStage];
-    float T[32 * kSymTld];
-};
-
-template <int TPL, bool COL>
-__device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx)[TPL], const float2 (&ty)[TPL],
-                                         const float (&wt)[TPL], float2 (&acc)[TPL], float2 (&acc2)[TPL], int dn,
-                                         float* __restrict__ colout, float knorm)
-{
-    const int dnp = (dn + 31) & ~31;
-    for (int c0 = 0; c0 < dnp; c0 += 32) {
-        float col[32];
-        if (COL) {
-#pragma unroll
-            for (int s = 0; s < 32; ++s) col[s] = 0.f;
-        }
-#pragma unroll
-        for (int s = 0; s < 32; s += 4) {
-            const float4 X = *reinterpret_cast<const float4*>(&S.sx[c0 + s]);
-            const float4 Y = *reinterpret_cast<const float4*>(&S.sy[c0 + s]);
-            const float4 Wv = *reinterpret_cast<const float4*>(&S.sw[c0 + s]);
-#pragma unroll
-            for (int t = 0; t < TPL; ++t) {
-                const float2 dx0 = f2_sub(tx[t], make_float2(X.x, X.y)), dy0 = f2_sub(ty[t], make_float2(Y.x, Y.y));
-                const float2 dx1 = f2_sub(tx[t], make_float2(X.z, X.w)), dy1 = f2_sub(ty[t], make_float2(Y.z, Y.w));
-                const float2 r0 = f2_fma(dy0, dy0, f2_mul(dx0, dx0));
-                const float2 r1 = f2_fma(dy1, dy1, f2_mul(dx1, dx1));
-                const float2 e0 = make_float2(ex2_approx(-r0.x), ex2_approx(-r0.y));
-                const float2 e1 = make_float2(ex2_approx(-r1.x), ex2_approx(-r1.y));
-                acc[t] = f2_fma(e0, make_float2(Wv.x, Wv.y), acc[t]);
-                acc2[t] = f2_fma(e1, make_float2(Wv.z, Wv.w), acc2[t]);
-                if (COL) {
-                    const float2 w2 = make_float2(wt[t], wt[t]);
-                    const float2 c01 = f2_fma(e0, w2, make_float2(col[s], col[s + 1]));
-                    const float2 c23 = f2_fma(e1, w2, make_float2(col[s + 2], col[s + 3]));
-                    col[s] = c01.x;
-                    col[s + 1] = c01.y;
-                    col[s + 2] = c23.x;
-                    col[s + 3] = c23.y;
-                }
-            }
-        }
-        if (COL) {
-            float4* row = reinterpret_cast<float4*>(&S.T[lane * kSymTld]);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) row[k] = make_float4(col[4 * k], col[4 * k + 1], col[4 * k + 2], col[4 * k + 3]);
-            __syncwarp();
-            float sum = 0.f;
-#pragma unroll 8
-            for (int r = 0; r < 32; ++r) sum += S.T[r * kSymTld + lane];
-            __syncwarp();
-            if (c0 + lane < dn) colout[c0 + lane] = sum * knorm;
-        }
-    }
-}
-
-template <int TPL>
-__device__ __forceinline__ void sym_cell(const MvParams& P, SymWarp& S, int lane, int cell, int cb, int cnt,
-                                         const Prob& pr, const float* __restrict__ w, float* __restrict__ rowslot,
-                                         float* __restrict__ colslot, int64_t n)
-{
-    const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, cbase = (int)pr.cellbase;
-    const float ca = pr.ca, knorm = (float)pr.knorm;
-    const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
-    float2 tx[TPL], ty[TPL], acc[TPL], acc2[TPL];
-    float wt[TPL];
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) {
-        const int q = lane + 32 * t;
-        const bool ok = q < cnt;
-        const float2 l = ok ? reinterpret_cast<const float2*>(P.loc)[cb + q] : make_float2(-1.0e4f, -1.0e4f);
-        tx[t] = make_float2(l.x, l.x);
-        ty[t] = make_float2(l.y, l.y);
-        wt[t] = ok ? w[cb + q] : 0.f;
-        acc[t] = make_float2(0.f, 0.f);
-        acc2[t] = make_float2(0.f, 0.f);
-    }
-    // slots of the backward directions whose source cell is missing (off the
-    // grid or empty) get zeros, so that the gather is a plain fixed-order sum
-    {
-        const int bx[4] = {cx - 1, cx + 1, cx, cx - 1}, by[4] = {cy, cy - 1, cy - 1, cy - 1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            bool missing = bx[q] < 0 || bx[q] >= ncx || by[q] < 0;
-            if (!missing) {
-                const int c = cbase + by[q] * ncx + bx[q];
-                missing = P.cell_start[c + 1] == P.cell_start[c];
-            }
-            if (missing)
-                for (int t = lane; t < cnt; t += 32) colslot[(int64_t)q * n + cb + t] = 0.f;
-        }
-    }
-#pragma unroll 1
-    for (int pass = 0; pass < 5; ++pass) {
-        const int dx = (pass == 1 || pass == 4) ? 1 : (pass == 2 ? -1 : 0);
-        const int dy = pass >= 2 ? 1 : 0;
-        const int nx = cx + dx, ny = cy + dy;
-        if (nx < 0 || nx >= ncx || ny >= ncy) continue;
-        const int dcell = cbase + ny * ncx + nx;
-        const int db = P.cell_start[dcell], dn = P.cell_start[dcell + 1] - db;
-        if (dn == 0) continue;
-        const int dnp = (dn + 31) & ~31;
-        for (int s = lane; s < dnp; s += 32) {
-            if (s < dn) {
-                const float2 l = reinterpret_cast<const float2*>(P.loc)[db + s];
-                S.sx[s] = l.x + (float)dx * ca;
-                S.sy[s] = l.y + (float)dy * ca;
-                S.sw[s] = w[db + s];
-            } else {
-                S.sx[s] = 1.0e4f;
-                S.sy[s] = 1.0e4f;
-                S.sw[s] = 0.f;
-            }
-        }
-        __syncwarp();
-        if (pass == 0) sym_pass<TPL, false>(S, lane, tx, ty, wt, acc, acc2, dn, nullptr, knorm);
-        else sym_pass<TPL, true>(S, lane, tx, ty, wt, acc, acc2, dn, colslot + (int64_t)(pass - 1) * n + db, knorm);
-        __syncwarp();
-    }
-#pragma unroll
-    for (int t = 0; t < TPL; ++t) {
-        const int q = lane + 32 * t;
-        if (q < cnt) rowslot[cb + q] = ((acc[t].x + acc[t].y) + (acc2[t].x + acc2[t].y)) * knorm;
-    }
-}
-
 // One warp per cell of one size class (TPL targets per lane, 32 (TPL - 1) <
 // points <= 32 TPL): the list holds (cell, 0) items of that class, and each
 // class has a kernel of its own register budget.
@@ -592,6 +401,21 @@ rbf_status launch_f32(rbf_ctx* ctx, MvParams P, int64_t nwork, const float* w, f
 }
 
 }  // namespace
+
+bool inner_sym_params(rbf_ctx* ctx, MvParams* P, const int32_t** cells, int64_t* ncells)
+{
+    if (!ctx->inner_on || !ctx->in.sym || ctx->sym_mode == 1) return false;
+    const InnerGrid& G = ctx->in;
+    *P = mv_params(ctx);
+    P->loc = G.loc.p;
+    P->cell_s = G.cell_s.p;
+    P->cell_start = G.cell_start.p;
+    P->prob = G.prob.p;
+    P->pid_cell = G.pid_cell.p;
+    *cells = ctx->al.on ? ctx->al.symw.p : G.symw.p;
+    *ncells = ctx->al.on ? ctx->al.symoff[4] : G.symoff[4];
+    return true;
+}
 
 rbf_status matvec_prepare(rbf_ctx* ctx)
 {

@@ -262,9 +262,11 @@ constexpr int gs_passes()
 // earlier Givens rotations applied to it, the new rotation, the rotated
 // right-hand side g and the residual estimate |g_{j+1}| / |f|. The rotation
 // chain runs in lane 0 on shared copies (one block per problem).
-__device__ __forceinline__ void arnoldi_column(GmresDev* __restrict__ g, int j, int passes)
+// The same with the warp's shared scratch passed in (hc: kMaxRestart + 1
+// entries, cs and sn: kMaxRestart), for several warps of a block at once.
+__device__ __forceinline__ void arnoldi_column_s(GmresDev* __restrict__ g, int j, int passes, double* hc, double* cs,
+                                                 double* sn)
 {
-    __shared__ double hc[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart];
     const int lane = threadIdx.x & 31;
     const int M = kMaxRestart;
     for (int q = lane; q <= j; q += 32) hc[q] = passes == 2 ? g->h1[q] + g->h2[q] : g->h1[q];
@@ -299,6 +301,12 @@ __device__ __forceinline__ void arnoldi_column(GmresDev* __restrict__ g, int j, 
     }
     __syncwarp();
     for (int q = lane; q <= j + 1; q += 32) g->H[q * M + j] = hc[q];
+}
+
+__device__ __forceinline__ void arnoldi_column(GmresDev* __restrict__ g, int j, int passes)
+{
+    __shared__ double hc[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart];
+    arnoldi_column_s(g, j, passes, hc, cs, sn);
 }
 
 // Load-batch width per precision (registers: G x kOrthoPer values of T).

@@ -32,7 +32,9 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
             "rbf_count_candidates", "rbf_profile_classes", "rbf_set_memory_limit",
             "rbf_count_pairs", "rbf_rasm_factor_counts",
-            "rbf_debug_inner_matvec"]
+            "rbf_debug_inner_matvec", "rbf_set_option"]
+
+RBF_OPT_FUSED_STEP, RBF_OPT_SYMMETRIC_F32, RBF_OPT_BARRIER_SPIN_LIMIT, RBF_OPT_BARRIER_EXTRA_BLOCK = 1, 2, 3, 4
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)
@@ -133,6 +135,7 @@ def load(path: str | None = None):
     L.rbf_device_bytes.argtypes = [P]
     L.rbf_device_bytes.restype = C.c_int64
     L.rbf_set_memory_limit.argtypes = [P, C.c_int64]
+    L.rbf_set_option.argtypes = [P, C.c_int, C.c_int64]
     L.rbf_profile_enable.argtypes = [P, C.c_int]
     L.rbf_profile_read.argtypes = [P, C.c_int, I64, D]
     L.rbf_debug_exp.argtypes = [P, P, P, C.c_int64, C.c_int, P]
@@ -338,6 +341,10 @@ def rbf_launch_count(ctx) -> int:
 
 def rbf_device_bytes(ctx) -> int:
     return int(load().rbf_device_bytes(ctx))
+
+
+def rbf_set_option(ctx, option: int, value: int) -> None:
+    _check(ctx, load().rbf_set_option(ctx, int(option), int(value)))
 
 
 def rbf_set_memory_limit(ctx, nbytes: int) -> None:
