@@ -405,12 +405,14 @@ uint64_t rbf_launch_count(rbf_ctx* ctx);
 int64_t rbf_device_bytes(rbf_ctx* ctx);
 /* Context options (no counterpart in the paper). */
 enum {
-    /* 1 (default): a batched mixed solve on the inner grid runs each Arnoldi
+    /* The fused Arnoldi step of a batched mixed solve on the inner grid: each
      * step as one persistent cooperative launch (apply, matvec, Gram-Schmidt,
      * Arnoldi column and scaling for every running problem, with grid-wide
      * barriers between the phases; the results are bit for bit those of the
-     * separate kernels); 0: separate kernels. Not used while a kernel class
-     * of the cycle is being profiled, nor for a single problem. */
+     * separate kernels). 0: never (separate kernels); 1: always; 2 (default):
+     * once at most 64 problems are still active, where the separate kernels'
+     * launches dominate the step. Not used while a kernel class of the cycle
+     * is being profiled, nor for a single problem. */
     RBF_OPT_FUSED_STEP = 1,
     /* 1 (default): the inner FP32 matvec of the mixed form visits each pair of
      * neighbouring cells once (cells of at most 128 points); 0: every target

@@ -281,7 +281,7 @@ rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
     if (!ctx) return RBF_ERR_INVALID_ARG;
     switch (option) {
     case RBF_OPT_FUSED_STEP:
-        if (value != 0 && value != 1) break;
+        if (value < 0 || value > 2) break;
         ctx->fused_mode = (int)value;
         return RBF_OK;
     case RBF_OPT_SYMMETRIC_F32:

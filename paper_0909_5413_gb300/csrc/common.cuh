@@ -205,7 +205,7 @@ struct rbf_ctx {
     uint64_t bgraph_launches = 0;           // kernels in that graph
     bool capturing = false;                 // launches are being captured into bgraph
     // fused Arnoldi step of the batched mixed solver (fused.cu)
-    int fused_mode = 1;                     // 1: one persistent launch per step where it applies; 0: separate kernels
+    int fused_mode = 2;                     // fused Arnoldi step: 0 never, 1 always, 2 once few problems are active
     unsigned int fused_grid = 0;            // its resident grid (computed on first use)
     unsigned long long fused_spin_limit = 1ull << 23;   // polls of a barrier wait before it gives up
     int fused_extra_block = 0;              // check of the timeout path: barriers wait for one block too many

@@ -31,6 +31,12 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2* loc, const float* w, float
 
 namespace {
 
+// Active problems from which the adaptive mode (RBF_OPT_FUSED_STEP = 2) runs
+// the fused Arnoldi step: in the tail of a batch the separate kernels are
+// short and their launches dominate; with many problems active they keep
+// more warps resident than the persistent kernel and are faster.
+constexpr int kFusedTail = 64;
+
 constexpr int kBPer = kOrthoPer;       // elements per thread (the single solver's chunking)
 constexpr int kBChunk = kOrthoChunk;   // elements per chunk
 
@@ -610,17 +616,19 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     ctx->active_mask = active;   // converged problems are skipped by the matvec and the apply
     batch_graph_reset(ctx);      // buffers may have moved since the last solve
     ctx->bgraph_off = false;
+    bool fused_ok = false;
     // the fused Arnoldi step: batches of the mixed form on the symmetric inner
     // matvec, unless a kernel class of the cycle is being profiled
     {
         constexpr unsigned kCycleClasses = (1u << RBF_PROF_MATVEC_F64) | (1u << RBF_PROF_MATVEC_F32) |
                                            (1u << RBF_PROF_RASM_APPLY) | (1u << RBF_PROF_ORTHO);
         const bool profiling = ctx->prof && (ctx->prof_mask & kCycleClasses);
-        B.fused = mixed && nprob > 1 && !profiling && fused_step_applies(ctx);
-        if (B.fused) {
+        fused_ok = mixed && nprob > 1 && !profiling && fused_step_applies(ctx);
+        if (fused_ok) {
             RBF_CHECK(ensure(ctx, ctx->fused_sync, 8));
             RBF_CUDA(ctx, cudaMemsetAsync(ctx->fused_sync.p, 0, 8 * sizeof(int), st));
         }
+        B.fused = fused_ok && (ctx->fused_mode == 1 || nprob <= kFusedTail);
     }
     // a zero initial guess (every problem) gives r0 = f without a product
     RBF_CHECK(ensure(ctx, ctx->flag_dev, 1));
@@ -681,6 +689,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
             B.C = Chunks{dk, dk + nk, dk + 2 * nk, dk + 3 * nk, nk};
             RBF_CHECK(build_active_lists(ctx, active, st));
             batch_graph_reset(ctx);
+            // few problems left: the fused step (one launch per Arnoldi step)
+            B.fused = fused_ok && (ctx->fused_mode == 1 || nact <= kFusedTail);
             compact_at = nact / 2;
             ++compactions;
         }

@@ -54,12 +54,15 @@ def solve(rbf, probs, fused, options=()):
 
 def test_fused_step_matches_separate_kernels_bit_for_bit(rbf):
     probs = problems()
-    c1, st1, inf1, w1, ptr, l1 = solve(rbf, probs, True)
-    c0, st0, inf0, w0, _, l0 = solve(rbf, probs, False)
+    c1, st1, inf1, w1, ptr, l1 = solve(rbf, probs, 1)
+    c0, st0, inf0, w0, _, l0 = solve(rbf, probs, 0)
+    c2, st2, inf2, w2, _, _ = solve(rbf, probs, 2)   # adaptive: six problems, all in the fused tail
     c1.close()
     c0.close()
-    assert st1 == 0 and st0 == 0, [i.as_dict() for i in inf1]
+    c2.close()
+    assert st1 == 0 and st0 == 0 and st2 == 0, [i.as_dict() for i in inf1]
     np.testing.assert_array_equal(w1, w0)
+    np.testing.assert_array_equal(w2, w0)
     assert [i.iters for i in inf1] == [i.iters for i in inf0]
     assert l1 * 3 < l0, (l1, l0)   # one launch per step instead of about ten
     for b, p in enumerate(probs):
@@ -70,7 +73,7 @@ def test_fused_step_matches_separate_kernels_bit_for_bit(rbf):
 
 def test_fused_step_barrier_timeout_is_reported_and_recoverable(rbf):
     probs = problems()[:3]
-    ctx, st, infos, _, _, _ = solve(rbf, probs, True, options=((rbf.RBF_OPT_BARRIER_SPIN_LIMIT, 2000),
+    ctx, st, infos, _, _, _ = solve(rbf, probs, 1, options=((rbf.RBF_OPT_BARRIER_SPIN_LIMIT, 2000),
                                                               (rbf.RBF_OPT_BARRIER_EXTRA_BLOCK, 1)))
     assert st == TIMEOUT
     assert "gave up waiting" in rbf.load().rbf_last_error(ctx.handle).decode()
@@ -92,7 +95,7 @@ def test_fused_step_barrier_timeout_is_reported_and_recoverable(rbf):
 
 def test_options_are_validated(rbf):
     ctx = rbf.Context(0)
-    for opt, val in ((99, 0), (rbf.RBF_OPT_FUSED_STEP, 2), (rbf.RBF_OPT_BARRIER_SPIN_LIMIT, 0)):
+    for opt, val in ((99, 0), (rbf.RBF_OPT_FUSED_STEP, 3), (rbf.RBF_OPT_BARRIER_SPIN_LIMIT, 0)):
         with pytest.raises(rbf.RbfError) as e:
             rbf.rbf_set_option(ctx.handle, opt, val)
         assert e.value.status == 1
