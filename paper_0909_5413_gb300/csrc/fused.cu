@@ -3,16 +3,16 @@
 // every problem of the batch on one GPU).
 //
 // The step's phases, for every problem still running in the cycle (the step
-// mask `run`):
+// mask `run`), separated by grid-wide barriers:
 //   1. u = M^{-1} v_j            RASM apply, one warp per subdomain (Eq. rasm)
-//   2. v_{j+1} = A_i u           symmetric FP32 matvec, one warp per inner cell,
-//   3.                           then the fixed-order gather of its slots
-//   4. h_k = V_k . v_{j+1}       Gram-Schmidt dots, one block per (chunk, k)
-//   5.                           reduced per problem and k, one warp each
-//   6. v_{j+1} -= V h, |v|^2     the update pass, one block per chunk
-//   7.                           |v|^2 reduced per problem; the Arnoldi column
-//                                (Hessenberg, Givens, estimate, stop test)
-//   8. v_{j+1} /= |v_{j+1}|      one block per chunk
+//   2. A_i u                     symmetric FP32 matvec, one warp per inner cell
+//   3. v_{j+1}, V_k . v_{j+1}    v_{j+1} summed from the matvec's slots (stored by
+//                                the chunk's k = 0 block), dots, one block per (chunk, k)
+//   4. v_{j+1} -= V h, |v|^2     per chunk: h of its problem reduced over the
+//                                problem's chunks, then the update pass
+//   5. v_{j+1} /= |v_{j+1}|      per chunk: |v|^2 of its problem reduced, the
+//                                scaling; the problem's first chunk also runs the
+//                                Arnoldi column (Hessenberg, Givens, estimate, stop)
 // run in one cooperative launch of a grid that is resident at once, with a
 // grid-wide barrier between phases. Each phase uses the same per-warp and
 // per-chunk code as the separate kernels of the step, in the same order, so
@@ -166,14 +166,9 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_step(FusedArgs A)
         }
     }
     if (!fused_barrier(A)) return;
-    // 3. the gather into v_{j+1}
-    for (int64_t p = gthread; p < A.n; p += nthreads) {
-        if (!A.run[A.pid[p]]) continue;
-        const int64_t n = A.n;
-        vn[p] = (((A.rowslot[p] + A.colslot[p]) + A.colslot[n + p]) + A.colslot[2 * n + p]) + A.colslot[3 * n + p];
-    }
-    if (!fused_barrier(A)) return;
-    // 4. dots, one block per (chunk, k)
+    // 3. v_{j+1} from the matvec's slots (the gather's fixed order; the k = 0
+    // block of a chunk stores it) and the dots V_k . v_{j+1}, one block per (chunk, k)
+    const int64_t n = A.n;
     for (int64_t unit = blockIdx.x; unit < A.C.nc * nv; unit += gridDim.x) {
         const int k = (int)(unit % nv);
         const int64_t c = unit / nv;
@@ -182,27 +177,49 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_step(FusedArgs A)
             if (tid == 0) A.partial[c * 32 + k] = 0.0;
             continue;
         }
-        ortho_dot_one<float>(A.V + k * A.ldv, vn, A.C.beg[c], A.C.end[c], S.o.red, A.partial + c * 32 + k);
+        const int64_t b = A.C.beg[c], e = A.C.end[c];
+        const float* vk = A.V + k * A.ldv;
+        float a[kOrthoPer], xs[kOrthoPer];
+#pragma unroll
+        for (int q = 0; q < kOrthoPer; ++q) {
+            const int64_t i = b + tid + (int64_t)q * kFusedThreads;
+            a[q] = i < e ? vk[i] : 0.f;
+            xs[q] = i < e ? (((A.rowslot[i] + A.colslot[i]) + A.colslot[n + i]) + A.colslot[2 * n + i]) +
+                                A.colslot[3 * n + i]
+                          : 0.f;
+        }
+        if (k == 0) {
+#pragma unroll
+            for (int q = 0; q < kOrthoPer; ++q) {
+                const int64_t i = b + tid + (int64_t)q * kFusedThreads;
+                if (i < e) vn[i] = xs[q];
+            }
+        }
+        ortho_warp_sum(ortho_thread_dot<float>(a, xs, b, e), S.o.red, 0);
+        __syncthreads();
+        if (tid == 0) A.partial[c * 32 + k] = ortho_block_total<float>(S.o.red, 0);
     }
     if (!fused_barrier(A)) return;
-    // 5. h per problem and k
-    for (int64_t unit = gwarp; unit < (int64_t)A.nprob * nv; unit += nwarps) {
-        const int pb = (int)(unit / nv), k = (int)(unit % nv);
-        if (!A.run[pb]) continue;
-        const double a = breduce_one(A.partial, A.C, pb, k, lane);
-        if (lane == 0) A.gm[pb].h1[k] = a;
-    }
-    if (!fused_barrier(A)) return;
-    // 6. v_{j+1} -= V h and |v_{j+1}|^2, one block per chunk
+    // 4. per chunk: h of its problem (reduced over the problem's chunks, the
+    // per-problem order; the problem's first chunk also stores it), then
+    // v_{j+1} -= V h and the chunk's |v_{j+1}|^2
+    double* partial2 = A.partial + A.C.nc * 32;
     for (int64_t c = blockIdx.x; c < A.C.nc; c += gridDim.x) {
         const int pb = A.C.pid[c];
-        double* out = A.partial + c * 32;
+        double* out = partial2 + c * 32;
         __syncthreads();   // the previous chunk is done with cf and red
         if (!A.run[pb]) {
             if (tid == 0) out[0] = 0.0;
             continue;
         }
-        if (tid < nv) ortho_coef_set(S.o.cf, tid, A.gm[pb].h1[tid]);
+        const bool first = c == A.C.cptr[pb];
+        for (int k = warp; k < nv; k += kFusedWarps) {
+            const double hk = breduce_one(A.partial, A.C, pb, k, lane);
+            if (lane == 0) {
+                ortho_coef_set(S.o.cf, k, hk);
+                if (first) A.gm[pb].h1[k] = hk;
+            }
+        }
         __syncthreads();
         const int64_t b = A.C.beg[c], e = A.C.end[c];
         DF xl[kOrthoPer];
@@ -215,27 +232,32 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_step(FusedArgs A)
         if (tid == 0) out[0] = ortho_block_total<float>(S.o.red, 0);
     }
     if (!fused_barrier(A)) return;
-    // 7. |v|^2 per problem, the Arnoldi column and the stop test (one warp per problem)
-    for (int64_t pb = gwarp; pb < A.nprob; pb += nwarps) {
-        if (!A.run[pb]) continue;
-        GmresDev* g = &A.gm[pb];
-        const double a = breduce_one(A.partial, A.C, (int)pb, 0, lane);
-        if (lane == 0) g->nrm2 = a;
-        __syncwarp();
-        arnoldi_column_s(g, A.j, 1, S.a.hc[warp], S.a.cs[warp], S.a.sn[warp]);
-        if (lane == 0) {
-            const int done = (g->est <= g->rtol || g->breakdown || A.j + 1 >= g->budget) ? 1 : 0;
-            g->done = done;
-            g->j = A.j + 1;
-            if (done) A.run[pb] = 0;
-        }
-    }
-    if (!fused_barrier(A)) return;
-    // 8. v_{j+1} /= |v_{j+1}| for the problems still running
+    // 5. per chunk: |v_{j+1}|^2 of its problem, v_{j+1} /= |v_{j+1}|; the
+    // problem's first chunk also takes the Arnoldi column and the stop test
+    // (a chunk that already sees its problem stopped leaves v_{j+1} as it is:
+    // it is not used)
     for (int64_t c = blockIdx.x; c < A.C.nc; c += gridDim.x) {
         const int pb = A.C.pid[c];
+        __syncthreads();
         if (!A.run[pb]) continue;
-        const double hn = sqrt(fmax(A.gm[pb].nrm2, 0.0));
+        if (warp == 0) {
+            const double nrm2 = breduce_one(partial2, A.C, pb, 0, lane);
+            if (lane == 0) S.a.hc[1][0] = nrm2;
+            if (c == A.C.cptr[pb]) {
+                GmresDev* g = &A.gm[pb];
+                if (lane == 0) g->nrm2 = nrm2;
+                __syncwarp();
+                arnoldi_column_s(g, A.j, 1, S.a.hc[0], S.a.cs[0], S.a.sn[0]);
+                if (lane == 0) {
+                    const int done = (g->est <= g->rtol || g->breakdown || A.j + 1 >= g->budget) ? 1 : 0;
+                    g->done = done;
+                    g->j = A.j + 1;
+                    if (done) A.run[pb] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        const double hn = sqrt(fmax(S.a.hc[1][0], 0.0));
         const float f = (float)(hn > 0.0 ? 1.0 / hn : 0.0);
         for (int64_t i = A.C.beg[c] + tid; i < A.C.end[c]; i += kFusedThreads) vn[i] = vn[i] * f;
     }

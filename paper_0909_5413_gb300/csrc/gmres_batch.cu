@@ -541,7 +541,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     RBF_CHECK(ensure(ctx, ctx->gmb, nprob));
     RBF_CHECK(ensure(ctx, ctx->bactive, 4 * (size_t)nprob));
     RBF_CHECK(ensure(ctx, ctx->bstat, 4 * (size_t)nprob));
-    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(nc, 1) * 32));
+    RBF_CHECK(ensure(ctx, ctx->partial, (size_t)std::max<int64_t>(nc, 1) * 64));   // dots, and the fused step's norms
     RBF_CHECK(ensure(ctx, ctx->vec_a, n));
     RBF_CHECK(ensure(ctx, ctx->vec_b, n));
     GmresDev* gm = ctx->gmb.p;
