@@ -138,8 +138,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_step(FusedArgs A)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t gwarp = (int64_t)blockIdx.x * kFusedWarps + warp;
     const int64_t nwarps = (int64_t)gridDim.x * kFusedWarps;
-    const int64_t gthread = (int64_t)blockIdx.x * kFusedThreads + tid;
-    const int64_t nthreads = (int64_t)gridDim.x * kFusedThreads;
     float* vj = A.V + (int64_t)A.j * A.ldv;
     float* vn = A.V + (int64_t)(A.j + 1) * A.ldv;
     const int nv = A.j + 1;
