@@ -117,6 +117,7 @@ def f32_matvec_roofline(pairs: int, cand: int, avg_s: float, launches: int, traf
 WORKLOADS = {
     "lattice64": (W.config_small, "64x64 jittered lattice on [-1,1]^2 (N=4,096)"),
     "lattice1024": (W.config_1m, "1024x1024 jittered lattice on [-1,1]^2 (N=1,048,576)"),
+    "lattice2048": (W.config_4m, "2048x2048 jittered lattice on [-1,1]^2 (N=4,194,304)"),
     "lattice7168": (W.config_51m, "7168x7168 jittered lattice on [-1,1]^2 (N=51,380,224)"),
     "batch4096": (None, "independent jittered lattices on [-1,1]^2, N log-uniform in [256, 16384], "
                         "h/sigma uniform in [0.6, 1.0], f = sum of four random Gaussians, one seed per problem"),

@@ -132,6 +132,12 @@ def config_1m(seed: int = DEFAULT_SEED) -> Problem:
     return lattice_problem(1024, 0.8, seed, name="lattice1024_f64")
 
 
+def config_4m(seed: int = DEFAULT_SEED) -> Problem:
+    """2048 x 2048 jittered lattice, h/sigma = 0.8 (N = 4,194,304): above the L2 cache, small
+    enough for detailed kernel captures."""
+    return lattice_problem(2048, 0.8, seed, name="lattice2048")
+
+
 def config_51m(seed: int = DEFAULT_SEED) -> Problem:
     """7168 x 7168 jittered lattice, h/sigma = 0.8 (N = 51,380,224)."""
     return lattice_problem(7168, 0.8, seed, name="lattice7168")
