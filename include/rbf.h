@@ -173,8 +173,9 @@ rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const doubl
  * use, interpolation from the scattered centres onto other points such as a
  * lattice (Sec. 3.2). xe_dev: m x 2 interleaved (x, y), device, any order;
  * w_dev: n weights in user order (from rbf_solve); s_dev: m outputs (device,
- * caller-owned). At the centres themselves s equals rbf_matvec's y bit for
- * bit. Points farther than r_c from every centre get 0. Needs rbf_bin (one
+ * caller-owned). At the centres themselves s equals rbf_matvec's y (bit for
+ * bit with the stencil FP64 kernel, to rounding with the symmetric one, which
+ * sums in another order). Points farther than r_c from every centre get 0. Needs rbf_bin (one
  * problem: STATE for a batch); INVALID_ARG for a non-finite point. The
  * points are binned into the centres' grid on each call (clamped to the edge
  * cells). */
@@ -418,6 +419,11 @@ enum {
      * neighbouring cells once (cells of at most 128 points); 0: every target
      * against its 3 x 3 cells. */
     RBF_OPT_SYMMETRIC_F32 = 2,
+    /* 1 (default): the FP64 matvec visits each pair of neighbouring cells once
+     * (cells as wide as r_c, of at most 160 points; kernel values shared by
+     * both directions, column sums gathered in a fixed order); 0: every target
+     * against its 3 x 3 cells. Both give the truncated product to rounding. */
+    RBF_OPT_SYMMETRIC_F64 = 5,
     /* Polls of a grid-barrier wait of the fused step before it gives up: the
      * step then ends, and the solve returns RBF_ERR_TIMEOUT (value >= 1;
      * default 2^23, about a second). */

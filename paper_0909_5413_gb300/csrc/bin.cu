@@ -484,6 +484,10 @@ rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, in
 
 // Bins all problems of ctx->prob_h (kernel parameters and point ranges filled
 // in; grids are set here from the bounding boxes).
+static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
+                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
+                                    cudaStream_t st);
+
 rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
 {
     const int64_t n = ctx->n;
@@ -576,6 +580,24 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
     int32_t smax = 0;
     RBF_CHECK(reduce_max_i32(ctx, ctx->mv_wcnt.p, ncell, &smax, st));
     ctx->stage_max = smax;
+    // the symmetric FP64 matvec: a 3 x 3 stencil (cells as wide as r_c) of cells
+    // of at most 160 points; its class lists and slots are made here, outside
+    // any graph capture
+    ctx->sym64 = false;
+    bool k1 = true;
+    for (int b = 0; b < nprob; ++b) k1 = k1 && P[b].k == 1;
+    if (k1) {
+        RBF_LAUNCH(ctx, k_cell_sizes, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell, ctx->mv_wcnt.p);
+        int32_t cmax = 0;
+        RBF_CHECK(reduce_max_i32(ctx, ctx->mv_wcnt.p, ncell, &cmax, st));
+        if (cmax <= 160) {
+            RBF_CHECK(ensure(ctx, ctx->tmp_i32, std::max<int64_t>(2 * (ncell + 1), n)));
+            RBF_CHECK(build_class_lists(ctx, ctx->cell_start.p, ncell, 5, ctx->sym64w, ctx->sym64off, ctx->tmp_i32.p,
+                                        ctx->tmp_i32.p + (ncell + 1), st));
+            RBF_CHECK(ensure(ctx, ctx->sym64_slots, (size_t)(5 * n)));
+            ctx->sym64 = true;
+        }
+    }
     RBF_CHECK(matvec_prepare(ctx));
     return prof_end(ctx, RBF_PROF_BIN, st);
 }
@@ -675,6 +697,28 @@ rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cud
     return RBF_OK;
 }
 
+// Cell lists by size class for the symmetric matvecs: non-empty cells with
+// ceil(points / 32) == t, t = 1..max_tpl, as (cell, 0) items in `lists`
+// (class t holds [off[t-1], off[t])), order kept within a class. flag and pos
+// are scratch of ncell + 1 entries each.
+static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
+                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
+                                    cudaStream_t st)
+{
+    RBF_CHECK(ensure(ctx, lists, 2 * (size_t)std::max<int64_t>(ncell, 1)));
+    off[0] = 0;
+    for (int t = 1; t <= max_tpl; ++t) {
+        RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, cell_start, ncell, t, flag);
+        RBF_CHECK(exclusive_scan_i32(ctx, flag, pos, ncell, st));
+        RBF_LAUNCH(ctx, k_scatter_cells, blocks_for(ncell, 256), 256, 0, st, ncell, flag, pos, lists.p + 2 * off[t - 1]);
+        int32_t cnt = 0;
+        RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, pos + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+        off[t] = off[t - 1] + cnt;
+    }
+    return RBF_OK;
+}
+
 rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
 {
     InnerGrid& G = ctx->in;
@@ -748,21 +792,9 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
         // its slots are allocated here, outside the solver's graph capture
         RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
         // its cell lists by size class (order kept within a class)
-        RBF_CHECK(ensure(ctx, G.symw, 2 * (size_t)std::max<int64_t>(ncell, 1)));
         RBF_CHECK(ensure(ctx, G.tmp, std::max<int64_t>(2 * (ncell + 1), 2 * kNumSMs + 1)));
-        int32_t* flag = G.tmp.p;
-        int32_t* pos = G.tmp.p + (ncell + 1);
-        G.symoff[0] = 0;
-        for (int t = 1; t <= 4; ++t) {
-            RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, t, flag);
-            RBF_CHECK(exclusive_scan_i32(ctx, flag, pos, ncell, st));
-            RBF_LAUNCH(ctx, k_scatter_cells, blocks_for(ncell, 256), 256, 0, st, ncell, flag, pos,
-                       G.symw.p + 2 * G.symoff[t - 1]);
-            int32_t cnt = 0;
-            RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, pos + ncell, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            RBF_CUDA(ctx, cudaStreamSynchronize(st));
-            G.symoff[t] = G.symoff[t - 1] + cnt;
-        }
+        RBF_CHECK(build_class_lists(ctx, G.cell_start.p, ncell, 4, G.symw, G.symoff, G.tmp.p, G.tmp.p + (ncell + 1),
+                                    st));
     }
     // subdomain lists in inner positions
     if (ctx->rasm_ready) {

@@ -288,6 +288,10 @@ rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
         if (value != 0 && value != 1) break;
         ctx->sym_mode = value ? 0 : 1;
         return RBF_OK;
+    case RBF_OPT_SYMMETRIC_F64:
+        if (value != 0 && value != 1) break;
+        ctx->sym64_mode = value ? 0 : 1;
+        return RBF_OK;
     case RBF_OPT_BARRIER_SPIN_LIMIT:
         if (value < 1) break;
         ctx->fused_spin_limit = (unsigned long long)value;

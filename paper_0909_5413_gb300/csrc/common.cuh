@@ -160,6 +160,11 @@ struct rbf_ctx {
     InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
     bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
     int sym_mode = 0;              // inner FP32 operator: 0 symmetric kernel when the grid allows, 1 stencil kernel
+    bool sym64 = false;            // the symmetric FP64 matvec applies (3 x 3 stencil, cells of <= 160 points)
+    int sym64_mode = 0;            // FP64 matvec: 0 symmetric kernel when it applies, 1 stencil kernel
+    rbf::DevArray<int32_t> sym64w;    // its (cell, 0) items by size class ceil(points / 32) = 1..5
+    int64_t sym64off[6] = {0, 0, 0, 0, 0, 0};
+    rbf::DevArray<double> sym64_slots;   // its row slot and four column slots per point
     rbf::DevArray<float> sym_slots;   // symmetric FP32 kernel: row slot and four column slots per point
     rbf::DevArray<unsigned long long> count_u64;   // one 64-bit counter (rbf_count_candidates)
     rbf::DevArray<int> flag_dev;                   // one flag (zero initial guess test of the solvers)

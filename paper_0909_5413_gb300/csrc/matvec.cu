@@ -333,6 +333,237 @@ __global__ void k_sym_gather(const float* __restrict__ rowslot, const float* __r
     y[p] = (((rowslot[p] + colslot[p]) + colslot[n + p]) + colslot[2 * n + p]) + colslot[3 * n + p];
 }
 
+// Symmetric FP64 matvec (the exact truncated operator): one warp per cell C of
+// at most 160 points (TPL = ceil(points / 32) targets per lane), with the 3 x
+// 3 stencil of cells as wide as r_c. As in the FP32 kernel, C takes itself (row
+// sums only) and its four forward neighbours D; each accepted pair (i, j) --
+// the packed FP32 filter, the exact FP64 pair test in the thin band around
+// r_c -- gets its kernel value once, by the fixed-point evaluation, which
+// feeds i's row sum (registers) and, through the lane's row of a shared FP64
+// tile (lane i adds k_ij w_i at column j), j's column sum: lane j adds the
+// warp's 32 rows in order. A missing backward neighbour's slot gets zero.
+// FP64 work stays one FMA per directed pair (row or column), the integer
+// work of the kernel values is halved.
+constexpr int kSym64Warps = 4;
+constexpr int kSym64Stage = 160 + 32;
+constexpr int kSym64Tld = 33;
+
+struct Sym64Warp {
+    double sx[2 * kSym64Stage];          // staged FP64 coordinates (x, y) for the exact band test
+    long long sxf[2 * kSym64Stage];      // pre-shifted fixed-point coordinates
+    double sw[kSym64Stage];
+    float sf[2 * kSym64Stage];           // FP32 offsets from C's corner, (x_a, x_b, y_a, y_b) per source pair
+    double T[32 * kSym64Tld];            // column tile: lane r's contributions at columns 0..31
+};
+
+template <int TPL, bool COL, bool F52>
+__device__ __forceinline__ void sym64_pass(Sym64Warp& S, int lane, const Prob& pr, const unsigned long long* T1,
+                                           const unsigned long long* T2, const double (&xi)[TPL],
+                                           const double (&yi)[TPL], const long long (&xf)[TPL],
+                                           const long long (&yf)[TPL], const float (&fx)[TPL], const float (&fy)[TPL],
+                                           const double (&wt)[TPL], double (&acc)[TPL], int dn,
+                                           double* __restrict__ colout, double knorm)
+{
+    const double rc2 = pr.rc2;
+    const float rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
+    const int F = pr.fx_F;
+    const unsigned long long M = pr.fx_M;
+    const int nw = (dn + 31) >> 5;
+    for (int wi = 0; wi < nw; ++wi) {
+        if (COL) {
+#pragma unroll 8
+            for (int b = 0; b < 32; ++b) S.T[lane * kSym64Tld + b] = 0.0;
+        }
+        const int lim = dn - wi * 32;
+        const float4* S4 = reinterpret_cast<const float4*>(S.sf) + wi * 16;
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            // FP32 filter of the word's 32 sources against target t, the band settled in FP64
+            uint32_t m = 0, mh = 0;
+            const float2 fx2 = make_float2(fx[t], fx[t]), fy2 = make_float2(fy[t], fy[t]);
+#pragma unroll
+            for (int b = 0; b < 32; b += 2) {
+                const float4 v = S4[b >> 1];
+                const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
+                const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
+                const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
+                m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
+                mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
+            }
+            if (lim < 32) {
+                const uint32_t keep = (1u << lim) - 1u;
+                m &= keep;
+                mh &= keep;
+            }
+            uint32_t band = mh & ~m;
+            while (band != 0u) {
+                const int b = __ffs(band) - 1;
+                band &= band - 1u;
+                const int idx = wi * 32 + b;
+                const double ex = __dsub_rn(xi[t], S.sx[2 * idx]), ey = __dsub_rn(yi[t], S.sx[2 * idx + 1]);
+                if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
+            }
+            // the accepted sources, two per step, the warp in lockstep
+            uint32_t cur = m;
+            for (;;) {
+                const bool has = cur != 0u;
+                if (!__any_sync(0xffffffffu, has)) break;
+                if (has) {
+                    const int b0 = __ffs(cur) - 1;
+                    cur &= cur - 1u;
+                    const bool two = cur != 0u;
+                    const int b1 = two ? __ffs(cur) - 1 : b0;
+                    cur &= cur - (two ? 1u : 0u);
+                    const int i0 = wi * 32 + b0, i1 = wi * 32 + b1;
+                    const long long du0 = (long long)((unsigned long long)xf[t] - (unsigned long long)S.sxf[2 * i0]);
+                    const long long dv0 = (long long)((unsigned long long)yf[t] - (unsigned long long)S.sxf[2 * i0 + 1]);
+                    const long long du1 = (long long)((unsigned long long)xf[t] - (unsigned long long)S.sxf[2 * i1]);
+                    const long long dv1 = (long long)((unsigned long long)yf[t] - (unsigned long long)S.sxf[2 * i1 + 1]);
+                    double k0, k1;
+                    if (F52) {
+                        k0 = kernel_fx52(du0, dv0, M, T1, T2);
+                        k1 = kernel_fx52(du1, dv1, M, T1, T2);
+                    } else {
+                        k0 = kernel_fx(du0, dv0, F, M, T1, T2);
+                        k1 = kernel_fx(du1, dv1, F, M, T1, T2);
+                    }
+                    acc[t] = fma(k0, S.sw[i0], acc[t]);
+                    if (two) acc[t] = fma(k1, S.sw[i1], acc[t]);
+                    if (COL) {
+                        double* row = S.T + lane * kSym64Tld;
+                        row[b0] = fma(k0, wt[t], row[b0]);
+                        if (two) row[b1] = fma(k1, wt[t], row[b1]);
+                    }
+                }
+            }
+        }
+        if (COL) {
+            __syncwarp();
+            double sum = 0.0;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) sum += S.T[r * kSym64Tld + lane];
+            __syncwarp();
+            if (lane < lim) colout[wi * 32 + lane] = sum * knorm;
+        }
+    }
+}
+
+template <int TPL, bool F52>
+__device__ __forceinline__ void sym64_cell(const MvParams& P, Sym64Warp& S, int lane, int cell, int cb, int cnt,
+                                           const Prob& pr, const double* __restrict__ w, double* __restrict__ rowslot,
+                                           double* __restrict__ colslot, int64_t n)
+{
+    const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, cbase = (int)pr.cellbase;
+    const float ca = pr.ca;
+    const double knorm = pr.knorm, fxs = pr.fx_scale;
+    const int sh = pr.fx_sh;
+    const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
+    double xi[TPL], yi[TPL], wt[TPL], acc[TPL];
+    long long xf[TPL], yf[TPL];
+    float fx[TPL], fy[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int q = lane + 32 * t;
+        const bool ok = q < cnt;
+        const int p = cb + (ok ? q : 0);
+        xi[t] = P.xy[2 * (int64_t)p];
+        yi[t] = P.xy[2 * (int64_t)p + 1];
+        xf[t] = fx_coord(xi[t], fxs, sh);
+        yf[t] = fx_coord(yi[t], fxs, sh);
+        fx[t] = ok ? P.loc[2 * (int64_t)p] : -1.0e4f;   // a missing target accepts no source
+        fy[t] = ok ? P.loc[2 * (int64_t)p + 1] : -1.0e4f;
+        wt[t] = ok ? w[p] : 0.0;
+        acc[t] = 0.0;
+    }
+    {   // zero slots of the backward directions whose source cell is missing
+        const int bx[4] = {cx - 1, cx + 1, cx, cx - 1}, by[4] = {cy, cy - 1, cy - 1, cy - 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bool missing = bx[q] < 0 || bx[q] >= ncx || by[q] < 0;
+            if (!missing) {
+                const int c = cbase + by[q] * ncx + bx[q];
+                missing = P.cell_start[c + 1] == P.cell_start[c];
+            }
+            if (missing)
+                for (int t = lane; t < cnt; t += 32) colslot[(int64_t)q * n + cb + t] = 0.0;
+        }
+    }
+    const unsigned long long* T1 = P.fxtab;
+    const unsigned long long* T2 = P.fxtab + kFxTab;
+#pragma unroll 1
+    for (int pass = 0; pass < 5; ++pass) {
+        const int dx = (pass == 1 || pass == 4) ? 1 : (pass == 2 ? -1 : 0);
+        const int dy = pass >= 2 ? 1 : 0;
+        const int nx = cx + dx, ny = cy + dy;
+        if (nx < 0 || nx >= ncx || ny >= ncy) continue;
+        const int dcell = cbase + ny * ncx + nx;
+        const int db = P.cell_start[dcell], dn = P.cell_start[dcell + 1] - db;
+        if (dn == 0) continue;
+        const int dnp = (dn + 31) & ~31;
+        for (int s = lane; s < dnp; s += 32) {
+            float lx = 1.0e4f, ly = 1.0e4f;
+            if (s < dn) {
+                const int64_t q = db + s;
+                const double x = P.xy[2 * q], y = P.xy[2 * q + 1];
+                S.sx[2 * s] = x;
+                S.sx[2 * s + 1] = y;
+                S.sxf[2 * s] = fx_coord(x, fxs, sh);
+                S.sxf[2 * s + 1] = fx_coord(y, fxs, sh);
+                S.sw[s] = w[q];
+                lx = P.loc[2 * q] + (float)dx * ca;
+                ly = P.loc[2 * q + 1] + (float)dy * ca;
+            } else {
+                S.sw[s] = 0.0;
+            }
+            S.sf[4 * (s >> 1) + (s & 1)] = lx;
+            S.sf[4 * (s >> 1) + 2 + (s & 1)] = ly;
+        }
+        __syncwarp();
+        if (pass == 0)
+            sym64_pass<TPL, false, F52>(S, lane, pr, T1, T2, xi, yi, xf, yf, fx, fy, wt, acc, dn, nullptr, knorm);
+        else
+            sym64_pass<TPL, true, F52>(S, lane, pr, T1, T2, xi, yi, xf, yf, fx, fy, wt, acc, dn,
+                                       colslot + (int64_t)(pass - 1) * n + db, knorm);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const int q = lane + 32 * t;
+        if (q < cnt) rowslot[cb + q] = acc[t] * knorm;
+    }
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(kSym64Warps * 32)
+    k_matvec_f64_sym(MvParams P, const int32_t* __restrict__ cells, int64_t ncells, const double* __restrict__ w,
+                     double* __restrict__ rowslot, double* __restrict__ colslot, int64_t n)
+{
+    extern __shared__ __align__(16) unsigned char sym64_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kSym64Warps + warp;
+    if (item >= ncells) return;
+    const int cell = cells[2 * item];
+    const int pcell = P.pid_cell[cell];
+    if (P.active && !P.active[pcell]) return;
+    const Prob& pr = P.prob[pcell];
+    const int cb = P.cell_start[cell], cnt = P.cell_start[cell + 1] - cb;
+    Sym64Warp& S = reinterpret_cast<Sym64Warp*>(sym64_raw)[warp];
+    if (pr.fx_F == 52) sym64_cell<TPL, true>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n);
+    else sym64_cell<TPL, false>(P, S, lane, cell, cb, cnt, pr, w, rowslot, colslot, n);
+}
+
+// y_p = row slot + the four column slots in the order of d (each already
+// carrying the normalisation). Points of masked problems are left alone.
+__global__ void k_sym64_gather(const double* __restrict__ rowslot, const double* __restrict__ colslot, int64_t n,
+                               const int32_t* __restrict__ pid, const int32_t* __restrict__ active,
+                               double* __restrict__ y)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (active && !active[pid[p]]) return;
+    y[p] = (((rowslot[p] + colslot[p]) + colslot[n + p]) + colslot[2 * n + p]) + colslot[3 * n + p];
+}
+
 __global__ void k_to_f32(const double* __restrict__ in, int64_t n, float* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -417,15 +648,53 @@ bool inner_sym_params(rbf_ctx* ctx, MvParams* P, const int32_t** cells, int64_t*
     return true;
 }
 
+template <int TPL>
+static rbf_status prepare_sym64(rbf_ctx* ctx)
+{
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64_sym<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(Sym64Warp) * kSym64Warps)));
+    return RBF_OK;
+}
+
 rbf_status matvec_prepare(rbf_ctx* ctx)
 {
     RBF_CHECK(prepare_f64<32>(ctx));
     RBF_CHECK(prepare_f64<64>(ctx));
-    return prepare_f64<128>(ctx);
+    RBF_CHECK(prepare_f64<128>(ctx));
+    RBF_CHECK(prepare_sym64<1>(ctx));
+    RBF_CHECK(prepare_sym64<2>(ctx));
+    RBF_CHECK(prepare_sym64<3>(ctx));
+    RBF_CHECK(prepare_sym64<4>(ctx));
+    return prepare_sym64<5>(ctx);
 }
 
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
+    if (ctx->sym64 && ctx->sym64_mode == 0 && !ctx->al.on) {
+        // each neighbouring pair of cells once, then the fixed-order gather
+        const int64_t n = ctx->n;
+        if (ctx->sym64_slots.count < (size_t)(5 * n))
+            return fail(ctx, RBF_ERR_STATE, "symmetric FP64 matvec: slots not allocated");
+        MvParams P = mv_params(ctx);
+        double* rowslot = ctx->sym64_slots.p;
+        double* colslot = rowslot + n;
+        const size_t smem = sizeof(Sym64Warp) * kSym64Warps;
+        for (int t = 1; t <= 5; ++t) {
+            const int64_t cnt = ctx->sym64off[t] - ctx->sym64off[t - 1];
+            if (cnt == 0) continue;
+            const int32_t* cl = ctx->sym64w.p + 2 * ctx->sym64off[t - 1];
+            const unsigned nb = blocks_for(cnt, kSym64Warps);
+            switch (t) {
+            case 1: RBF_LAUNCH(ctx, k_matvec_f64_sym<1>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            case 2: RBF_LAUNCH(ctx, k_matvec_f64_sym<2>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            case 3: RBF_LAUNCH(ctx, k_matvec_f64_sym<3>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            case 4: RBF_LAUNCH(ctx, k_matvec_f64_sym<4>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n); break;
+            default: RBF_LAUNCH(ctx, k_matvec_f64_sym<5>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n);
+            }
+        }
+        RBF_LAUNCH(ctx, k_sym64_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active, y);
+        return RBF_OK;
+    }
     if (ctx->al.on) {   // batched solve: only the work items of active problems
         MvParams P = mv_params(ctx);
         P.work = ctx->al.w64.p;

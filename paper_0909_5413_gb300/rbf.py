@@ -35,6 +35,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_debug_inner_matvec", "rbf_set_option"]
 
 RBF_OPT_FUSED_STEP, RBF_OPT_SYMMETRIC_F32, RBF_OPT_BARRIER_SPIN_LIMIT, RBF_OPT_BARRIER_EXTRA_BLOCK = 1, 2, 3, 4
+RBF_OPT_SYMMETRIC_F64 = 5
 
 RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
     range(6)

@@ -150,10 +150,15 @@ def test_eval_matches_oracle_and_matvec(rbf):
     ref = O.eval_points(p.xy, w, xe, p.sigma, p.cutoff)
     assert rel_err(got, ref) <= 1e-13
     assert got[20000] == 0.0
-    # at the centres (user order) the interpolant is the matvec, bit for bit
+    # at the centres (user order) the interpolant is the matvec: bit for bit with
+    # the stencil kernel (the same per-target sum), to rounding with the
+    # symmetric one (each pair once, another summation order)
     s2 = torch.empty(p.n, dtype=torch.float64, device="cuda")
     y = torch.empty(p.n, dtype=torch.float64, device="cuda")
     rbf.rbf_eval(ctx.handle, dev(p.xy), p.n, dev(w), s2)
+    rbf.rbf_matvec(ctx.handle, dev(w), y)
+    assert np.max(np.abs(host(s2) - host(y))) <= 1e-14 * np.max(np.abs(host(y)))
+    rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, 0)
     rbf.rbf_matvec(ctx.handle, dev(w), y)
     np.testing.assert_array_equal(host(s2), host(y))
     ctx.close()

@@ -582,3 +582,42 @@ def test_tune_picks_a_valid_setting_and_solves(rbf, w32):
                              check=False)
     assert st == 0 and info.relres <= 1e-13
     ctx.close()
+
+
+# ------------------------------------------------- symmetric FP64 matvec
+
+@pytest.mark.parametrize("n_side,ratio,normalized", [(96, 0.8, False), (61, 0.9, True), (80, 1.0, False),
+                                                     (40, 0.85, False)])
+def test_symmetric_f64_matvec(rbf, n_side, ratio, normalized):
+    """Each neighbouring pair of cells once (kernel values shared by both
+    directions, column sums gathered in a fixed order) against the stencil
+    kernel and the oracle, element by element; and the same bits on a second call."""
+    p = W.lattice_problem(n_side, ratio, seed=600 + n_side)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff, 0.0, normalized)
+    w = np.random.default_rng(7).standard_normal(p.n)
+    ys, yt, y2 = (torch.empty(p.n, dtype=torch.float64, device="cuda") for _ in range(3))
+    rbf.rbf_matvec(ctx.handle, dev(w), ys)
+    rbf.rbf_matvec(ctx.handle, dev(w), y2)
+    rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, 0)
+    rbf.rbf_matvec(ctx.handle, dev(w), yt)
+    a, b, c = host(ys), host(yt), host(y2)
+    np.testing.assert_array_equal(a, c)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+    ref = O.matvec_cutoff(p.xy, w, p.sigma, p.cutoff, normalized=normalized)
+    assert np.max(np.abs(a - ref)) <= 1e-13 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_symmetric_f64_matvec_uneven_points(rbf):
+    """Uniform random points (empty and crowded cells, ragged edges)."""
+    rng = np.random.default_rng(12)
+    xy = np.ascontiguousarray(rng.uniform(-1.0, 1.0, size=(9000, 2)))
+    sigma, rc = 0.015, 0.129
+    ctx, _ = make_ctx(rbf, xy, sigma, rc)
+    w = rng.standard_normal(xy.shape[0])
+    y = torch.empty(xy.shape[0], dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(w), y)
+    ref = O.matvec_cutoff(xy, w, sigma, rc)
+    got = host(y)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    ctx.close()
