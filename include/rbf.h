@@ -419,10 +419,15 @@ enum {
      * neighbouring cells once (cells of at most 128 points); 0: every target
      * against its 3 x 3 cells. */
     RBF_OPT_SYMMETRIC_F32 = 2,
-    /* 1 (default): the FP64 matvec visits each pair of neighbouring cells once
-     * (cells as wide as r_c, of at most 160 points; kernel values shared by
-     * both directions, column sums gathered in a fixed order); 0: every target
-     * against its 3 x 3 cells. Both give the truncated product to rounding. */
+    /* 1: the FP64 matvec visits each pair of neighbouring cells once, for
+     * each problem with cells as wide as r_c holding at most 160 points (kernel
+     * values shared by both directions, column sums gathered in a fixed
+     * order); 0 (default): every target against its 3 x 3 cells. Both give the
+     * truncated product to rounding. Takes effect at the next rbf_bin or
+     * rbf_bin_batch (which allocates its 5 N doubles of slots); setting 0
+     * after binning returns to the stencil kernel at once. The default is the
+     * faster form on GB300: the FP64 pipe, which carries one FMA per directed
+     * pair in both, bounds the symmetric form. */
     RBF_OPT_SYMMETRIC_F64 = 5,
     /* Polls of a grid-barrier wait of the fused step before it gives up: the
      * step then ends, and the solve returns RBF_ERR_TIMEOUT (value >= 1;

@@ -263,12 +263,24 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
 
 // Size class t (ceil(points / 32) == t) flags of the cells, and the scatter of
 // the flagged cells as (cell, 0) items.
-__global__ void k_flag_class(const int32_t* __restrict__ cell_start, int64_t ncell, int t, int32_t* __restrict__ flag)
+__global__ void k_flag_class(const int32_t* __restrict__ cell_start, int64_t ncell, int t,
+                             const int32_t* __restrict__ pid_cell, const int32_t* __restrict__ prob_ok,
+                             int32_t* __restrict__ flag)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int cnt = cell_start[c + 1] - cell_start[c];
-    flag[c] = (cnt > 0 && (cnt + 31) / 32 == t) ? 1 : 0;
+    flag[c] = (cnt > 0 && (cnt + 31) / 32 == t && (!prob_ok || prob_ok[pid_cell[c]])) ? 1 : 0;
+}
+
+// Largest cell of each problem (atomic max per problem).
+__global__ void k_prob_max_cell(const int32_t* __restrict__ cell_start, int64_t ncell,
+                                const int32_t* __restrict__ pid_cell, int32_t* __restrict__ pmax)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int cnt = cell_start[c + 1] - cell_start[c];
+    if (cnt > 0) atomicMax(&pmax[pid_cell[c]], cnt);
 }
 
 __global__ void k_scatter_cells(int64_t ncell, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
@@ -281,12 +293,6 @@ __global__ void k_scatter_cells(int64_t ncell, const int32_t* __restrict__ flag,
     }
 }
 
-// Points per cell.
-__global__ void k_cell_sizes(const int32_t* __restrict__ cell_start, int64_t ncell, int32_t* __restrict__ out)
-{
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell) out[c] = cell_start[c + 1] - cell_start[c];
-}
 
 // Pairs (i, j), i = j included, of a cell grid with r2_ij <= R^2 by the FP64
 // pair test (R = r_c on the main grid, the cell side on the inner grid, whose
@@ -482,12 +488,16 @@ rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, in
     return RBF_OK;
 }
 
+static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
+                                    const int32_t* pid_cell, const int32_t* prob_ok, DevArray<int32_t>& lists,
+                                    int64_t* off, int32_t* flag, int32_t* pos, cudaStream_t st);
+namespace {
+rbf_status select_work_into(rbf_ctx* ctx, const int32_t* work, int64_t nwork, const int32_t* pid_cell,
+                            const int32_t* active, int32_t* out, int64_t* nout, cudaStream_t st);
+}  // namespace
+
 // Bins all problems of ctx->prob_h (kernel parameters and point ranges filled
 // in; grids are set here from the bounding boxes).
-static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
-                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
-                                    cudaStream_t st);
-
 rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
 {
     const int64_t n = ctx->n;
@@ -580,22 +590,42 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
     int32_t smax = 0;
     RBF_CHECK(reduce_max_i32(ctx, ctx->mv_wcnt.p, ncell, &smax, st));
     ctx->stage_max = smax;
-    // the symmetric FP64 matvec: a 3 x 3 stencil (cells as wide as r_c) of cells
-    // of at most 160 points; its class lists and slots are made here, outside
-    // any graph capture
-    ctx->sym64 = false;
-    bool k1 = true;
-    for (int b = 0; b < nprob; ++b) k1 = k1 && P[b].k == 1;
-    if (k1) {
-        RBF_LAUNCH(ctx, k_cell_sizes, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell, ctx->mv_wcnt.p);
-        int32_t cmax = 0;
-        RBF_CHECK(reduce_max_i32(ctx, ctx->mv_wcnt.p, ncell, &cmax, st));
-        if (cmax <= 160) {
+    // When enabled, the symmetric FP64 matvec serves each problem whose
+    // stencil is 3 x 3 (cells as wide as r_c) and whose cells hold at most 160
+    // points; the stencil kernel serves the others. The choice depends on the
+    // problem alone, so a problem sums in the same order alone and in any
+    // batch. The class lists, the other problems' work list and the slots are
+    // made here, outside any graph capture.
+    ctx->sym64 = ctx->sym64_all = false;
+    if (ctx->sym64_mode == 0) {
+        RBF_CHECK(ensure(ctx, ctx->sym64_prob, 2 * (size_t)nprob));
+        int32_t* pmax = ctx->sym64_prob.p + nprob;
+        RBF_CUDA(ctx, cudaMemsetAsync(pmax, 0, sizeof(int32_t) * nprob, st));
+        RBF_LAUNCH(ctx, k_prob_max_cell, blocks_for(ncell, 256), 256, 0, st, ctx->cell_start.p, ncell,
+                   ctx->pid_cell.p, pmax);
+        std::vector<int32_t> hmax(nprob), ok(2 * (size_t)nprob);
+        RBF_CUDA(ctx, cudaMemcpyAsync(hmax.data(), pmax, sizeof(int32_t) * nprob, cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+        int64_t nsym = 0;
+        for (int b = 0; b < nprob; ++b) {
+            ok[b] = (P[b].k == 1 && hmax[b] <= 160) ? 1 : 0;
+            ok[nprob + b] = 1 - ok[b];
+            nsym += ok[b];
+        }
+        ctx->sym64 = nsym > 0;
+        ctx->sym64_all = nsym == nprob;
+        // [0, nprob): symmetric kernel; [nprob, 2 nprob): stencil kernel
+        RBF_CUDA(ctx, cudaMemcpyAsync(ctx->sym64_prob.p, ok.data(), sizeof(int32_t) * 2 * nprob, cudaMemcpyHostToDevice,
+                                      st));
+        if (ctx->sym64) {
             RBF_CHECK(ensure(ctx, ctx->tmp_i32, std::max<int64_t>(2 * (ncell + 1), n)));
-            RBF_CHECK(build_class_lists(ctx, ctx->cell_start.p, ncell, 5, ctx->sym64w, ctx->sym64off, ctx->tmp_i32.p,
-                                        ctx->tmp_i32.p + (ncell + 1), st));
+            RBF_CHECK(build_class_lists(ctx, ctx->cell_start.p, ncell, 5, ctx->pid_cell.p, ctx->sym64_prob.p,
+                                        ctx->sym64w, ctx->sym64off, ctx->tmp_i32.p, ctx->tmp_i32.p + (ncell + 1),
+                                        st));
             RBF_CHECK(ensure(ctx, ctx->sym64_slots, (size_t)(5 * n)));
-            ctx->sym64 = true;
+            RBF_CHECK(ensure(ctx, ctx->mv_work_ns, 2 * (size_t)std::max<int64_t>(ctx->n_work, 1)));
+            RBF_CHECK(select_work_into(ctx, ctx->mv_work.p, ctx->n_work, ctx->pid_cell.p, ctx->sym64_prob.p + nprob,
+                                       ctx->mv_work_ns.p, &ctx->n_work_ns, st));
         }
     }
     RBF_CHECK(matvec_prepare(ctx));
@@ -698,17 +728,19 @@ rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cud
 }
 
 // Cell lists by size class for the symmetric matvecs: non-empty cells with
-// ceil(points / 32) == t, t = 1..max_tpl, as (cell, 0) items in `lists`
-// (class t holds [off[t-1], off[t])), order kept within a class. flag and pos
-// are scratch of ncell + 1 entries each.
+// ceil(points / 32) == t, t = 1..max_tpl, of the problems prob_ok marks (all
+// when it is null), as (cell, 0) items in `lists` (class t holds [off[t-1],
+// off[t])), order kept within a class. flag and pos are scratch of ncell + 1
+// entries each.
 static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
-                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
-                                    cudaStream_t st)
+                                    const int32_t* pid_cell, const int32_t* prob_ok, DevArray<int32_t>& lists,
+                                    int64_t* off, int32_t* flag, int32_t* pos, cudaStream_t st)
 {
     RBF_CHECK(ensure(ctx, lists, 2 * (size_t)std::max<int64_t>(ncell, 1)));
     off[0] = 0;
     for (int t = 1; t <= max_tpl; ++t) {
-        RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, cell_start, ncell, t, flag);
+        RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, cell_start, ncell, t, pid_cell, prob_ok,
+                   flag);
         RBF_CHECK(exclusive_scan_i32(ctx, flag, pos, ncell, st));
         RBF_LAUNCH(ctx, k_scatter_cells, blocks_for(ncell, 256), 256, 0, st, ncell, flag, pos, lists.p + 2 * off[t - 1]);
         int32_t cnt = 0;
@@ -783,18 +815,37 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
     int32_t smax = 0;
     RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &smax, st));
     G.stage_max = smax;
-    // the symmetric FP32 kernel takes cells of at most 128 points (four targets per lane)
-    RBF_LAUNCH(ctx, k_cell_sizes, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, G.wcnt.p);
-    int32_t cmax = 0;
-    RBF_CHECK(reduce_max_i32(ctx, G.wcnt.p, ncell, &cmax, st));
-    G.sym = cmax <= 128;
+    // the symmetric FP32 kernel serves each problem whose inner cells hold at
+    // most 128 points (four targets per lane), the stencil kernel the others:
+    // a choice made per problem, so that it sums alike alone and in a batch
+    {
+        RBF_CHECK(ensure(ctx, G.sym_prob, 2 * (size_t)nprob));
+        int32_t* pmax = G.sym_prob.p + nprob;
+        RBF_CUDA(ctx, cudaMemsetAsync(pmax, 0, sizeof(int32_t) * nprob, st));
+        RBF_LAUNCH(ctx, k_prob_max_cell, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, G.pid_cell.p, pmax);
+        std::vector<int32_t> hmax(nprob), ok(2 * (size_t)nprob);
+        RBF_CUDA(ctx, cudaMemcpyAsync(hmax.data(), pmax, sizeof(int32_t) * nprob, cudaMemcpyDeviceToHost, st));
+        RBF_CUDA(ctx, cudaStreamSynchronize(st));
+        int64_t nsym = 0;
+        for (int b = 0; b < nprob; ++b) {
+            ok[b] = hmax[b] <= 128 ? 1 : 0;
+            ok[nprob + b] = 1 - ok[b];
+            nsym += ok[b];
+        }
+        G.sym = nsym > 0;
+        G.sym_all = nsym == nprob;
+        RBF_CUDA(ctx, cudaMemcpyAsync(G.sym_prob.p, ok.data(), sizeof(int32_t) * 2 * nprob, cudaMemcpyHostToDevice, st));
+    }
     if (G.sym) {
         // its slots are allocated here, outside the solver's graph capture
         RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
         // its cell lists by size class (order kept within a class)
         RBF_CHECK(ensure(ctx, G.tmp, std::max<int64_t>(2 * (ncell + 1), 2 * kNumSMs + 1)));
-        RBF_CHECK(build_class_lists(ctx, G.cell_start.p, ncell, 4, G.symw, G.symoff, G.tmp.p, G.tmp.p + (ncell + 1),
-                                    st));
+        RBF_CHECK(build_class_lists(ctx, G.cell_start.p, ncell, 4, G.pid_cell.p, G.sym_prob.p, G.symw, G.symoff,
+                                    G.tmp.p, G.tmp.p + (ncell + 1), st));
+        RBF_CHECK(ensure(ctx, G.work_ns, 2 * (size_t)std::max<int64_t>(G.n_work, 1)));
+        RBF_CHECK(select_work_into(ctx, G.work.p, G.n_work, G.pid_cell.p, G.sym_prob.p + nprob, G.work_ns.p,
+                                   &G.n_work_ns, st));
     }
     // subdomain lists in inner positions
     if (ctx->rasm_ready) {
@@ -940,6 +991,20 @@ rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t 
 {
     ctx->al.on = false;
     RBF_CHECK(select_work(ctx, ctx->mv_work.p, ctx->n_work, ctx->pid_cell.p, active, ctx->al.w64, &ctx->al.n64, st));
+    if (ctx->sym64) {   // the symmetric FP64 kernel's class lists and the other problems' stencil items
+        RBF_CHECK(ensure(ctx, ctx->al.sym64w, 2 * (size_t)std::max<int64_t>(ctx->sym64off[5], 1)));
+        ctx->al.sym64off[0] = 0;
+        for (int t = 1; t <= 5; ++t) {
+            int64_t got = 0;
+            RBF_CHECK(select_work_into(ctx, ctx->sym64w.p + 2 * ctx->sym64off[t - 1],
+                                       ctx->sym64off[t] - ctx->sym64off[t - 1], ctx->pid_cell.p, active,
+                                       ctx->al.sym64w.p + 2 * ctx->al.sym64off[t - 1], &got, st));
+            ctx->al.sym64off[t] = ctx->al.sym64off[t - 1] + got;
+        }
+        RBF_CHECK(ensure(ctx, ctx->al.w64ns, 2 * (size_t)std::max<int64_t>(ctx->n_work_ns, 1)));
+        RBF_CHECK(select_work_into(ctx, ctx->mv_work_ns.p, ctx->n_work_ns, ctx->pid_cell.p, active, ctx->al.w64ns.p,
+                                   &ctx->al.n64ns, st));
+    }
     if (ctx->inner_on)
         RBF_CHECK(select_work(ctx, ctx->in.work.p, ctx->in.n_work, ctx->in.pid_cell.p, active, ctx->al.w32,
                               &ctx->al.n32, st));
@@ -956,6 +1021,9 @@ rbf_status build_active_lists(rbf_ctx* ctx, const int32_t* active, cudaStream_t 
                                        G.pid_cell.p, active, ctx->al.symw.p + 2 * ctx->al.symoff[t - 1], &got, st));
             ctx->al.symoff[t] = ctx->al.symoff[t - 1] + got;
         }
+        RBF_CHECK(ensure(ctx, ctx->al.w32ns, 2 * (size_t)std::max<int64_t>(G.n_work_ns, 1)));
+        RBF_CHECK(select_work_into(ctx, G.work_ns.p, G.n_work_ns, G.pid_cell.p, active, ctx->al.w32ns.p,
+                                   &ctx->al.n32ns, st));
     }
     const int64_t nsub = ctx->nsub;
     RBF_CHECK(ensure(ctx, ctx->al.flag, std::max<int64_t>(nsub, 1)));

@@ -77,9 +77,15 @@ struct Prob {
 // subdomain lists re-indexed into that order.
 struct InnerGrid {
     bool ready = false;
-    bool sym = false;          // every cell holds at most 128 points: the symmetric FP32 kernel applies
+    // The symmetric FP32 kernel serves each problem whose inner cells hold at
+    // most 128 points; the stencil kernel serves the others.
+    bool sym = false;          // ... some problem
+    bool sym_all = false;      // ... every problem
+    rbf::DevArray<int32_t> sym_prob;   // per problem: 1 symmetric kernel; then 1 stencil kernel
     rbf::DevArray<int32_t> symw;   // its (cell, 0) items, non-empty cells by size class ceil(points / 32)
     int64_t symoff[5] = {0, 0, 0, 0, 0};   // class t holds items [symoff[t-1], symoff[t])
+    rbf::DevArray<int32_t> work_ns;   // stencil kernel items of the other problems
+    int64_t n_work_ns = 0;
     double ri_sigmas = 0.0;
     int tile = 64;
     int stage_max = 0;
@@ -160,8 +166,12 @@ struct rbf_ctx {
     InnerGrid in;                  // mixed form: FP32 inner grid (built on demand by the solvers)
     bool inner_on = false;         // the FP32 operators and hand-offs use the inner grid
     int sym_mode = 0;              // inner FP32 operator: 0 symmetric kernel when the grid allows, 1 stencil kernel
-    bool sym64 = false;            // the symmetric FP64 matvec applies (3 x 3 stencil, cells of <= 160 points)
-    int sym64_mode = 0;            // FP64 matvec: 0 symmetric kernel when it applies, 1 stencil kernel
+    bool sym64 = false;            // the symmetric FP64 matvec serves some problem (3 x 3 stencil, cells <= 160 points)
+    bool sym64_all = false;        // ... every problem
+    rbf::DevArray<int32_t> sym64_prob;   // per problem: 1 symmetric kernel; then 1 stencil kernel
+    rbf::DevArray<int32_t> mv_work_ns;   // stencil kernel items of the problems the symmetric one does not serve
+    int64_t n_work_ns = 0;
+    int sym64_mode = 1;            // FP64 matvec: 0 symmetric kernel where it applies (from the next binning), 1 stencil kernel
     rbf::DevArray<int32_t> sym64w;    // its (cell, 0) items by size class ceil(points / 32) = 1..5
     int64_t sym64off[6] = {0, 0, 0, 0, 0, 0};
     rbf::DevArray<double> sym64_slots;   // its row slot and four column slots per point
@@ -225,9 +235,10 @@ struct rbf_ctx {
     // the full lists, so every problem's sums run in the same order.
     struct ActiveLists {
         bool on = false;
-        rbf::DevArray<int32_t> w64, w32, sub, flag, pos, symw;
-        int64_t n64 = 0, n32 = 0, nsub = 0;
+        rbf::DevArray<int32_t> w64, w32, sub, flag, pos, symw, sym64w, w64ns, w32ns;
+        int64_t n64 = 0, n32 = 0, nsub = 0, n64ns = 0, n32ns = 0;
         int64_t symoff[5] = {0, 0, 0, 0, 0};
+        int64_t sym64off[6] = {0, 0, 0, 0, 0, 0};
     } al;
 };
 

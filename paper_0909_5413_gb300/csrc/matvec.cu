@@ -323,13 +323,16 @@ __global__ void __launch_bounds__(kSymWarps * 32, TPL == 1 ? 6 : (TPL == 2 ? 5 :
 
 // y_p = row slot + the four column slots in the order of d (a missing
 // backward neighbour's slot holds zero); the slots already carry the
-// normalisation. Points of masked problems are left alone.
+// normalisation. Points of masked problems, and of problems the symmetric
+// kernel does not serve (served[b] == 0), are left alone.
 __global__ void k_sym_gather(const float* __restrict__ rowslot, const float* __restrict__ colslot, int64_t n,
-                             const int32_t* __restrict__ pid, const int32_t* __restrict__ active, float* __restrict__ y)
+                             const int32_t* __restrict__ pid, const int32_t* __restrict__ active,
+                             const int32_t* __restrict__ served, float* __restrict__ y)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    if (active && !active[pid[p]]) return;
+    const int pb = pid[p];
+    if ((active && !active[pb]) || !served[pb]) return;
     y[p] = (((rowslot[p] + colslot[p]) + colslot[n + p]) + colslot[2 * n + p]) + colslot[3 * n + p];
 }
 
@@ -553,14 +556,16 @@ __global__ void __launch_bounds__(kSym64Warps * 32)
 }
 
 // y_p = row slot + the four column slots in the order of d (each already
-// carrying the normalisation). Points of masked problems are left alone.
+// carrying the normalisation), for the points of the problems the symmetric
+// kernel serves; points of masked problems are left alone.
 __global__ void k_sym64_gather(const double* __restrict__ rowslot, const double* __restrict__ colslot, int64_t n,
                                const int32_t* __restrict__ pid, const int32_t* __restrict__ active,
-                               double* __restrict__ y)
+                               const int32_t* __restrict__ served, double* __restrict__ y)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    if (active && !active[pid[p]]) return;
+    const int pb = pid[p];
+    if ((active && !active[pb]) || !served[pb]) return;   // served: the problems of the symmetric kernel
     y[p] = (((rowslot[p] + colslot[p]) + colslot[n + p]) + colslot[2 * n + p]) + colslot[3 * n + p];
 }
 
@@ -635,7 +640,7 @@ rbf_status launch_f32(rbf_ctx* ctx, MvParams P, int64_t nwork, const float* w, f
 
 bool inner_sym_params(rbf_ctx* ctx, MvParams* P, const int32_t** cells, int64_t* ncells)
 {
-    if (!ctx->inner_on || !ctx->in.sym || ctx->sym_mode == 1) return false;
+    if (!ctx->inner_on || !ctx->in.sym_all || ctx->sym_mode == 1) return false;
     const InnerGrid& G = ctx->in;
     *P = mv_params(ctx);
     P->loc = G.loc.p;
@@ -670,8 +675,9 @@ rbf_status matvec_prepare(rbf_ctx* ctx)
 
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
 {
-    if (ctx->sym64 && ctx->sym64_mode == 0 && !ctx->al.on) {
-        // each neighbouring pair of cells once, then the fixed-order gather
+    if (ctx->sym64 && ctx->sym64_mode == 0) {
+        // each neighbouring pair of cells once, then the fixed-order gather, for
+        // the problems the symmetric kernel serves; the stencil kernel for the others
         const int64_t n = ctx->n;
         if (ctx->sym64_slots.count < (size_t)(5 * n))
             return fail(ctx, RBF_ERR_STATE, "symmetric FP64 matvec: slots not allocated");
@@ -679,10 +685,12 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
         double* rowslot = ctx->sym64_slots.p;
         double* colslot = rowslot + n;
         const size_t smem = sizeof(Sym64Warp) * kSym64Warps;
+        const int32_t* lists = ctx->al.on ? ctx->al.sym64w.p : ctx->sym64w.p;
+        const int64_t* off = ctx->al.on ? ctx->al.sym64off : ctx->sym64off;
         for (int t = 1; t <= 5; ++t) {
-            const int64_t cnt = ctx->sym64off[t] - ctx->sym64off[t - 1];
+            const int64_t cnt = off[t] - off[t - 1];
             if (cnt == 0) continue;
-            const int32_t* cl = ctx->sym64w.p + 2 * ctx->sym64off[t - 1];
+            const int32_t* cl = lists + 2 * off[t - 1];
             const unsigned nb = blocks_for(cnt, kSym64Warps);
             switch (t) {
             case 1: RBF_LAUNCH(ctx, k_matvec_f64_sym<1>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n); break;
@@ -692,8 +700,12 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
             default: RBF_LAUNCH(ctx, k_matvec_f64_sym<5>, nb, kSym64Warps * 32, smem, st, P, cl, cnt, w, rowslot, colslot, n);
             }
         }
-        RBF_LAUNCH(ctx, k_sym64_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active, y);
-        return RBF_OK;
+        RBF_LAUNCH(ctx, k_sym64_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active,
+                   ctx->sym64_prob.p, y);
+        if (ctx->sym64_all) return RBF_OK;
+        MvParams Q = mv_params(ctx);
+        Q.work = ctx->al.on ? ctx->al.w64ns.p : ctx->mv_work_ns.p;
+        return dispatch_f64(ctx, Q, ctx->al.on ? ctx->al.n64ns : ctx->n_work_ns, w, y, st);
     }
     if (ctx->al.on) {   // batched solve: only the work items of active problems
         MvParams P = mv_params(ctx);
@@ -775,7 +787,19 @@ rbf_status matvec_f32_raw(rbf_ctx* ctx, const float2*, const float* w, float* y,
             default: RBF_LAUNCH(ctx, k_matvec_f32_sym<4>, nb, kSymWarps * 32, 0, st, P, cl, cnt, w, rowslot, colslot, n);
             }
         }
-        RBF_LAUNCH(ctx, k_sym_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active, y);
+        RBF_LAUNCH(ctx, k_sym_gather, blocks_for(n, 256), 256, 0, st, rowslot, colslot, n, ctx->pid.p, P.active,
+                   G.sym_prob.p, y);
+        if (!G.sym_all) {   // the stencil kernel for the problems the symmetric one does not serve
+            P.work = ctx->al.on ? ctx->al.w32ns.p : G.work_ns.p;
+            const int64_t nns = ctx->al.on ? ctx->al.n32ns : G.n_work_ns;
+            if (nns > 0) {
+                switch (tile) {
+                case 32: RBF_CHECK(launch_f32<32>(ctx, P, nns, w, y, st)); break;
+                case 64: RBF_CHECK(launch_f32<64>(ctx, P, nns, w, y, st)); break;
+                default: RBF_CHECK(launch_f32<128>(ctx, P, nns, w, y, st)); break;
+                }
+            }
+        }
     } else if (nwork > 0) {
         switch (tile) {
         case 32: RBF_CHECK(launch_f32<32>(ctx, P, nwork, w, y, st)); break;

@@ -34,9 +34,10 @@ def host(t):
     return t.cpu().numpy()
 
 
-def setup(rbf, probs, factor_precision=0):
+def setup(rbf, probs, factor_precision=0, sym64=0):
     xy, f, ptr, params, rasm = rbf.batch_arrays(probs, factor_precision=factor_precision)
     ctx = rbf.Context(0)
+    rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, sym64)
     rbf.rbf_bin_batch(ctx.handle, dev(xy), ptr, params)
     rbf.rbf_rasm_setup_batch(ctx.handle, rasm)
     return ctx, xy, f, ptr
@@ -95,8 +96,42 @@ def test_batch_matvec_and_rasm_per_problem(rbf):
     ctx.close()
 
 
-def solve_batch(rbf, probs, mixed=False, repeat=1):
-    ctx, xy, f, ptr = setup(rbf, probs, factor_precision=1 if mixed else 0)
+@pytest.mark.parametrize("sym64", [1, 0])
+def test_batch_matvec_kernel_choice_is_per_problem(rbf, sym64):
+    """With the symmetric FP64 matvec enabled it serves problems with cells as
+    wide as r_c holding at most 160 points; a crowded problem (h/sigma = 0.6,
+    about 205 points a cell) and one with cells of r_c / 2 take the stencil
+    kernel. In one batch each problem gets the same bits as alone, and the
+    oracle's values; likewise with the stencil kernel throughout."""
+    probs = [W.lattice_problem(24, 0.9, seed=71), W.lattice_problem(20, 0.6, seed=72),
+             W.lattice_problem(28, 0.85, seed=73), W.lattice_problem(17, 1.0, seed=74)]
+    cells = [0.0, 0.0, 0.5 * probs[2].cutoff, 0.0]
+    xy, f, ptr, params, rasm = rbf.batch_arrays(probs)
+    for b, c in enumerate(cells):
+        params[b].cell_size = c
+    ctx = rbf.Context(0)
+    rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, sym64)
+    rbf.rbf_bin_batch(ctx.handle, dev(xy), ptr, params)
+    v = np.random.default_rng(8).standard_normal(ptr[-1])
+    y = torch.empty(ptr[-1], dtype=torch.float64, device="cuda")
+    rbf.rbf_matvec(ctx.handle, dev(v), y)
+    y = host(y)
+    ctx.close()
+    for b, p in enumerate(probs):
+        lo, hi = ptr[b], ptr[b + 1]
+        c1 = rbf.Context(0)
+        rbf.rbf_set_option(c1.handle, rbf.RBF_OPT_SYMMETRIC_F64, sym64)
+        rbf.rbf_bin_batch(c1.handle, dev(p.xy), [0, p.n], [params[b]])
+        y1 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        rbf.rbf_matvec(c1.handle, dev(v[lo:hi]), y1)
+        c1.close()
+        np.testing.assert_array_equal(host(y1), y[lo:hi])
+        ref = O.matvec_cutoff(p.xy, v[lo:hi], p.sigma, p.cutoff)
+        assert np.max(np.abs(y[lo:hi] - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def solve_batch(rbf, probs, mixed=False, repeat=1, sym64=0):
+    ctx, xy, f, ptr = setup(rbf, probs, factor_precision=1 if mixed else 0, sym64=sym64)
     sp = rbf.RbfSolveParams(1e-13, 30, 20000, int(mixed), 60, 1e-5)
     outs = []
     for _ in range(repeat):
@@ -128,6 +163,21 @@ def test_batch_result_independent_of_the_mix(rbf):
     for b in (1, 4, 6):
         _, _, (wa,), _ = solve_batch(rbf, [probs[b]])
         np.testing.assert_array_equal(wa, w1[ptr[b]:ptr[b + 1]])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_with_symmetric_f64_matvec(rbf, mixed):
+    """The symmetric FP64 matvec inside the solver (captured cycles, batch
+    compaction): every problem converges and gets the same bits alone as in
+    the batch."""
+    probs = small_batch()[2:7]
+    st, infos, (w,), ptr = solve_batch(rbf, probs, mixed, sym64=1)
+    assert st == 0
+    for b, p in enumerate(probs):
+        assert infos[b].status == 0 and infos[b].relres <= 1e-13, infos[b].as_dict()
+    for b in (0, 3, 4):
+        _, _, (wa,), _ = solve_batch(rbf, [probs[b]], mixed, sym64=1)
+        np.testing.assert_array_equal(wa, w[ptr[b]:ptr[b + 1]])
 
 
 def test_single_solver_equals_batch_of_one(rbf):

@@ -157,11 +157,14 @@ def test_eval_matches_oracle_and_matvec(rbf):
     y = torch.empty(p.n, dtype=torch.float64, device="cuda")
     rbf.rbf_eval(ctx.handle, dev(p.xy), p.n, dev(w), s2)
     rbf.rbf_matvec(ctx.handle, dev(w), y)
-    assert np.max(np.abs(host(s2) - host(y))) <= 1e-14 * np.max(np.abs(host(y)))
-    rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, 0)
-    rbf.rbf_matvec(ctx.handle, dev(w), y)
     np.testing.assert_array_equal(host(s2), host(y))
     ctx.close()
+    c2 = rbf.Context(0)
+    rbf.rbf_set_option(c2.handle, rbf.RBF_OPT_SYMMETRIC_F64, 1)
+    c2.bin(dev(p.xy), cfg)
+    rbf.rbf_matvec(c2.handle, dev(w), y)
+    assert np.max(np.abs(host(s2) - host(y))) <= 1e-14 * np.max(np.abs(host(y)))
+    c2.close()
 
 
 def test_eval_reproduces_data_and_approximates_franke(rbf):

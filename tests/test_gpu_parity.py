@@ -36,8 +36,10 @@ def host(t):
     return t.cpu().numpy()
 
 
-def make_ctx(rbf, xy, sigma, rc, cell=0.0, normalized=False):
+def make_ctx(rbf, xy, sigma, rc, cell=0.0, normalized=False, sym64=False):
     ctx = rbf.Context(0)
+    if sym64:   # the symmetric FP64 matvec (chosen at binning)
+        rbf.rbf_set_option(ctx.handle, rbf.RBF_OPT_SYMMETRIC_F64, 1)
     xyd = dev(xy)
     rbf.rbf_bin(ctx.handle, xyd, xy.shape[0], rbf.RbfParams(sigma, rc, cell, int(normalized)))
     return ctx, xyd
@@ -593,7 +595,7 @@ def test_symmetric_f64_matvec(rbf, n_side, ratio, normalized):
     directions, column sums gathered in a fixed order) against the stencil
     kernel and the oracle, element by element; and the same bits on a second call."""
     p = W.lattice_problem(n_side, ratio, seed=600 + n_side)
-    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff, 0.0, normalized)
+    ctx, _ = make_ctx(rbf, p.xy, p.sigma, p.cutoff, 0.0, normalized, sym64=True)
     w = np.random.default_rng(7).standard_normal(p.n)
     ys, yt, y2 = (torch.empty(p.n, dtype=torch.float64, device="cuda") for _ in range(3))
     rbf.rbf_matvec(ctx.handle, dev(w), ys)
@@ -613,7 +615,7 @@ def test_symmetric_f64_matvec_uneven_points(rbf):
     rng = np.random.default_rng(12)
     xy = np.ascontiguousarray(rng.uniform(-1.0, 1.0, size=(9000, 2)))
     sigma, rc = 0.015, 0.129
-    ctx, _ = make_ctx(rbf, xy, sigma, rc)
+    ctx, _ = make_ctx(rbf, xy, sigma, rc, sym64=True)
     w = rng.standard_normal(xy.shape[0])
     y = torch.empty(xy.shape[0], dtype=torch.float64, device="cuda")
     rbf.rbf_matvec(ctx.handle, dev(w), y)
