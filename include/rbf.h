@@ -429,13 +429,23 @@ enum {
      * faster form on GB300: the FP64 pipe, which carries one FMA per directed
      * pair in both, bounds the symmetric form. */
     RBF_OPT_SYMMETRIC_F64 = 5,
-    /* Polls of a grid-barrier wait of the fused step before it gives up: the
-     * step then ends, and the solve returns RBF_ERR_TIMEOUT (value >= 1;
-     * default 2^23, about a second). */
+    /* Polls of a device-side wait before it gives up -- a grid barrier of the
+     * fused step, or the arrival of a bulk copy in a Gram-Schmidt pass: the
+     * kernel then ends (once its copies in flight have landed), and the solve
+     * returns RBF_ERR_TIMEOUT (value >= 1; default 2^23, about a second). */
     RBF_OPT_BARRIER_SPIN_LIMIT = 3,
     /* Check of the timeout path: 1 makes every barrier of the fused step wait
      * for one block more than the grid has, so that every wait runs out. */
-    RBF_OPT_BARRIER_EXTRA_BLOCK = 4
+    RBF_OPT_BARRIER_EXTRA_BLOCK = 4,
+    /* 1 (default): the FP32 Gram-Schmidt passes of the mixed form stream the
+     * basis vectors through shared memory by bulk asynchronous copies (several
+     * vectors in flight per chunk); 0: each thread loads them into registers.
+     * The results are the same bits. */
+    RBF_OPT_STREAM_GS = 6,
+    /* Check of the timeout path: 1 makes every bulk-copy wait of those passes
+     * wait on a barrier that no copy completes (and copy nothing), so that it
+     * runs out and the solve returns RBF_ERR_TIMEOUT. */
+    RBF_OPT_STREAM_WAIT_CHECK = 7
 };
 /* Set a context option. INVALID_ARG for an unknown option or value. */
 rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value);

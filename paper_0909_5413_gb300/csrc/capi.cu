@@ -300,6 +300,14 @@ rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
         if (value != 0 && value != 1) break;
         ctx->fused_extra_block = (int)value;
         return RBF_OK;
+    case RBF_OPT_STREAM_GS:
+        if (value != 0 && value != 1) break;
+        ctx->gs_stream_mode = (int)value;
+        return RBF_OK;
+    case RBF_OPT_STREAM_WAIT_CHECK:
+        if (value != 0 && value != 1) break;
+        ctx->stream_check = (int)value;
+        return RBF_OK;
     default:
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_option: unknown option %d", option);
     }

@@ -225,7 +225,11 @@ struct rbf_ctx {
     unsigned long long fused_spin_limit = 1ull << 23;   // polls of a barrier wait before it gives up
     int fused_extra_block = 0;              // check of the timeout path: barriers wait for one block too many
     bool bgraph_off = false;                // this solve launches its cycles directly (no capture)
-    rbf::DevArray<int> fused_sync;          // barrier state (4 ints), then the solve's status word
+    rbf::DevArray<int> fused_sync;          // barrier state (4 ints), then status words: fused step, bulk copies
+    int gs_stream_mode = 1;                 // FP32 Gram-Schmidt passes: 1 basis streamed by bulk copies, 0 registers
+    bool gs_stream = false;                 // ... in the current solve
+    bool gs_stream_ready = false;           // the kernels' shared-memory attribute is set
+    int stream_check = 0;                   // 1: the bulk-copy waits wait on a barrier nothing completes
     int prof_step = -1;                     // Arnoldi step of the launches being issued (-1: none)
     unsigned bgraph_prof_mask = 0;          // profiler classes the captured graph records
     std::vector<rbf_graph_prof> bgraph_prof;   // its event pairs

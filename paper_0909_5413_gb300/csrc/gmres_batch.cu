@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "ortho.cuh"
 #include "batch.cuh"
+#include "bulk.cuh"
 #include "vecops.cuh"
 
 namespace rbf {
@@ -89,6 +90,161 @@ __global__ void __launch_bounds__(kDotThreads, 2)
         __syncthreads();
         if (threadIdx.x == 0) out[0] = ortho_block_total<T>(red, 0);
     }
+}
+
+// The FP32 passes with the basis streamed through shared memory: one block per
+// chunk keeps its x elements in registers while a thread issues bulk copies
+// of the chunk's segment of V_0, V_1, ... into kStreamStages stages (copies in
+// flight: the stages, not registers), every thread taking its elements from
+// the stage. Element for element the arithmetic and the summation order are
+// those of k_bdots / k_bupdate (and of the fused step), so the results are
+// the same bits. A stage holds the chunk widened to 16-byte boundaries
+// (V is 16-byte aligned, ldv a multiple of 4). A copy that does not arrive
+// within `spin` polls ends the pass: status = RBF_ERR_TIMEOUT, x and the
+// partial sums are left alone once the copies in flight have landed (each
+// waited for at most `spin` polls). check = 1: every wait is on a barrier that
+// no copy completes and nothing is copied (the check of that path).
+constexpr int kStreamStages = 4;
+constexpr int kStreamLd = kOrthoChunk + 4;   // floats per stage
+constexpr size_t kStreamSmem = sizeof(float) * kStreamStages * kStreamLd;
+
+struct StreamChunk {
+    int64_t b, e, b0;   // the chunk and its 16-byte aligned start
+    int off;            // b - b0
+    uint32_t bytes;     // of one copy
+};
+
+__device__ __forceinline__ StreamChunk stream_chunk(const Chunks& C, int64_t c)
+{
+    StreamChunk s;
+    s.b = C.beg[c];
+    s.e = C.end[c];
+    s.b0 = s.b & ~3LL;
+    s.off = (int)(s.b - s.b0);
+    s.bytes = (uint32_t)((((s.e + 3) & ~3LL) - s.b0) * (int64_t)sizeof(float));
+    return s;
+}
+
+// Issues the first copies; returns how many were issued (thread 0 only).
+__device__ __forceinline__ int stream_start(float* stage, uint64_t* bar, const float* V, int64_t ldv, int nv,
+                                            const StreamChunk& s, int check)
+{
+    if (threadIdx.x == 0) {
+        for (int q = 0; q <= kStreamStages; ++q) mbar_init(&bar[q], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const int npre = check ? 0 : min(nv, kStreamStages);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < npre; ++k) bulk_load(stage + k * kStreamLd, V + (int64_t)k * ldv + s.b0, s.bytes, &bar[k]);
+    return npre;
+}
+
+// After a failed wait at vector kf: record the timeout, then let the copies
+// still in flight (vectors kf .. issued - 1) land before the block exits.
+__device__ __forceinline__ void stream_abort(uint64_t* bar, int kf, int issued, int* status,
+                                             unsigned long long spin)
+{
+    if (threadIdx.x != 0) return;
+    atomicExch(status, (int)RBF_ERR_TIMEOUT);
+    for (int k = kf; k < issued; ++k) mbar_wait(&bar[k % kStreamStages], (k / kStreamStages) & 1, spin);
+}
+
+// partial_k = V_k . x over the chunk, k < nv (k_bdots for all k of a chunk).
+__global__ void __launch_bounds__(kDotThreads)
+    k_bdots_stream(const float* __restrict__ V, int64_t ldv, int nv, const float* __restrict__ x, Chunks C,
+                   const int32_t* __restrict__ active, double* __restrict__ partial, int* __restrict__ status,
+                   unsigned long long spin, int check)
+{
+    extern __shared__ __align__(128) float stream_stage[];
+    __shared__ __align__(8) uint64_t bar[kStreamStages + 1];
+    __shared__ OrthoRed red;
+    const int64_t c = blockIdx.x;
+    double* out = partial + c * 32;
+    if (!active[C.pid[c]]) {
+        if (threadIdx.x < (unsigned)nv) out[threadIdx.x] = 0.0;
+        return;
+    }
+    const StreamChunk s = stream_chunk(C, c);
+    int issued = stream_start(stream_stage, bar, V, ldv, nv, s, check);
+    float xs[kOrthoPer];
+#pragma unroll
+    for (int u = 0; u < kOrthoPer; ++u) {
+        const int64_t i = s.b + threadIdx.x + (int64_t)u * kDotThreads;
+        xs[u] = i < s.e ? x[i] : 0.f;
+    }
+    for (int k = 0; k < nv; ++k) {
+        const int q = k % kStreamStages;
+        const bool ok = mbar_wait(check ? &bar[kStreamStages] : &bar[q], (k / kStreamStages) & 1, spin);
+        if (ok) {
+            const float* v = stream_stage + q * kStreamLd + s.off;
+            float a[kOrthoPer];
+#pragma unroll
+            for (int u = 0; u < kOrthoPer; ++u) a[u] = v[threadIdx.x + u * kDotThreads];
+            ortho_warp_sum(ortho_thread_dot<float>(a, xs, s.b, s.e), red, k);
+        }
+        if (__syncthreads_or(!ok)) {
+            stream_abort(bar, k, issued, status, spin);
+            return;
+        }
+        if (threadIdx.x == 0 && k + kStreamStages < nv) {
+            fence_async_smem();
+            bulk_load(stream_stage + q * kStreamLd, V + (int64_t)(k + kStreamStages) * ldv + s.b0, s.bytes, &bar[q]);
+            ++issued;
+        }
+    }
+    if (threadIdx.x < (unsigned)nv) out[threadIdx.x] = ortho_block_total<float>(red, (int)threadIdx.x);
+}
+
+// x -= V coef (the chunk's problem's coefficients, field `field`), then
+// partial_0 = |x|^2 (k_bupdate<float, 2>).
+__global__ void __launch_bounds__(kDotThreads)
+    k_bupdate_stream(const float* __restrict__ V, int64_t ldv, int nv, GmresDev* __restrict__ gm, int field,
+                     float* __restrict__ x, Chunks C, const int32_t* __restrict__ active, double* __restrict__ partial,
+                     int* __restrict__ status, unsigned long long spin, int check)
+{
+    extern __shared__ __align__(128) float stream_stage[];
+    __shared__ __align__(8) uint64_t bar[kStreamStages + 1];
+    __shared__ OrthoCoef cf;
+    __shared__ OrthoRed red;
+    const int64_t c = blockIdx.x;
+    const int pb = C.pid[c];
+    double* out = partial + c * 32;
+    if (!active[pb]) {
+        if (threadIdx.x == 0) out[0] = 0.0;
+        return;
+    }
+    if (threadIdx.x < (unsigned)nv) ortho_coef_set(cf, (int)threadIdx.x, field_ptr(gm[pb], field)[threadIdx.x]);
+    const StreamChunk s = stream_chunk(C, c);
+    int issued = stream_start(stream_stage, bar, V, ldv, nv, s, check);   // its block barrier publishes cf
+    DF xl[kOrthoPer];
+    ortho_load_x<float>(xl, x, s.b, s.e);
+    for (int k = 0; k < nv; ++k) {
+        const int q = k % kStreamStages;
+        const bool ok = mbar_wait(check ? &bar[kStreamStages] : &bar[q], (k / kStreamStages) & 1, spin);
+        if (ok) {
+            const float* v = stream_stage + q * kStreamLd + s.off;
+            const float ch = cf.hi[k], cl = cf.lo[k];
+#pragma unroll
+            for (int u = 0; u < kOrthoPer; ++u)
+                if (s.b + threadIdx.x + (int64_t)u * kDotThreads < s.e)
+                    ortho_axpy(xl[u], ch, cl, v[threadIdx.x + u * kDotThreads]);
+        }
+        if (__syncthreads_or(!ok)) {
+            stream_abort(bar, k, issued, status, spin);
+            return;
+        }
+        if (threadIdx.x == 0 && k + kStreamStages < nv) {
+            fence_async_smem();
+            bulk_load(stream_stage + q * kStreamLd, V + (int64_t)(k + kStreamStages) * ldv + s.b0, s.bytes, &bar[q]);
+            ++issued;
+        }
+    }
+    float xs[kOrthoPer];
+    ortho_store_x<float>(xl, xs, x, s.b, s.e);
+    ortho_warp_sum(ortho_thread_dot<float>(xs, xs, s.b, s.e), red, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = ortho_block_total<float>(red, 0);
 }
 
 // r = f - t over one chunk (FP64) and |r|^2 partial sums.
@@ -338,6 +494,22 @@ struct BatchWork {
     template <int MODE, class T>
     rbf_status mdot(const T* V, int64_t ldv, int nv, T* x, int field_in, int field_out, const int32_t* mask)
     {
+        if constexpr (sizeof(T) == 4) {
+            if (ctx->gs_stream && MODE != 1) {   // the basis streamed by bulk copies
+                int* status = ctx->fused_sync.p + 5;
+                const int check = ctx->stream_check;
+                if (MODE == 0)
+                    RBF_LAUNCH(ctx, k_bdots_stream, (unsigned)C.nc, kDotThreads, kStreamSmem, st, V, ldv, nv,
+                               (const T*)x, C, mask, partial, status, ctx->fused_spin_limit, check);
+                else
+                    RBF_LAUNCH(ctx, k_bupdate_stream, (unsigned)C.nc, kDotThreads, kStreamSmem, st, V, ldv, nv, gm,
+                               field_in, x, C, mask, partial, status, ctx->fused_spin_limit, check);
+                const int nout = MODE == 2 ? 1 : nv;
+                RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out,
+                           mask);
+                return RBF_OK;
+            }
+        }
         if (MODE == 0)
             RBF_LAUNCH(ctx, (k_bdots<T>), (unsigned)(C.nc * nv), kDotThreads, 0, st, V, ldv, nv, (const T*)x, C,
                        mask, partial);
@@ -624,9 +796,17 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
                                            (1u << RBF_PROF_RASM_APPLY) | (1u << RBF_PROF_ORTHO);
         const bool profiling = ctx->prof && (ctx->prof_mask & kCycleClasses);
         fused_ok = mixed && nprob > 1 && !profiling && fused_step_applies(ctx);
-        if (fused_ok) {
+        if (mixed) {   // the fused step's barrier state and the status words of the cycle's waits
             RBF_CHECK(ensure(ctx, ctx->fused_sync, 8));
             RBF_CUDA(ctx, cudaMemsetAsync(ctx->fused_sync.p, 0, 8 * sizeof(int), st));
+        }
+        ctx->gs_stream = mixed && ctx->gs_stream_mode != 0;
+        if (ctx->gs_stream && !ctx->gs_stream_ready) {   // before any capture
+            RBF_CUDA(ctx, cudaFuncSetAttribute(k_bdots_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kStreamSmem));
+            RBF_CUDA(ctx, cudaFuncSetAttribute(k_bupdate_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kStreamSmem));
+            ctx->gs_stream_ready = true;
         }
         B.fused = fused_ok && (ctx->fused_mode == 1 || nprob <= kFusedTail);
     }
@@ -707,14 +887,17 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
                        ctx->inner_on ? (const int32_t*)ctx->in.perm.p : nullptr, Vf);
             RBF_CHECK(run_cycle<float>(B, Vf, ldv, m, uf, tf, w));
         }
-        int fused_status = 0;
-        if (B.fused)
-            RBF_CUDA(ctx, cudaMemcpyAsync(&fused_status, ctx->fused_sync.p + 4, sizeof(int), cudaMemcpyDeviceToHost,
+        int cycle_status[2] = {0, 0};   // the fused step's grid barriers; the bulk copies of the passes
+        if (mixed)
+            RBF_CUDA(ctx, cudaMemcpyAsync(cycle_status, ctx->fused_sync.p + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                           st));
         RBF_CHECK(read_stat());
-        if (fused_status != 0)
-            return fail(ctx, (rbf_status)fused_status,
+        if (cycle_status[0] != 0)
+            return fail(ctx, (rbf_status)cycle_status[0],
                         "rbf_solve_batch: a grid barrier of the fused Arnoldi step gave up waiting");
+        if (cycle_status[1] != 0)
+            return fail(ctx, (rbf_status)cycle_status[1],
+                        "rbf_solve_batch: a bulk copy of a Gram-Schmidt pass did not arrive in time");
         if (!ctx->bgraph_prof.empty()) {
             int steps_run = 0;
             for (int b = 0; b < nprob; ++b)

@@ -85,17 +85,16 @@ __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx
                                          float* __restrict__ colout, float knorm)
 {
     const int dnp = (dn + 31) & ~31;
+    float4* row = reinterpret_cast<float4*>(&S.T[lane * kSymTld]);
     for (int c0 = 0; c0 < dnp; c0 += 32) {
-        float col[32];
-        if (COL) {
-#pragma unroll
-            for (int s = 0; s < 32; ++s) col[s] = 0.f;
-        }
 #pragma unroll
         for (int s = 0; s < 32; s += 4) {
             const float4 X = *reinterpret_cast<const float4*>(&S.sx[c0 + s]);
             const float4 Y = *reinterpret_cast<const float4*>(&S.sy[c0 + s]);
             const float4 Wv = *reinterpret_cast<const float4*>(&S.sw[c0 + s]);
+            // this lane's column terms of sources s..s+3, summed over its targets
+            // in order; stored to its row of the transpose as soon as complete
+            float2 c01 = make_float2(0.f, 0.f), c23 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < TPL; ++t) {
                 const float2 dx0 = f2_sub(tx[t], make_float2(X.x, X.y)), dy0 = f2_sub(ty[t], make_float2(Y.x, Y.y));
@@ -108,19 +107,13 @@ __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx
                 acc2[t] = f2_fma(e1, make_float2(Wv.z, Wv.w), acc2[t]);
                 if (COL) {
                     const float2 w2 = make_float2(wt[t], wt[t]);
-                    const float2 c01 = f2_fma(e0, w2, make_float2(col[s], col[s + 1]));
-                    const float2 c23 = f2_fma(e1, w2, make_float2(col[s + 2], col[s + 3]));
-                    col[s] = c01.x;
-                    col[s + 1] = c01.y;
-                    col[s + 2] = c23.x;
-                    col[s + 3] = c23.y;
+                    c01 = f2_fma(e0, w2, c01);
+                    c23 = f2_fma(e1, w2, c23);
                 }
             }
+            if (COL) row[s >> 2] = make_float4(c01.x, c01.y, c23.x, c23.y);
         }
         if (COL) {
-            float4* row = reinterpret_cast<float4*>(&S.T[lane * kSymTld]);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) row[k] = make_float4(col[4 * k], col[4 * k + 1], col[4 * k + 2], col[4 * k + 3]);
             __syncwarp();
             float sum = 0.f;
 #pragma unroll 8
