@@ -87,8 +87,12 @@ __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx
     const int dnp = (dn + 31) & ~31;
     float4* row = reinterpret_cast<float4*>(&S.T[lane * kSymTld]);
     for (int c0 = 0; c0 < dnp; c0 += 32) {
+        // steps of four sources up to the last real one (the padding sources
+        // would add exact zeros; the transpose's columns past dn are not stored)
+        const int smax = dn - c0;
 #pragma unroll
         for (int s = 0; s < 32; s += 4) {
+            if (s >= smax) break;
             const float4 X = *reinterpret_cast<const float4*>(&S.sx[c0 + s]);
             const float4 Y = *reinterpret_cast<const float4*>(&S.sy[c0 + s]);
             const float4 Wv = *reinterpret_cast<const float4*>(&S.sw[c0 + s]);
