@@ -94,23 +94,28 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic, note: 
 # FP32 matvec roofline (the inner solves of the mixed form). Every in-cutoff
 # pair at the inner cutoff needs one exp2 on the SFU (MUFU.EX2), which issues
 # 16 results per SM per clock: 152 x 16 x 2.07 GHz = 5.03 T pairs/s. The
-# kernel evaluates every candidate of its 3 x 3 stencil (no mask), so its
-# useful rate is in-cutoff pairs (rbf_count_pairs on the inner grid) over the
-# launch time, and candidates evaluated are reported beside it.
+# symmetric kernel evaluates each neighbouring cell pair once, every pair of
+# the two cells (no mask), so its useful rate is in-cutoff pairs
+# (rbf_count_pairs on the inner grid) over the launch time (the symmetric
+# kernel and its gather); the 3 x 3 stencil's candidate count is reported
+# beside it.
 MUFU_PEAK_PAIRS = SM_COUNT * 16 * SM_CLOCK_HZ
-MATVEC_F32_REV = "inner-4src-v4"
-# DRAM read + write of one launch on the 1024 x 1024 lattice's inner grid (ncu, this revision)
-MATVEC_F32_TRAFFIC_1M = {"inner-4src-v4": 17_079_040}
+MATVEC_F32_REV = "sym-early-exit-v3"
+MATVEC_F32_KERNEL = "k_matvec_f32_sym<TPL> + k_sym_gather"
+# DRAM read + write of one launch (the symmetric kernel of the 33-64 point
+# cells, 84,684,800 B, and the gather, 107,271,424 B) on the 2048 x 2048
+# lattice's inner grid (ncu, this revision), and that lattice's N
+MATVEC_F32_TRAFFIC = {"sym-early-exit-v3": (191_956_224, 4_194_304)}
 
 
 def f32_matvec_roofline(pairs: int, cand: int, avg_s: float, launches: int, traffic, grid: str) -> dict:
     rate = pairs / avg_s
-    return {"kernel": "k_matvec_f32v2", "bound": "alu", "achieved": rate / 1e12, "peak": MUFU_PEAK_PAIRS / 1e12,
+    return {"kernel": MATVEC_F32_KERNEL, "bound": "alu", "achieved": rate / 1e12, "peak": MUFU_PEAK_PAIRS / 1e12,
             "unit": "Tpair/s", "frac": rate / MUFU_PEAK_PAIRS, "traffic": traffic,
             "peak_note": ("SFU: one ex2 per in-cutoff pair at the inner cutoff, 152 SMs x 16 MUFU.EX2/clk x 2.07 GHz "
                           "(derived from unit counts and clocks)"),
-            "kernel_rev": MATVEC_F32_REV, "pairs_per_launch": pairs, "candidates_per_launch": cand,
-            "candidates_per_pair": cand / max(pairs, 1), "candidate_rate_t_per_s": cand / avg_s / 1e12,
+            "kernel_rev": MATVEC_F32_REV, "pairs_per_launch": pairs, "stencil_candidates_per_launch": cand,
+            "stencil_candidates_per_pair": cand / max(pairs, 1),
             "avg_launch_ms": avg_s * 1e3, "launches": launches, "grid": grid}
 
 
@@ -465,13 +470,15 @@ def run_ours(args, ws, rank, local):
         pairs_in = rbf.rbf_count_pairs(h, 1 if inner else 0)
         cand = rbf.rbf_count_candidates(h, 1 if inner else 0)
         traffic = None
-        if inner and args.inner_cutoff == 6.1 and not args.tune and MATVEC_F32_REV in MATVEC_F32_TRAFFIC_1M:
-            # scaled from the 1024 x 1024 capture by the candidates processed
-            traffic = MATVEC_F32_TRAFFIC_1M[MATVEC_F32_REV] * p.n / 1048576.0
+        if inner and args.inner_cutoff == 6.1 and not args.tune and MATVEC_F32_REV in MATVEC_F32_TRAFFIC:
+            # scaled from the 2048 x 2048 capture by the points processed
+            t_cap, n_cap = MATVEC_F32_TRAFFIC[MATVEC_F32_REV]
+            traffic = t_cap * p.n / n_cap
         roofline = f32_matvec_roofline(pairs_in, cand, t_mv / n_mv / 1e3, n_mv, traffic,
                                        f"inner, cells of {args.inner_cutoff} sigma" if inner else "cells of side r_c")
         if traffic is not None:
-            roofline["traffic_note"] = "ncu DRAM read + write of one launch on the 1024 x 1024 lattice x N / 2^20"
+            roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
+                                        "2048 x 2048 lattice x N / 4,194,304")
     elif n_mv:
         default_cfg = (cfg.cell_size in (0.0, p.cutoff)) and cfg.tile_f64 in (0, 128)
         traffic = MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if default_cfg else None
@@ -479,7 +486,8 @@ def run_ours(args, ws, rank, local):
             traffic = traffic * p.n / 1048576.0
         roofline = f64_matvec_roofline(pairs, t_mv / n_mv / 1e3, n_mv, traffic)
         if traffic is not None:
-            roofline["traffic_note"] = "ncu DRAM read + write of one launch on the 1024 x 1024 lattice x N / 2^20"
+            roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
+                                        "2048 x 2048 lattice x N / 4,194,304")
     # the FP64 matvec (outer residuals of the mixed form) from the breakdown step
     n64, t64 = prof_all[rbf.RBF_PROF_MATVEC_F64]
     if mode == "mixed" and n64:

@@ -642,7 +642,8 @@ rbf_status run_cycle(BatchWork& B, T* V, int64_t ldv, int m, T* u, T* t, double*
     return RBF_OK;
 }
 
-// Clears the matvec / apply mask and the inner-grid switch when the batched solve returns.
+// Clears the matvec / apply mask, the inner-grid switch and the streamed
+// passes' switch when the batched solve returns.
 struct MaskGuard {
     rbf_ctx* ctx;
     ~MaskGuard()
@@ -650,6 +651,7 @@ struct MaskGuard {
         ctx->active_mask = nullptr;
         ctx->inner_on = false;
         ctx->al.on = false;
+        ctx->gs_stream = false;
     }
 };
 

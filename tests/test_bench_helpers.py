@@ -40,7 +40,13 @@ def test_f32_roofline_counts_in_cutoff_pairs_not_candidates():
     assert r["unit"] == "Tpair/s" and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(pairs / avg_s / 1e12)
     assert r["frac"] == pytest.approx(pairs / avg_s / bench.MUFU_PEAK_PAIRS)
-    assert r["candidates_per_pair"] == pytest.approx(cand / pairs)
+    assert r["stencil_candidates_per_pair"] == pytest.approx(cand / pairs)
+    assert r["kernel"] == bench.MATVEC_F32_KERNEL and r["kernel_rev"] == bench.MATVEC_F32_REV
+
+
+def test_f32_traffic_constant_is_for_the_current_revision():
+    t, n = bench.MATVEC_F32_TRAFFIC[bench.MATVEC_F32_REV]
+    assert t >= 16 * n   # at least the algorithmic 16 B per point (offsets 8, w 4, y 4)
 
 
 def test_roofline_constants():
