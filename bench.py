@@ -102,10 +102,11 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic, note: 
 MUFU_PEAK_PAIRS = SM_COUNT * 16 * SM_CLOCK_HZ
 MATVEC_F32_REV = "sym-early-exit-v3"
 MATVEC_F32_KERNEL = "k_matvec_f32_sym<TPL> + k_sym_gather"
-# DRAM read + write of one launch (the symmetric kernel of the 33-64 point
-# cells, 84,684,800 B, and the gather, 107,271,424 B) on the 2048 x 2048
-# lattice's inner grid (ncu, this revision), and that lattice's N
-MATVEC_F32_TRAFFIC = {"sym-early-exit-v3": (191_956_224, 4_194_304)}
+# DRAM read + write of one launch on the 7168 x 7168 lattice's inner grid
+# (ncu, one-pass dram__bytes metrics, this revision): the symmetric kernel of
+# the 33-64 point cells 631.8 MB + 977.3 MB (its five FP32 slots per point
+# written), the gather 1230 MB + 192.3 MB; and that lattice's N
+MATVEC_F32_TRAFFIC = {"sym-early-exit-v3": (3_031_360_000, 51_380_224)}
 
 
 def f32_matvec_roofline(pairs: int, cand: int, avg_s: float, launches: int, traffic, grid: str) -> dict:
@@ -471,14 +472,15 @@ def run_ours(args, ws, rank, local):
         cand = rbf.rbf_count_candidates(h, 1 if inner else 0)
         traffic = None
         if inner and args.inner_cutoff == 6.1 and not args.tune and MATVEC_F32_REV in MATVEC_F32_TRAFFIC:
-            # scaled from the 2048 x 2048 capture by the points processed
+            # the 7168 x 7168 capture, scaled by the points processed
             t_cap, n_cap = MATVEC_F32_TRAFFIC[MATVEC_F32_REV]
             traffic = t_cap * p.n / n_cap
         roofline = f32_matvec_roofline(pairs_in, cand, t_mv / n_mv / 1e3, n_mv, traffic,
                                        f"inner, cells of {args.inner_cutoff} sigma" if inner else "cells of side r_c")
         if traffic is not None:
             roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
-                                        "2048 x 2048 lattice x N / 4,194,304")
+                                        "7168 x 7168 lattice x N / 51,380,224; algorithmic 16 B per point plus "
+                                        "40 B per point of slots")
     elif n_mv:
         default_cfg = (cfg.cell_size in (0.0, p.cutoff)) and cfg.tile_f64 in (0, 128)
         traffic = MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if default_cfg else None
@@ -487,7 +489,8 @@ def run_ours(args, ws, rank, local):
         roofline = f64_matvec_roofline(pairs, t_mv / n_mv / 1e3, n_mv, traffic)
         if traffic is not None:
             roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
-                                        "2048 x 2048 lattice x N / 4,194,304")
+                                        "7168 x 7168 lattice x N / 51,380,224; algorithmic 16 B per point plus "
+                                        "40 B per point of slots")
     # the FP64 matvec (outer residuals of the mixed form) from the breakdown step
     n64, t64 = prof_all[rbf.RBF_PROF_MATVEC_F64]
     if mode == "mixed" and n64:

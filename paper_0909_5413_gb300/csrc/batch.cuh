@@ -29,16 +29,29 @@ struct Chunks {
     int64_t nc;
 };
 
-// Sum over problem pb's chunks, in chunk order, of partial[c * 32 + k] (one
+// Segments of a problem's chunk partials, summed one per warp and then in
+// segment order: one for up to 2047 chunks, up to kRedSeg for large problems
+// (a function of the problem's own chunk count only, so that every kernel
+// that reduces a problem's partials sums them in the same order).
+constexpr int kRedSeg = 8;
+
+__host__ __device__ __forceinline__ int breduce_segments(int nch)
+{
+    const int s = nch / 1024;
+    return s < 1 ? 1 : (s > kRedSeg ? kRedSeg : s);
+}
+
+// Sum of partial[c * 32 + k] over segment s of S of problem pb's chunks (one
 // warp; the lanes take every 32nd chunk, 8 loads issued together and added in
 // order, then a fixed shuffle tree); every lane returns the total.
-__device__ __forceinline__ double breduce_one(const double* __restrict__ partial, const Chunks& C, int pb, int k,
-                                              int lane)
+__device__ __forceinline__ double breduce_seg(const double* __restrict__ partial, const Chunks& C, int pb, int k,
+                                              int lane, int s, int S)
 {
+    const int p0 = C.cptr[pb], nch = C.cptr[pb + 1] - p0;
+    const int c_beg = p0 + (int)((int64_t)nch * s / S), c1 = p0 + (int)((int64_t)nch * (s + 1) / S);
     double a = 0.0;
     constexpr int U = 8;
-    const int c1 = C.cptr[pb + 1];
-    for (int c0 = C.cptr[pb] + lane; c0 < c1; c0 += 32 * U) {
+    for (int c0 = c_beg + lane; c0 < c1; c0 += 32 * U) {
         double p[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -51,6 +64,17 @@ __device__ __forceinline__ double breduce_one(const double* __restrict__ partial
     }
     for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
     return a;
+}
+
+// The problem's total by one warp: its segments in order (what k_breduce
+// computes with a warp per segment).
+__device__ __forceinline__ double breduce_one(const double* __restrict__ partial, const Chunks& C, int pb, int k,
+                                              int lane)
+{
+    const int S = breduce_segments(C.cptr[pb + 1] - C.cptr[pb]);
+    double t = 0.0;
+    for (int s = 0; s < S; ++s) t += breduce_seg(partial, C, pb, k, lane, s, S);
+    return t;
 }
 
 }  // namespace rbf

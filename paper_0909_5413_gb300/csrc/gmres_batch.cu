@@ -272,16 +272,27 @@ __global__ void __launch_bounds__(kDotThreads)
     if (threadIdx.x == 0) partial[c * 32] = s;
 }
 
-// Per problem (block), per vector k (warp): sum of the problem's chunk partials
-// in a fixed order, written to the field of its state.
+// Per (problem, vector k) block: the problem's chunk partials of k summed in
+// a fixed order (a warp per segment, then the segments in order; the value of
+// breduce_one), written to the field of its state.
 __global__ void k_breduce(const double* __restrict__ partial, Chunks C, int nprob, int nv, GmresDev* __restrict__ gm,
                           int field, const int32_t* __restrict__ active)
 {
-    const int pb = blockIdx.x;
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (pb >= nprob || k >= nv || !active[pb]) return;
-    const double a = breduce_one(partial, C, pb, k, lane);
-    if (lane == 0) field_ptr(gm[pb], field)[k] = a;
+    __shared__ double seg[kRedSeg];
+    const int pb = blockIdx.x / nv, k = blockIdx.x % nv;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (pb >= nprob || !active[pb]) return;   // block-uniform
+    const int S = breduce_segments(C.cptr[pb + 1] - C.cptr[pb]);
+    if (w < S) {
+        const double a = breduce_seg(partial, C, pb, k, lane, w, S);
+        if (lane == 0) seg[w] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int s = 0; s < S; ++s) t += seg[s];
+        field_ptr(gm[pb], field)[k] = t;
+    }
 }
 
 // Start of a cycle of every active problem (mode 1: reference norm = |r|).
@@ -489,6 +500,7 @@ struct BatchWork {
     bool fused;              // FP32 cycle: one persistent launch per Arnoldi step (fused.cu)
     const int32_t* pid;
     int64_t n;
+    int red_warps;           // warps of a k_breduce block: the most segments of any problem
 
     // The Gram-Schmidt passes of one step, over the problems still running.
     template <int MODE, class T>
@@ -505,7 +517,8 @@ struct BatchWork {
                     RBF_LAUNCH(ctx, k_bupdate_stream, (unsigned)C.nc, kDotThreads, kStreamSmem, st, V, ldv, nv, gm,
                                field_in, x, C, mask, partial, status, ctx->fused_spin_limit, check);
                 const int nout = MODE == 2 ? 1 : nv;
-                RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out,
+                RBF_LAUNCH(ctx, k_breduce, (unsigned)(nprob * nout), 32 * red_warps, 0, st, partial, C, nprob, nout, gm,
+                           field_out,
                            mask);
                 return RBF_OK;
             }
@@ -517,7 +530,8 @@ struct BatchWork {
             RBF_LAUNCH(ctx, (k_bupdate<T, MODE>), (unsigned)C.nc, kDotThreads, 0, st, V, ldv, nv, gm, field_in, x,
                        C, mask, partial);
         const int nout = MODE == 2 ? 1 : nv;
-        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * nout, 0, st, partial, C, nprob, nout, gm, field_out, mask);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)(nprob * nout), 32 * red_warps, 0, st, partial, C, nprob, nout, gm,
+                   field_out, mask);
         return RBF_OK;
     }
 };
@@ -729,7 +743,10 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
     RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
 
-    BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, false, ctx->pid.p, n};
+    int max_chunks = 0;
+    for (int b = 0; b < nprob; ++b) max_chunks = std::max(max_chunks, cptr[b + 1] - cptr[b]);
+    BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, false, ctx->pid.p, n,
+                breduce_segments(max_chunks)};
     // |f_b|^2
     RBF_CHECK((B.mdot<0, double>(f, 0, 1, const_cast<double*>(f), -1, F_FNORM2, active)));
     std::vector<double> stat(4 * (size_t)nprob);
@@ -825,7 +842,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         if (!w_zero) RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
         RBF_LAUNCH(ctx, k_bresidual, (unsigned)B.C.nc, kDotThreads, 0, st, f, w_zero ? nullptr : ctx->vec_a.p, r64,
                    B.C, active, B.partial);
-        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32, 0, st, B.partial, B.C, nprob, 1, gm, F_BETA2, active);
+        RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * B.red_warps, 0, st, B.partial, B.C, nprob, 1, gm, F_BETA2,
+                   active);
         RBF_CHECK(read_stat());
         int nact = 0;
         for (int b = 0; b < nprob; ++b) {
