@@ -162,7 +162,10 @@ rbf_status rbf_solve(rbf_ctx* ctx, const double* f_dev, double* w_dev, const rbf
 
 /* End-to-end call on host buffers: copies xy_host (n x 2) and f_host to the
  * device, runs rbf_bin, rbf_rasm_setup and rbf_solve from w = 0, and copies w
- * back into w_host. Host buffers should be pinned for full copy speed. */
+ * back into w_host. Host buffers should be pinned for full copy speed. The
+ * device copies of xy, f and w (32 B per point) stay with the context for the
+ * next call, so repeated calls of the same size allocate nothing; they are
+ * freed by rbf_destroy. */
 rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const double* f_host, double* w_host,
                                 int64_t n, const rbf_params* params, const rbf_rasm_params* rasm,
                                 const rbf_solve_params* solve, rbf_solve_info* info, rbf_stream stream);

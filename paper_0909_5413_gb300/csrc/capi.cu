@@ -638,8 +638,10 @@ rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const doubl
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_interpolate_host: null buffer or n < 1");
     RBF_CUDA(ctx, cudaSetDevice(ctx->device));
     static_assert(sizeof(double) == 8, "double");
-    rbf::DevArray<double> xy, f, w;
-    // staging buffers are owned by the context for the duration of the call
+    // staging buffers held by the context between calls (no allocation when the size repeats)
+    rbf::DevArray<double>& xy = ctx->host_xy;
+    rbf::DevArray<double>& f = ctx->host_f;
+    rbf::DevArray<double>& w = ctx->host_w;
     RBF_CHECK(ensure(ctx, xy, (size_t)(2 * n)));
     rbf_status st = ensure(ctx, f, (size_t)n);
     if (st == RBF_OK) st = ensure(ctx, w, (size_t)n);
@@ -661,9 +663,6 @@ rbf_status rbf_interpolate_host(rbf_ctx* ctx, const double* xy_host, const doubl
         }
         st = ss;
     }
-    release(ctx, xy.p);
-    release(ctx, f.p);
-    release(ctx, w.p);
     return st;
 }
 

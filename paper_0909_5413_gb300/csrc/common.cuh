@@ -225,6 +225,7 @@ struct rbf_ctx {
     unsigned long long fused_spin_limit = 1ull << 23;   // polls of a barrier wait before it gives up
     int fused_extra_block = 0;              // check of the timeout path: barriers wait for one block too many
     bool bgraph_off = false;                // this solve launches its cycles directly (no capture)
+    rbf::DevArray<double> host_xy, host_f, host_w;   // rbf_interpolate_host's device copies (kept between calls)
     rbf::DevArray<int> fused_sync;          // barrier state (4 ints), then status words: fused step, bulk copies
     int gs_stream_mode = 1;                 // FP32 Gram-Schmidt passes: 1 basis streamed by bulk copies, 0 registers
     bool gs_stream = false;                 // ... in the current solve

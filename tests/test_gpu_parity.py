@@ -522,6 +522,18 @@ def test_interpolate_host_matches_device_path(rbf):
     _, _, w = solve_gpu(rbf, p)
     np.testing.assert_array_equal(w_h.numpy(), w)
     assert ctx.launches > 0
+    # a second call of the same size reuses the context's device copies: no
+    # allocation, the same bits; a smaller problem then fits in them
+    held = rbf.rbf_device_bytes(ctx.handle)
+    w_h.zero_()
+    st, info = ctx.interpolate_host(xy_h, f_h, w_h, cfg)
+    assert st == 0 and rbf.rbf_device_bytes(ctx.handle) == held
+    np.testing.assert_array_equal(w_h.numpy(), w)
+    q = W.lattice_problem(40, 0.85, seed=9)
+    wq = torch.zeros(q.n, dtype=torch.float64).pin_memory()
+    st, info = ctx.interpolate_host(torch.from_numpy(q.xy.copy()).pin_memory(),
+                                    torch.from_numpy(q.f.copy()).pin_memory(), wq, rbf.config_for(q))
+    assert st == 0 and oracle_relres(q, wq.numpy()) <= 1e-13
     ctx.close()
 
 
