@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(T) k_matvec_f32v2(MvParams P, const float* __r
 // points <= 32 TPL): the list holds (cell, 0) items of that class, and each
 // class has a kernel of its own register budget.
 template <int TPL>
-__global__ void __launch_bounds__(kSymWarps * 32, TPL == 1 ? 8 : (TPL == 2 ? 7 : 4))
+__global__ void __launch_bounds__(kSymWarps * 32, TPL == 1 ? 8 : (TPL == 2 ? 8 : 4))
     k_matvec_f32_sym(MvParams P, const int32_t* __restrict__ cells, int64_t ncells, const float* __restrict__ w,
                      float* __restrict__ rowslot, float* __restrict__ colslot, int64_t n)
 {

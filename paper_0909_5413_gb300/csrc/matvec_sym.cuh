@@ -40,6 +40,13 @@ __device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
     return *reinterpret_cast<float2*>(&d);
 }
 
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b)
+{
+    unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(A), "l"(B));
+    return *reinterpret_cast<float2*>(&d);
+}
+
 __device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
 {
     unsigned long long d, A = *reinterpret_cast<unsigned long long*>(&a), B = *reinterpret_cast<unsigned long long*>(&b);
@@ -118,12 +125,30 @@ __device__ __forceinline__ void sym_pass(SymWarp& S, int lane, const float2 (&tx
             if (COL) row[s >> 2] = make_float4(c01.x, c01.y, c23.x, c23.y);
         }
         if (COL) {
+            // column sums of the transpose: lane (g, q) = (lane % 8, lane / 8)
+            // adds rows 8q .. 8q + 7 of columns 4g .. 4g + 3 in order (packed
+            // pairs), then the four row groups are added by a fixed shuffle
+            // tree; lane (g, q) stores column 4g + q
             __syncwarp();
-            float sum = 0.f;
-#pragma unroll 8
-            for (int r = 0; r < 32; ++r) sum += S.T[r * kSymTld + lane];
+            const int g = lane & 7, q = lane >> 3;
+            float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 v = *reinterpret_cast<const float4*>(&S.T[(8 * q + i) * kSymTld + 4 * g]);
+                a01 = f2_add(a01, make_float2(v.x, v.y));
+                a23 = f2_add(a23, make_float2(v.z, v.w));
+            }
+#pragma unroll
+            for (int d = 8; d <= 16; d <<= 1) {
+                a01.x += __shfl_xor_sync(0xffffffffu, a01.x, d);
+                a01.y += __shfl_xor_sync(0xffffffffu, a01.y, d);
+                a23.x += __shfl_xor_sync(0xffffffffu, a23.x, d);
+                a23.y += __shfl_xor_sync(0xffffffffu, a23.y, d);
+            }
             __syncwarp();
-            if (c0 + lane < dn) colout[c0 + lane] = sum * knorm;
+            const float sum = q == 0 ? a01.x : (q == 1 ? a01.y : (q == 2 ? a23.x : a23.y));
+            const int col = c0 + 4 * g + q;
+            if (col < dn) colout[col] = sum * knorm;
         }
     }
 }
