@@ -100,13 +100,13 @@ def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic, note: 
 # kernel and its gather); the 3 x 3 stencil's candidate count is reported
 # beside it.
 MUFU_PEAK_PAIRS = SM_COUNT * 16 * SM_CLOCK_HZ
-MATVEC_F32_REV = "sym-early-exit-v3"
+MATVEC_F32_REV = "sym-colsum-v4"
 MATVEC_F32_KERNEL = "k_matvec_f32_sym<TPL> + k_sym_gather"
 # DRAM read + write of one launch on the 7168 x 7168 lattice's inner grid
 # (ncu, one-pass dram__bytes metrics, this revision): the symmetric kernel of
-# the 33-64 point cells 631.8 MB + 977.3 MB (its five FP32 slots per point
+# the 33-64 point cells 630.8 MB + 976.9 MB (its five FP32 slots per point
 # written), the gather 1230 MB + 192.3 MB; and that lattice's N
-MATVEC_F32_TRAFFIC = {"sym-early-exit-v3": (3_031_360_000, 51_380_224)}
+MATVEC_F32_TRAFFIC = {"sym-colsum-v4": (3_030_010_000, 51_380_224)}
 
 
 def f32_matvec_roofline(pairs: int, cand: int, avg_s: float, launches: int, traffic, grid: str) -> dict:
@@ -503,6 +503,21 @@ def run_ours(args, ws, rank, local):
     factors = {"precision": "fp32 tensor cores" if mode == "mixed" else "fp64", "tensor_core_subdomains": tc,
                "fp64_subdomains": f64}
 
+    # end to end through the host-buffer entry point, right after the timed
+    # steps (before the other forms below change the context's state)
+    e2e = None
+    if not args.no_e2e:
+        xy_h = torch.from_numpy(p.xy.copy()).pin_memory()
+        f_h = torch.from_numpy(p.f.copy()).pin_memory()
+        w_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+        ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False)
+        te, _ = timed_steps(lambda: ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False),
+                            max(1, min(args.steps, 3)), flush, barrier)
+        e2e = {"value": max_over_ranks(statistics.mean(te), dist, "cuda"), "unit": UNIT,
+               "h2d_bytes_per_step": xy_h.numel() * 8 + f_h.numel() * 8, "d2h_bytes_per_step": w_h.numel() * 8,
+               "call": "rbf_interpolate_host (pinned host buffers, copies inside the timed region)"}
+        del xy_h, f_h, w_h
+
     # the mixed form with subdomain inverses computed in FP64 (stored FP32), for
     # the inner-step cost of the tensor-core inverses
     if mode == "mixed" and not args.no_extra:
@@ -527,19 +542,6 @@ def run_ours(args, ws, rank, local):
                  "steps": len(ts), "step_ms": [round(t, 3) for t in ts], "status": st2, **i2.as_dict()}
         extra["speedup_mixed_over_f64"] = (extra["ms_per_step"] / ms) if mode == "mixed" else (ms / extra["ms_per_step"])
 
-    # end to end through the host-buffer entry point
-    e2e = None
-    if not args.no_e2e:
-        xy_h = torch.from_numpy(p.xy.copy()).pin_memory()
-        f_h = torch.from_numpy(p.f.copy()).pin_memory()
-        w_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
-        ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False)
-        te, _ = timed_steps(lambda: ctx.interpolate_host(xy_h, f_h, w_h, cfg, check=False),
-                            max(1, min(args.steps, 3)), flush, barrier)
-        e2e = {"value": max_over_ranks(statistics.mean(te), dist, "cuda"), "unit": UNIT,
-               "h2d_bytes_per_step": xy_h.numel() * 8 + f_h.numel() * 8, "d2h_bytes_per_step": w_h.numel() * 8,
-               "call": "rbf_interpolate_host (pinned host buffers, copies inside the timed region)"}
-        del xy_h, f_h, w_h
     ctx.close()
     del w, flush
     torch.cuda.empty_cache()
