@@ -5,9 +5,12 @@
 // mixed form these serve only the FP32 inner solves, so they are computed in
 // FP32 here, with the dense work on the tensor pipe:
 //
-//   * A_i is formed over the overlap list with the FP64 matvec's pair test and
-//     fixed-point kernel values (the operator the GPU applies), rounded to FP32,
-//     and padded with an identity block to Np = 8 ceil(n / 8) <= 48;
+//   * A_i is formed over the overlap list in FP32: offsets from the list's
+//     first point scaled so that the kernel is exp2(-|d|^2), the pair test
+//     |d|^2 <= r_c^2 in those units, exp2 on the SFU (the entries carry a few
+//     FP32 roundings, below the FP32 inverse's own error, which the
+//     conditioning of A_i sets), and padded with an identity block to
+//     Np = 8 ceil(n / 8) <= 48;
 //   * A_i^{-1} comes from the block sweep (Gauss-Jordan elimination without
 //     pivoting, which is stable on SPD matrices: its pivots are the Schur
 //     complements): for each 8 x 8 diagonal block K in turn,
@@ -44,8 +47,7 @@ struct TcWarp {
     float A[kTcMax * kTcLd];
     float U[kTcMax * kTcUld];
     float P[64];                 // the 8 x 8 pivot block, swept in place
-    double px[kTcMax], py[kTcMax];
-    long long pxf[kTcMax], pyf[kTcMax];
+    float fx[kTcMax], fy[kTcMax];   // scaled offsets from the list's first point
     int cpos[kTcMax];
 };
 
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kTcWarps * 32)
                     const int32_t* __restrict__ ov_idx, const int32_t* __restrict__ core_of,
                     const int32_t* __restrict__ core_ptr, const int64_t* __restrict__ w_off, int64_t nsub,
                     const Prob* __restrict__ prob, const int32_t* __restrict__ pid_sub, int full,
-                    const unsigned long long* __restrict__ fxtab, float* __restrict__ W32,
+                    float* __restrict__ W32,
                     int32_t* __restrict__ fb_list, unsigned int* __restrict__ fb_count)
 {
     extern __shared__ __align__(16) unsigned char tc_smem[];
@@ -143,17 +145,18 @@ __global__ void __launch_bounds__(kTcWarps * 32)
         return;
     }
     const Prob& pr = prob[pid_sub[sub]];
-    const double rc2 = pr.rc2, knorm = pr.knorm, fxs = pr.fx_scale;
-    const int sh = pr.fx_sh, F = pr.fx_F;
-    const unsigned long long M = pr.fx_M;
+    const double al = (double)pr.a_loc;
+    const float rc2s = (float)(pr.rc2 * al * al), knorm = (float)pr.knorm;
     const int np = (n + 7) & ~7;   // padded order
     const int nb = np >> 3;
-    for (int a = lane; a < n; a += 32) {
-        const int p = ov_idx[b + a];
-        S.px[a] = xy_s[2 * (int64_t)p];
-        S.py[a] = xy_s[2 * (int64_t)p + 1];
-        S.pxf[a] = fx_coord(S.px[a], fxs, sh);
-        S.pyf[a] = fx_coord(S.py[a], fxs, sh);
+    {
+        const int p0 = ov_idx[b];
+        const double x0 = xy_s[2 * (int64_t)p0], y0 = xy_s[2 * (int64_t)p0 + 1];
+        for (int a = lane; a < n; a += 32) {
+            const int p = ov_idx[b + a];
+            S.fx[a] = (float)((xy_s[2 * (int64_t)p] - x0) * al);
+            S.fy[a] = (float)((xy_s[2 * (int64_t)p + 1] - y0) * al);
+        }
     }
     // kept rows (ascending positions in the overlap list)
     int nkept = 0;
@@ -170,24 +173,23 @@ __global__ void __launch_bounds__(kTcWarps * 32)
         S.A[e] = (r >= n && r == c) ? 1.0f : 0.0f;
     }
     __syncwarp();
-    // A_i: lower triangle by packed index over the lanes, mirrored (the FP64
-    // kernel's pair test and kernel value, rounded to FP32)
+    // A_i: lower triangle by packed index over the lanes, mirrored (FP32 pair
+    // test and kernel value in the scaled units)
     {
         const int total = n * (n + 1) / 2;
         int i = 0, j = lane;
         while (j > i) { j -= i + 1; ++i; }
         for (int t = lane; t < total; t += 32) {
-            const double dx = __dsub_rn(S.px[i], S.px[j]), dy = __dsub_rn(S.py[i], S.py[j]);
-            const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-            double v = 0.0;
-            if (r2 <= rc2) {
-                const long long du = (long long)((unsigned long long)S.pxf[i] - (unsigned long long)S.pxf[j]);
-                const long long dv = (long long)((unsigned long long)S.pyf[i] - (unsigned long long)S.pyf[j]);
-                v = (F == 52 ? kernel_fx52(du, dv, M, fxtab, fxtab + kFxTab)
-                             : kernel_fx(du, dv, F, M, fxtab, fxtab + kFxTab)) * knorm;
+            const float dx = S.fx[i] - S.fx[j], dy = S.fy[i] - S.fy[j];
+            const float r2 = fmaf(dy, dy, dx * dx);
+            float v = 0.f;
+            if (r2 <= rc2s) {
+                float e;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-r2));
+                v = e * knorm;
             }
-            S.A[i * kTcLd + j] = (float)v;
-            S.A[j * kTcLd + i] = (float)v;
+            S.A[i * kTcLd + j] = v;
+            S.A[j * kTcLd + i] = v;
             j += 32;
             while (j > i) { j -= i + 1; ++i; }
         }
@@ -288,7 +290,7 @@ rbf_status rasm_factor_tc(rbf_ctx* ctx, int32_t* fb_list, unsigned int* fb_count
     RBF_CUDA(ctx, cudaMemsetAsync(fb_count_dev, 0, sizeof(unsigned int), st));
     RBF_LAUNCH(ctx, k_rasm_setup_tc, blocks_for(nsub, kTcWarps), kTcWarps * 32, smem, st, ctx->xy_s.p, ctx->ov_ptr.p,
                ctx->ov_idx.p, ctx->core_of.p, ctx->core_ptr.p, ctx->w_off.p, nsub, ctx->prob.p, ctx->pid_sub.p,
-               ctx->rasm_additive ? 1 : 0, ctx->fxtab.p, ctx->W32.p, fb_list, fb_count_dev);
+               ctx->rasm_additive ? 1 : 0, ctx->W32.p, fb_list, fb_count_dev);
     unsigned int cnt = 0;
     RBF_CUDA(ctx, cudaMemcpyAsync(&cnt, fb_count_dev, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     RBF_CUDA(ctx, cudaStreamSynchronize(st));
