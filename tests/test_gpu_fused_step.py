@@ -100,3 +100,25 @@ def test_options_are_validated(rbf):
             rbf.rbf_set_option(ctx.handle, opt, val)
         assert e.value.status == 1
     ctx.close()
+
+
+def test_fused_step_matches_separate_kernels_with_segmented_reductions(rbf):
+    """A problem of more than 2047 chunks (8.4 M points) has its chunk partials
+    summed in several segments, by one warp each in the separate kernels and in
+    sequence in the fused step: the same bits either way, next to small
+    problems of one segment."""
+    probs = [W.lattice_problem(2900, 0.9, seed=560, rhs="four_gaussians"),
+             W.lattice_problem(40, 0.85, seed=561, rhs="four_gaussians"),
+             W.lattice_problem(23, 1.0, seed=562, rhs="four_gaussians")]
+    assert probs[0].n > 2048 * 4096
+    c1, st1, inf1, w1, ptr, _ = solve(rbf, probs, 1)
+    c0, st0, inf0, w0, _, _ = solve(rbf, probs, 0)
+    c1.close()
+    c0.close()
+    assert st1 == 0 and st0 == 0, [i.as_dict() for i in inf0]
+    np.testing.assert_array_equal(w1, w0)
+    assert all(i.relres <= 1e-13 for i in inf0)
+    for b in (1, 2):
+        wb = w0[ptr[b]:ptr[b + 1]]
+        r = probs[b].f - O.matvec_cutoff(probs[b].xy, wb, probs[b].sigma, probs[b].cutoff)
+        assert np.linalg.norm(r) / np.linalg.norm(probs[b].f) <= 1e-13
