@@ -50,7 +50,9 @@ typedef enum {
  * inverses of rbf_rasm_setup (rbf_rasm_params.precision):
  *   RBF_FP64           computed and stored in FP64 (Cholesky, Sec. 2.2);
  *   RBF_FP32           computed in FP32 on the tensor cores and stored in FP32,
- *                      for the inner solves of the mixed form: the block sweep
+ *                      for the inner solves of the mixed form: A_i formed in
+ *                      FP32 (the pair test and exp2 on scaled offsets), then
+ *                      the block sweep
  *                      (Gauss-Jordan without pivoting on the SPD A_i, 8 x 8
  *                      blocks) with every product a TF32 MMA split into three
  *                      (FP32 accuracy) and FP32 accumulation; a subdomain of
