@@ -417,8 +417,8 @@ enum {
      * barriers between the phases; the results are bit for bit those of the
      * separate kernels). 0: never (separate kernels); 1: always; 2 (default):
      * once at most 64 problems are still active, where the separate kernels'
-     * launches dominate the step. Not used while a kernel class of the cycle
-     * is being profiled, nor for a single problem. */
+     * launches dominate the step, and for a single problem of at most 262,144
+     * points. Not used while a kernel class of the cycle is being profiled. */
     RBF_OPT_FUSED_STEP = 1,
     /* 1 (default): the inner FP32 matvec of the mixed form visits each pair of
      * neighbouring cells once (cells of at most 128 points); 0: every target

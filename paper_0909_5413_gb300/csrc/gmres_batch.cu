@@ -37,6 +37,11 @@ namespace {
 // short and their launches dominate; with many problems active they keep
 // more warps resident than the persistent kernel and are faster.
 constexpr int kFusedTail = 64;
+// A single problem takes it up to this many points: below, its launches
+// dominate the step (4,096 points: 12.2 against 13.6 ms per solve; 65,536:
+// 15.9 against 17.5 ms); above, the separate kernels keep more warps resident
+// (524,176 points: 43.0 against 34.7 ms).
+constexpr int64_t kFusedSingleMax = 262144;
 
 constexpr int kBPer = kOrthoPer;       // elements per thread (the single solver's chunking)
 constexpr int kBChunk = kOrthoChunk;   // elements per chunk
@@ -814,7 +819,8 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
         constexpr unsigned kCycleClasses = (1u << RBF_PROF_MATVEC_F64) | (1u << RBF_PROF_MATVEC_F32) |
                                            (1u << RBF_PROF_RASM_APPLY) | (1u << RBF_PROF_ORTHO);
         const bool profiling = ctx->prof && (ctx->prof_mask & kCycleClasses);
-        fused_ok = mixed && nprob > 1 && !profiling && fused_step_applies(ctx);
+        fused_ok = mixed && (nprob > 1 || ctx->fused_mode == 1 || n <= kFusedSingleMax) && !profiling &&
+                   fused_step_applies(ctx);
         if (mixed) {   // the fused step's barrier state and the status words of the cycle's waits
             RBF_CHECK(ensure(ctx, ctx->fused_sync, 8));
             RBF_CUDA(ctx, cudaMemsetAsync(ctx->fused_sync.p, 0, 8 * sizeof(int), st));

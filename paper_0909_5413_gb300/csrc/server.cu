@@ -98,6 +98,11 @@ rbf_status rbf_server::run(Slot& s, Ticket& t)
     if (!s.ctx) {
         rbf_status c = rbf_create(&s.ctx, device);
         if (c != RBF_OK) return c;
+        // the slots run at once on their own streams: no cooperative (fused)
+        // Arnoldi steps, whose grid would have to share the SMs with the
+        // other slots' kernels
+        c = rbf_set_option(s.ctx, RBF_OPT_FUSED_STEP, 0);
+        if (c != RBF_OK) return c;
     }
     const int64_t n = r.n;
     if (s.cap < n) {

@@ -122,3 +122,21 @@ def test_fused_step_matches_separate_kernels_with_segmented_reductions(rbf):
         wb = w0[ptr[b]:ptr[b + 1]]
         r = probs[b].f - O.matvec_cutoff(probs[b].xy, wb, probs[b].sigma, probs[b].cutoff)
         assert np.linalg.norm(r) / np.linalg.norm(probs[b].f) <= 1e-13
+
+
+@pytest.mark.parametrize("n_side,fused_by_default", [(90, True), (600, False)])
+def test_single_problem_default_takes_fused_step_when_small(rbf, n_side, fused_by_default):
+    """The default (adaptive) mode runs a single problem of at most 262,144
+    points on the fused step and a larger one on the separate kernels; either
+    way the bits are those of the separate kernels."""
+    p = W.lattice_problem(n_side, 0.85, seed=570 + n_side, rhs="four_gaussians")
+    c2, st2, i2, w2, ptr, l2 = solve(rbf, [p], 2)
+    c0, st0, i0, w0, _, l0 = solve(rbf, [p], 0)
+    c2.close()
+    c0.close()
+    assert st2 == 0 and st0 == 0
+    np.testing.assert_array_equal(w2, w0)
+    if fused_by_default:
+        assert l2 * 3 < l0, (l2, l0)
+    else:
+        assert l2 == l0

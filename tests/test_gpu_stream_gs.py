@@ -30,9 +30,12 @@ def dev(a):
 
 
 def solve(rbf, probs, options=()):
+    """Mixed solve of a batch on the separate kernels (the passes under test)
+    unless the options choose the fused step."""
     xy, f, ptr, params, rasm = rbf.batch_arrays(probs, factor_precision=rbf.RBF_FP32)
     ctx = rbf.Context(0)
     h = ctx.handle
+    rbf.rbf_set_option(h, rbf.RBF_OPT_FUSED_STEP, 0)
     for opt, val in options:
         rbf.rbf_set_option(h, opt, val)
     rbf.rbf_bin_batch(h, dev(xy), ptr, params)
