@@ -265,12 +265,14 @@ __global__ void k_candidate_count(const int32_t* __restrict__ cell_start, const 
 // the flagged cells as (cell, 0) items.
 __global__ void k_flag_class(const int32_t* __restrict__ cell_start, int64_t ncell, int t,
                              const int32_t* __restrict__ pid_cell, const int32_t* __restrict__ prob_ok,
-                             int32_t* __restrict__ flag)
+                             const int32_t* __restrict__ min_cls, int32_t* __restrict__ flag)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int cnt = cell_start[c + 1] - cell_start[c];
-    flag[c] = (cnt > 0 && (cnt + 31) / 32 == t && (!prob_ok || prob_ok[pid_cell[c]])) ? 1 : 0;
+    const int pb = pid_cell[c];
+    const int cls = max((cnt + 31) / 32, min_cls ? min_cls[pb] : 1);
+    flag[c] = (cnt > 0 && cls == t && (!prob_ok || prob_ok[pb])) ? 1 : 0;
 }
 
 // Largest cell of each problem (atomic max per problem).
@@ -489,8 +491,9 @@ rbf_status build_work(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, in
 }
 
 static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
-                                    const int32_t* pid_cell, const int32_t* prob_ok, DevArray<int32_t>& lists,
-                                    int64_t* off, int32_t* flag, int32_t* pos, cudaStream_t st);
+                                    const int32_t* pid_cell, const int32_t* prob_ok, const int32_t* min_cls,
+                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
+                                    cudaStream_t st);
 namespace {
 rbf_status select_work_into(rbf_ctx* ctx, const int32_t* work, int64_t nwork, const int32_t* pid_cell,
                             const int32_t* active, int32_t* out, int64_t* nout, cudaStream_t st);
@@ -619,7 +622,7 @@ rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
                                       st));
         if (ctx->sym64) {
             RBF_CHECK(ensure(ctx, ctx->tmp_i32, std::max<int64_t>(2 * (ncell + 1), n)));
-            RBF_CHECK(build_class_lists(ctx, ctx->cell_start.p, ncell, 5, ctx->pid_cell.p, ctx->sym64_prob.p,
+            RBF_CHECK(build_class_lists(ctx, ctx->cell_start.p, ncell, 5, ctx->pid_cell.p, ctx->sym64_prob.p, nullptr,
                                         ctx->sym64w, ctx->sym64off, ctx->tmp_i32.p, ctx->tmp_i32.p + (ncell + 1),
                                         st));
             RBF_CHECK(ensure(ctx, ctx->sym64_slots, (size_t)(5 * n)));
@@ -727,20 +730,21 @@ rbf_status targets_to_user(rbf_ctx* ctx, const double* sorted, double* user, cud
     return RBF_OK;
 }
 
-// Cell lists by size class for the symmetric matvecs: non-empty cells with
-// ceil(points / 32) == t, t = 1..max_tpl, of the problems prob_ok marks (all
-// when it is null), as (cell, 0) items in `lists` (class t holds [off[t-1],
-// off[t])), order kept within a class. flag and pos are scratch of ncell + 1
-// entries each.
+// Cell lists by size class for the symmetric matvecs: non-empty cells of
+// class t = max(ceil(points / 32), min_cls of their problem), t = 1..max_tpl,
+// of the problems prob_ok marks (all when it is null; min_cls null: 1), as
+// (cell, 0) items in `lists` (class t holds [off[t-1], off[t])), order kept
+// within a class. flag and pos are scratch of ncell + 1 entries each.
 static rbf_status build_class_lists(rbf_ctx* ctx, const int32_t* cell_start, int64_t ncell, int max_tpl,
-                                    const int32_t* pid_cell, const int32_t* prob_ok, DevArray<int32_t>& lists,
-                                    int64_t* off, int32_t* flag, int32_t* pos, cudaStream_t st)
+                                    const int32_t* pid_cell, const int32_t* prob_ok, const int32_t* min_cls,
+                                    DevArray<int32_t>& lists, int64_t* off, int32_t* flag, int32_t* pos,
+                                    cudaStream_t st)
 {
     RBF_CHECK(ensure(ctx, lists, 2 * (size_t)std::max<int64_t>(ncell, 1)));
     off[0] = 0;
     for (int t = 1; t <= max_tpl; ++t) {
         RBF_LAUNCH(ctx, k_flag_class, blocks_for(ncell, 256), 256, 0, st, cell_start, ncell, t, pid_cell, prob_ok,
-                   flag);
+                   min_cls, flag);
         RBF_CHECK(exclusive_scan_i32(ctx, flag, pos, ncell, st));
         RBF_LAUNCH(ctx, k_scatter_cells, blocks_for(ncell, 256), 256, 0, st, ncell, flag, pos, lists.p + 2 * off[t - 1]);
         int32_t cnt = 0;
@@ -819,29 +823,34 @@ rbf_status bin_inner(rbf_ctx* ctx, double ri_sigmas, cudaStream_t st)
     // most 128 points (four targets per lane), the stencil kernel the others:
     // a choice made per problem, so that it sums alike alone and in a batch
     {
-        RBF_CHECK(ensure(ctx, G.sym_prob, 2 * (size_t)nprob));
+        RBF_CHECK(ensure(ctx, G.sym_prob, 3 * (size_t)nprob));
         int32_t* pmax = G.sym_prob.p + nprob;
         RBF_CUDA(ctx, cudaMemsetAsync(pmax, 0, sizeof(int32_t) * nprob, st));
         RBF_LAUNCH(ctx, k_prob_max_cell, blocks_for(ncell, 256), 256, 0, st, G.cell_start.p, ncell, G.pid_cell.p, pmax);
-        std::vector<int32_t> hmax(nprob), ok(2 * (size_t)nprob);
+        std::vector<int32_t> hmax(nprob), ok(3 * (size_t)nprob);
         RBF_CUDA(ctx, cudaMemcpyAsync(hmax.data(), pmax, sizeof(int32_t) * nprob, cudaMemcpyDeviceToHost, st));
         RBF_CUDA(ctx, cudaStreamSynchronize(st));
         int64_t nsym = 0;
         for (int b = 0; b < nprob; ++b) {
             ok[b] = hmax[b] <= 128 ? 1 : 0;
             ok[nprob + b] = 1 - ok[b];
+            // a problem with cells of more than 32 points takes its smaller
+            // (edge) cells in the two-target class too: one launch less, the
+            // same sums (the second target of such a lane is empty)
+            ok[2 * nprob + b] = hmax[b] > 32 ? 2 : 1;
             nsym += ok[b];
         }
         G.sym = nsym > 0;
         G.sym_all = nsym == nprob;
-        RBF_CUDA(ctx, cudaMemcpyAsync(G.sym_prob.p, ok.data(), sizeof(int32_t) * 2 * nprob, cudaMemcpyHostToDevice, st));
+        RBF_CUDA(ctx, cudaMemcpyAsync(G.sym_prob.p, ok.data(), sizeof(int32_t) * 3 * nprob, cudaMemcpyHostToDevice, st));
     }
     if (G.sym) {
         // its slots are allocated here, outside the solver's graph capture
         RBF_CHECK(ensure(ctx, ctx->sym_slots, (size_t)(5 * n)));
         // its cell lists by size class (order kept within a class)
         RBF_CHECK(ensure(ctx, G.tmp, std::max<int64_t>(2 * (ncell + 1), 2 * kNumSMs + 1)));
-        RBF_CHECK(build_class_lists(ctx, G.cell_start.p, ncell, 4, G.pid_cell.p, G.sym_prob.p, G.symw, G.symoff,
+        RBF_CHECK(build_class_lists(ctx, G.cell_start.p, ncell, 4, G.pid_cell.p, G.sym_prob.p, G.sym_prob.p + 2 * nprob,
+                                    G.symw, G.symoff,
                                     G.tmp.p, G.tmp.p + (ncell + 1), st));
         RBF_CHECK(ensure(ctx, G.work_ns, 2 * (size_t)std::max<int64_t>(G.n_work, 1)));
         RBF_CHECK(select_work_into(ctx, G.work.p, G.n_work, G.pid_cell.p, G.sym_prob.p + nprob, G.work_ns.p,
