@@ -450,7 +450,21 @@ enum {
     /* Check of the timeout path: 1 makes every bulk-copy wait of those passes
      * wait on a barrier that no copy completes (and copy nothing), so that it
      * runs out and the solve returns RBF_ERR_TIMEOUT. */
-    RBF_OPT_STREAM_WAIT_CHECK = 7
+    RBF_OPT_STREAM_WAIT_CHECK = 7,
+    /* 1 (default): at the start of a solve, the FP64 matvec's accept masks and
+     * kernel values of the current binning are computed once and kept in
+     * device memory (about 10.7 B per in-cutoff pair: 8 B values in slots
+     * padded to the walk's warp steps, and the masks; 363 pairs per point at
+     * h/sigma = 0.8), if they fit in the device's free memory less 8 GiB and in
+     * the context's memory limit; the FP64 products then read them instead of
+     * evaluating the kernel, with the same sums bit for bit. Recomputed at
+     * the first solve after each binning; freed by rbf_destroy or by setting
+     * 0. Not used by the symmetric FP64 kernel (RBF_OPT_SYMMETRIC_F64), by a
+     * batched solve once some of its problems have stopped (their products
+     * run on lists of the active problems' items), or by a solve under
+     * stream capture; an allocation that fails leaves the solve matrix-free.
+     * 0: never (matrix-free). */
+    RBF_OPT_STORE_F64 = 8
 };
 /* Set a context option. INVALID_ARG for an unknown option or value. */
 rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value);

@@ -75,6 +75,7 @@ template rbf_status ensure<int32_t>(rbf_ctx*, DevArray<int32_t>&, size_t);
 template rbf_status ensure<int64_t>(rbf_ctx*, DevArray<int64_t>&, size_t);
 template rbf_status ensure<double>(rbf_ctx*, DevArray<double>&, size_t);
 template rbf_status ensure<float>(rbf_ctx*, DevArray<float>&, size_t);
+template rbf_status ensure<uint32_t>(rbf_ctx*, DevArray<uint32_t>&, size_t);
 template rbf_status ensure<GmresDev>(rbf_ctx*, DevArray<GmresDev>&, size_t);
 template rbf_status ensure<Prob>(rbf_ctx*, DevArray<Prob>&, size_t);
 template rbf_status ensure<unsigned long long>(rbf_ctx*, DevArray<unsigned long long>&, size_t);
@@ -307,6 +308,11 @@ rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
     case RBF_OPT_STREAM_WAIT_CHECK:
         if (value != 0 && value != 1) break;
         ctx->stream_check = (int)value;
+        return RBF_OK;
+    case RBF_OPT_STORE_F64:
+        if (value != 0 && value != 1) break;
+        ctx->store_mode = (int)value;
+        if (value == 0) f64_store_release(ctx);
         return RBF_OK;
     default:
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_option: unknown option %d", option);

@@ -71,6 +71,16 @@ struct Prob {
 
 }  // namespace rbf
 
+// The FP64 matvec's accept masks and kernel values of one binning, in the
+// order its walk takes them (per work item of the full list).
+struct F64Keep {
+    bool valid = false;
+    int tile = 0;
+    rbf::DevArray<int64_t> cnt, nwords, val_off, mask_off;
+    rbf::DevArray<double> val;
+    rbf::DevArray<uint32_t> mask;
+};
+
 // The inner grid of the mixed form: the points binned again with cells of side
 // r_i (a shorter cutoff for the FP32 inner matvec, stencil 3 x 3), their own
 // order (inner position q holds main cell-ordered point perm[q]), and the
@@ -226,6 +236,8 @@ struct rbf_ctx {
     int fused_extra_block = 0;              // check of the timeout path: barriers wait for one block too many
     bool bgraph_off = false;                // this solve launches its cycles directly (no capture)
     rbf::DevArray<double> host_xy, host_f, host_w;   // rbf_interpolate_host's device copies (kept between calls)
+    F64Keep f64s;                  // the FP64 matvec's pair values, kept for replays (valid until the next binning)
+    int store_mode = 1;            // keep them when they fit (1), never (0)
     rbf::DevArray<int> fused_sync;          // barrier state (4 ints), then status words: fused step, bulk copies
     int gs_stream_mode = 1;                 // FP32 Gram-Schmidt passes: 1 basis streamed by bulk copies, 0 registers
     bool gs_stream = false;                 // ... in the current solve
@@ -336,6 +348,11 @@ rbf_status matvec_sorted_f64(rbf_ctx* ctx, const double* w, double* y, cudaStrea
 rbf_status matvec_sorted_f32(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 // The FP64 matvec launch alone (no profiler events), for the allocation-free entry point.
 rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
+// Computes and keeps the FP64 matvec's accept masks and pair values of the
+// current binning when the store is enabled and they fit in free memory (the
+// following FP64 products replay them, bit for bit); a no-op otherwise.
+rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st);
+void f64_store_release(rbf_ctx* ctx);   // frees the kept values (the small per-item tables stay)
 // The FP64 kernel for targets binned by bin_targets (cell-sorted; s in target order).
 rbf_status eval_sorted_f64(rbf_ctx* ctx, const double* txy, const float* tloc, const int32_t* tcell_start,
                            const int32_t* twork, int64_t nwork, const double* w, double* s, cudaStream_t st);

@@ -748,6 +748,9 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
     RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
 
+    // the FP64 products of this solve replay kept pair values when they fit
+    // (computed here, before any cycle is captured)
+    RBF_CHECK(f64_store_prepare(ctx, st));
     int max_chunks = 0;
     for (int b = 0; b < nprob; ++b) max_chunks = std::max(max_chunks, cptr[b + 1] - cptr[b]);
     BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, false, ctx->pid.p, n,

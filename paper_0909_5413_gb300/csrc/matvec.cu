@@ -50,11 +50,62 @@ __host__ __device__ constexpr size_t mv64_smem(int T, int S)
            (size_t)kMvQ * T * sizeof(double) + (size_t)(S / 32) * T * 4;
 }
 
-template <int T>
+// The FP64 matvec's pair values kept in device memory: MODE 1 counts, per work
+// item of the full list, its value slots and its 32-source words; MODE 2
+// stores the accept masks and the kernel values; MODE 3 replays the matvec
+// from them: the same values, the same sums, bit for bit, without the filter
+// or the kernel evaluations. The values are laid out for the lockstep walk
+// below: per pass, per warp, per step of the walk, 64 doubles, lane l's one or
+// two values of that step at 2l and 2l + 1 (a slot of a lane with nothing at
+// that step is written as zeros and never read), so that a step loads 512
+// contiguous bytes per warp. A warp takes, per pass, as many steps as its
+// busiest lane: sum over the lane's words of ceil(popcount / 2).
+struct F64Store {
+    int64_t* cnt;               // MODE 1: value slots of each item (doubles, a multiple of 64)
+    int64_t* nwords;            // MODE 1: 32-source words of each item (all passes)
+    const int64_t* val_off;     // MODE 2, 3: first value of each item
+    const int64_t* mask_off;    // MODE 2, 3: first word of each item (T masks per word)
+    double* val;
+    uint32_t* mask;
+};
+
+// Exclusive prefix of v over the block's threads in thread order, and the
+// block's total. sh: one V per warp.
+template <class V>
+__device__ __forceinline__ V block_excl_scan(V v, V* sh, V& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+    V x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const V u = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += u;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        V z = lane < nwp ? sh[lane] : V(0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const V u = __shfl_up_sync(0xffffffffu, z, d);
+            if (lane >= d) z += u;
+        }
+        if (lane < nwp) sh[lane] = z;
+    }
+    __syncthreads();
+    const V pre = (wid ? sh[wid - 1] : V(0)) + x - v;
+    total = sh[nwp - 1];
+    __syncthreads();
+    return pre;
+}
+
+template <int T, int MODE>
 __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, const double* __restrict__ w,
-                                                                 double* __restrict__ y)
+                                                                 double* __restrict__ y, F64Store FS)
 {
     constexpr int kThreads = T * kMvQ;
+    constexpr bool kEval = MODE == 0 || MODE == 2;   // kernel values computed here
+    constexpr bool kFilter = MODE <= 2;              // accept masks computed here
     const int kStage = P.stage;
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long* T1 = smem_u64;
@@ -66,13 +117,16 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     float* SF = (float*)(PART + kMvQ * T);
     uint32_t* MASK = (uint32_t*)(SF + 2 * kStage);
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
+    __shared__ long long scan_sh[kThreads / 32];
 
     const int tid = threadIdx.x;
     const int t = tid & (T - 1), qtr = tid / T;   // target, quarter (warp-uniform)
-    const int cell = P.work[2 * blockIdx.x], first = P.work[2 * blockIdx.x + 1];
+    const int64_t item = blockIdx.x;
+    const int cell = P.work[2 * item], first = P.work[2 * item + 1];
     const int pcell = P.pid_cell[cell];
     if (P.active && !P.active[pcell]) return;   // masked problem (the whole block belongs to it)
-    for (int i = tid; i < 2 * kFxTab; i += kThreads) T1[i] = P.fxtab[i];
+    if (kEval)
+        for (int i = tid; i < 2 * kFxTab; i += kThreads) T1[i] = P.fxtab[i];
     const Prob& pr = P.prob[pcell];
     const int ncx = (int)pr.ncx, ncy = (int)pr.ncy, kst = pr.k, cbase = (int)pr.cellbase;
     const double rc2 = pr.rc2, knorm = pr.knorm, fxs = pr.fx_scale;
@@ -100,7 +154,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     double xi = 0.0, yi = 0.0;
     long long xf = 0, yf = 0;
     float fx = 0.f, fy = 0.f;
-    if (active) {
+    if (active && kFilter) {
         xi = P.txy[2 * p];
         yi = P.txy[2 * p + 1];
         xf = fx_coord(xi, fxs, sh);
@@ -110,6 +164,10 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     }
     __syncthreads();
     const int S = row_pre[nrow];
+    if (MODE == 1 && tid == 0) FS.nwords[item] = (S + 31) / 32;
+    const int lane = tid & 31;
+    int64_t vbase = (MODE >= 2) ? FS.val_off[item] : 0;   // this pass's first slot (block-uniform)
+    long long slots = 0;                                  // MODE 1: this warp's slots so far
     double acc = 0.0;
     for (int base = 0; base < S; base += kStage) {
         const int ns = min(kStage, S - base);
@@ -119,54 +177,83 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             int r = 0;
             while (r + 1 < nrow && g >= row_pre[r + 1]) ++r;
             int q = row_beg[r] + (g - row_pre[r]);
-            const double qx = P.xy[2 * q], qy = P.xy[2 * q + 1];
-            SX[2 * idx] = qx;
-            SX[2 * idx + 1] = qy;
-            SXF[2 * idx] = fx_coord(qx, fxs, sh);
-            SXF[2 * idx + 1] = fx_coord(qy, fxs, sh);
-            SW[idx] = w[q];
-            int cq = P.cell_s[q] - cbase;
-            // FP32 offsets, two sources per float4: (x_a, x_b, y_a, y_b)
-            SF[4 * (idx >> 1) + (idx & 1)] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
-            SF[4 * (idx >> 1) + 2 + (idx & 1)] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
+            if (kFilter) {
+                const double qx = P.xy[2 * q], qy = P.xy[2 * q + 1];
+                SX[2 * idx] = qx;
+                SX[2 * idx + 1] = qy;
+                if (kEval) {
+                    SXF[2 * idx] = fx_coord(qx, fxs, sh);
+                    SXF[2 * idx + 1] = fx_coord(qy, fxs, sh);
+                }
+                int cq = P.cell_s[q] - cbase;
+                // FP32 offsets, two sources per float4: (x_a, x_b, y_a, y_b)
+                SF[4 * (idx >> 1) + (idx & 1)] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
+                SF[4 * (idx >> 1) + 2 + (idx & 1)] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
+            }
+            if (MODE == 0 || MODE == 3) SW[idx] = w[q];
         }
         __syncthreads();
-        // FP32 filter: one accept bit per staged source. Sources in the thin band
-        // around the cutoff get a second bit and are settled afterwards by the
-        // exact FP64 test, in a loop of its own so that no FP64 instruction is
-        // issued (predicated or not) for the ordinary candidates. Two
-        // candidates per packed f32x2 step; a partial last word is masked.
         const int nw = (ns + 31) >> 5;
-        const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
-        for (int wi = qtr; wi < nw; wi += kMvQ) {
-            uint32_t m = 0, mh = 0;
-            if (active) {
-                const float4* S4 = reinterpret_cast<const float4*>(SF) + wi * 16;
+        const int64_t mbase = (MODE >= 2) ? (FS.mask_off[item] + (base >> 5)) * T : 0;
+        int steps = 0;   // MODE 1: this lane's walk steps in this pass
+        if (kFilter) {
+            // FP32 filter: one accept bit per staged source. Sources in the thin
+            // band around the cutoff get a second bit and are settled afterwards
+            // by the exact FP64 test, in a loop of its own so that no FP64
+            // instruction is issued (predicated or not) for the ordinary
+            // candidates. Two candidates per packed f32x2 step; a partial last
+            // word is masked.
+            const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
+            for (int wi = qtr; wi < nw; wi += kMvQ) {
+                uint32_t m = 0, mh = 0;
+                if (active) {
+                    const float4* S4 = reinterpret_cast<const float4*>(SF) + wi * 16;
 #pragma unroll
-                for (int b = 0; b < 32; b += 2) {
-                    const float4 v = S4[b >> 1];
-                    const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
-                    const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
-                    const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
-                    m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
-                    mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
+                    for (int b = 0; b < 32; b += 2) {
+                        const float4 v = S4[b >> 1];
+                        const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
+                        const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
+                        const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
+                        m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
+                        mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
+                    }
+                    const int lim = ns - wi * 32;
+                    if (lim < 32) {
+                        const uint32_t keep = (1u << lim) - 1u;
+                        m &= keep;
+                        mh &= keep;
+                    }
                 }
-                const int lim = ns - wi * 32;
-                if (lim < 32) {
-                    const uint32_t keep = (1u << lim) - 1u;
-                    m &= keep;
-                    mh &= keep;
+                uint32_t band = mh & ~m;
+                while (band != 0u) {
+                    const int b = __ffs(band) - 1;
+                    band &= band - 1u;
+                    const int idx = wi * 32 + b;
+                    double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
+                    if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
                 }
+                MASK[wi * T + t] = m;
+                if (MODE == 1) steps += (__popc(m) + 1) >> 1;
+                if (MODE == 2) FS.mask[mbase + (int64_t)wi * T + t] = m;
             }
-            uint32_t band = mh & ~m;
-            while (band != 0u) {
-                const int b = __ffs(band) - 1;
-                band &= band - 1u;
-                const int idx = wi * 32 + b;
-                double ex = __dsub_rn(xi, SX[2 * idx]), ey = __dsub_rn(yi, SX[2 * idx + 1]);
-                if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
-            }
-            MASK[wi * T + t] = m;
+        } else {   // MODE 3: the stored masks of this lane's words
+            for (int wi = qtr; wi < nw; wi += kMvQ) MASK[wi * T + t] = __ldg(FS.mask + mbase + (int64_t)wi * T + t);
+        }
+        if (MODE == 1) {
+            slots += 64 * (long long)__reduce_max_sync(0xffffffffu, steps);
+            continue;
+        }
+        // this warp's slots in this pass: after the earlier warps' (warp
+        // order), after the block's earlier passes
+        int64_t wbase = 0;
+        if (MODE >= 2) {
+            for (int wi = qtr; wi < nw; wi += kMvQ) steps += (__popc(MASK[wi * T + t]) + 1) >> 1;
+            const int wsteps = __reduce_max_sync(0xffffffffu, steps);
+            const long long ws = lane == 0 ? 64 * (long long)wsteps : 0LL;
+            long long total = 0;
+            const long long pre = block_excl_scan(ws, scan_sh, total);
+            wbase = vbase + __shfl_sync(0xffffffffu, pre, 0);
+            vbase += total;
         }
         // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
         // (up to two sources of the current mask word per step: two independent
@@ -180,7 +267,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             };
             int wi = qtr;
             uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
-            for (;;) {
+            for (int64_t at = wbase + 2 * lane;; at += 64) {   // MODE 2, 3: this lane's slot of the step
                 while (cur == 0u && wi + kMvQ < nw) {
                     wi += kMvQ;
                     cur = MASK[wi * T + t];
@@ -193,18 +280,40 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                     const bool two = cur != 0u;
                     const int i1 = two ? wi * 32 + (__ffs(cur) - 1) : i0;
                     cur &= cur - (two ? 1u : 0u);
-                    const double k0 = kval(i0), k1 = kval(i1);
-                    acc = fma(k0, SW[i0], acc);
-                    if (two) acc = fma(k1, SW[i1], acc);
+                    if constexpr (MODE == 3) {
+                        const double2 kv = __ldg(reinterpret_cast<const double2*>(FS.val + at));
+                        acc = fma(kv.x, SW[i0], acc);
+                        if (two) acc = fma(kv.y, SW[i1], acc);
+                    } else {
+                        const double k0 = kval(i0), k1 = kval(i1);
+                        if constexpr (MODE == 2) {
+                            *reinterpret_cast<double2*>(FS.val + at) = make_double2(k0, two ? k1 : 0.0);
+                        } else {
+                            acc = fma(k0, SW[i0], acc);
+                            if (two) acc = fma(k1, SW[i1], acc);
+                        }
+                    }
+                } else if constexpr (MODE == 2) {
+                    *reinterpret_cast<double2*>(FS.val + at) = make_double2(0.0, 0.0);
                 }
             }
         };
-        if (F == 52) walk(std::true_type{});   // block-uniform
-        else walk(std::false_type{});
+        if constexpr (MODE == 3) {
+            walk(std::true_type{});   // the kernel-value branch is not taken
+        } else {
+            if (F == 52) walk(std::true_type{});   // block-uniform
+            else walk(std::false_type{});
+        }
     }
-    PART[qtr * T + t] = acc;
-    __syncthreads();
-    if (qtr == 0 && active) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
+    if constexpr (MODE == 1) {
+        long long total = 0;
+        block_excl_scan(lane == 0 ? slots : 0LL, scan_sh, total);
+        if (tid == 0) FS.cnt[item] = total;
+    } else if constexpr (MODE == 0 || MODE == 3) {
+        PART[qtr * T + t] = acc;
+        __syncthreads();
+        if (qtr == 0 && active) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
+    }
 }
 
 
@@ -600,32 +709,49 @@ MvParams mv_params(const rbf_ctx* ctx)
     return P;
 }
 
-template <int T>
-rbf_status prepare_f64(rbf_ctx* ctx)
+template <int T, int MODE>
+rbf_status prepare_f64_mode(rbf_ctx* ctx)
 {
-    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)mv64_smem(T, kMvStage)));
-    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    RBF_CUDA(ctx, cudaFuncSetAttribute(k_matvec_f64<T, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared));
     return RBF_OK;
 }
 
 template <int T>
-rbf_status launch_f64(rbf_ctx* ctx, const MvParams& P, int64_t nwork, const double* w, double* y, cudaStream_t st)
+rbf_status prepare_f64(rbf_ctx* ctx)
 {
-    RBF_LAUNCH(ctx, k_matvec_f64<T>, (unsigned)nwork, T * kMvQ, mv64_smem(T, P.stage), st, P, w, y);
+    RBF_CHECK((prepare_f64_mode<T, 0>(ctx)));
+    RBF_CHECK((prepare_f64_mode<T, 1>(ctx)));
+    RBF_CHECK((prepare_f64_mode<T, 2>(ctx)));
+    return prepare_f64_mode<T, 3>(ctx);
+}
+
+template <int T, int MODE>
+rbf_status launch_f64(rbf_ctx* ctx, const MvParams& P, int64_t nwork, const double* w, double* y,
+                      const F64Store& FS, cudaStream_t st)
+{
+    RBF_LAUNCH(ctx, (k_matvec_f64<T, MODE>), (unsigned)nwork, T * kMvQ, mv64_smem(T, P.stage), st, P, w, y, FS);
     return RBF_OK;
 }
 
-rbf_status dispatch_f64(rbf_ctx* ctx, MvParams P, int64_t nwork, const double* w, double* y, cudaStream_t st)
+template <int MODE>
+rbf_status dispatch_f64_mode(rbf_ctx* ctx, MvParams P, int64_t nwork, const double* w, double* y, const F64Store& FS,
+                             cudaStream_t st)
 {
     if (nwork == 0) return RBF_OK;
     P.stage = stage_for(ctx, kMvStage);
     switch (ctx->tile64) {
-    case 32: return launch_f64<32>(ctx, P, nwork, w, y, st);
-    case 64: return launch_f64<64>(ctx, P, nwork, w, y, st);
-    default: return launch_f64<128>(ctx, P, nwork, w, y, st);
+    case 32: return launch_f64<32, MODE>(ctx, P, nwork, w, y, FS, st);
+    case 64: return launch_f64<64, MODE>(ctx, P, nwork, w, y, FS, st);
+    default: return launch_f64<128, MODE>(ctx, P, nwork, w, y, FS, st);
     }
+}
+
+rbf_status dispatch_f64(rbf_ctx* ctx, MvParams P, int64_t nwork, const double* w, double* y, cudaStream_t st)
+{
+    return dispatch_f64_mode<0>(ctx, P, nwork, w, y, F64Store{}, st);
 }
 
 template <int T>
@@ -712,7 +838,77 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
         P.work = ctx->al.w64.p;
         return dispatch_f64(ctx, P, ctx->al.n64, w, y, st);
     }
+    if (ctx->f64s.valid && ctx->f64s.tile == ctx->tile64) {   // the kept pair values, the same sums
+        F64Store FS{};
+        FS.val_off = ctx->f64s.val_off.p;
+        FS.mask_off = ctx->f64s.mask_off.p;
+        FS.val = ctx->f64s.val.p;
+        FS.mask = ctx->f64s.mask.p;
+        return dispatch_f64_mode<3>(ctx, mv_params(ctx), ctx->n_work, w, y, FS, st);
+    }
     return dispatch_f64(ctx, mv_params(ctx), ctx->n_work, w, y, st);
+}
+
+void f64_store_release(rbf_ctx* ctx)
+{
+    F64Keep& K = ctx->f64s;
+    K.valid = false;
+    release(ctx, K.val.p);
+    K.val = {};
+    release(ctx, K.mask.p);
+    K.mask = {};
+}
+
+rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st)
+{
+    F64Keep& K = ctx->f64s;
+    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64) || ctx->n_work == 0) return RBF_OK;
+    if (ctx->sym64 && ctx->sym64_mode == 0) return RBF_OK;   // the symmetric kernel serves those problems
+    if (ctx->capturing) return RBF_OK;
+    K.valid = false;
+    const int64_t nwork = ctx->n_work;
+    MvParams P = mv_params(ctx);
+    P.active = nullptr;   // every problem's pairs
+    RBF_CHECK(ensure(ctx, K.cnt, (size_t)nwork + 1));
+    RBF_CHECK(ensure(ctx, K.nwords, (size_t)nwork + 1));
+    RBF_CHECK(ensure(ctx, K.val_off, (size_t)nwork + 1));
+    RBF_CHECK(ensure(ctx, K.mask_off, (size_t)nwork + 1));
+    F64Store FS{};
+    FS.cnt = K.cnt.p;
+    FS.nwords = K.nwords.p;
+    RBF_CHECK(dispatch_f64_mode<1>(ctx, P, nwork, nullptr, nullptr, FS, st));
+    RBF_CHECK(exclusive_scan_i64(ctx, K.cnt.p, K.val_off.p, nwork, st));
+    RBF_CHECK(exclusive_scan_i64(ctx, K.nwords.p, K.mask_off.p, nwork, st));
+    int64_t tot[2] = {0, 0};
+    RBF_CUDA(ctx, cudaMemcpyAsync(&tot[0], K.val_off.p + nwork, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&tot[1], K.mask_off.p + nwork, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(ctx, cudaStreamSynchronize(st));
+    const int64_t nmask = tot[1] * ctx->tile64;
+    const size_t need = (size_t)tot[0] * sizeof(double) + (size_t)nmask * sizeof(uint32_t);
+    // only when it fits beside everything else: the device's free memory less
+    // a margin (and the context's own limit); otherwise the matvec stays
+    // matrix-free
+    size_t free_b = 0, total_b = 0;
+    RBF_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
+    const size_t have = (K.val.count * sizeof(double) + K.mask.count * sizeof(uint32_t));
+    const size_t margin = (size_t)8 << 30;
+    if (need > have && need - have + margin > free_b) return RBF_OK;
+    if (ctx->mem_limit > 0 && ctx->dev_bytes + (int64_t)(need > have ? need - have : 0) > ctx->mem_limit) return RBF_OK;
+    // an allocation that fails all the same (the device shared with another
+    // process) leaves the matvec matrix-free rather than failing the solve
+    if (ensure(ctx, K.val, (size_t)tot[0]) != RBF_OK || ensure(ctx, K.mask, (size_t)nmask) != RBF_OK) {
+        f64_store_release(ctx);
+        return RBF_OK;
+    }
+    FS = F64Store{};
+    FS.val_off = K.val_off.p;
+    FS.mask_off = K.mask_off.p;
+    FS.val = K.val.p;
+    FS.mask = K.mask.p;
+    RBF_CHECK(dispatch_f64_mode<2>(ctx, P, nwork, nullptr, nullptr, FS, st));
+    K.valid = true;
+    K.tile = ctx->tile64;
+    return RBF_OK;
 }
 
 // s = sum_j k(|t - x_j|) w_j for the cell-sorted targets of another point

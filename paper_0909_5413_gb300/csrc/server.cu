@@ -102,6 +102,8 @@ rbf_status rbf_server::run(Slot& s, Ticket& t)
         // Arnoldi steps, whose grid would have to share the SMs with the
         // other slots' kernels
         c = rbf_set_option(s.ctx, RBF_OPT_FUSED_STEP, 0);
+        // nor kept FP64 pair values: admission counts each request's own footprint
+        if (c == RBF_OK) c = rbf_set_option(s.ctx, RBF_OPT_STORE_F64, 0);
         if (c != RBF_OK) return c;
     }
     const int64_t n = r.n;
