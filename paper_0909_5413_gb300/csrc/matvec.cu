@@ -60,6 +60,8 @@ __host__ __device__ constexpr size_t mv64_smem(int T, int S)
 // that step is written as zeros and never read), so that a step loads 512
 // contiguous bytes per warp. A warp takes, per pass, as many steps as its
 // busiest lane: sum over the lane's words of ceil(popcount / 2).
+constexpr int kReplayAhead = 4;   // replay: walk steps whose values are in flight together
+
 struct F64Store {
     int64_t* cnt;               // MODE 1: value slots of each item (doubles, a multiple of 64)
     int64_t* nwords;            // MODE 1: 32-source words of each item (all passes)
@@ -246,9 +248,10 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         // this warp's slots in this pass: after the earlier warps' (warp
         // order), after the block's earlier passes
         int64_t wbase = 0;
+        int wsteps = 0;   // MODE 2, 3: the warp's steps in this pass
         if (MODE >= 2) {
             for (int wi = qtr; wi < nw; wi += kMvQ) steps += (__popc(MASK[wi * T + t]) + 1) >> 1;
-            const int wsteps = __reduce_max_sync(0xffffffffu, steps);
+            wsteps = __reduce_max_sync(0xffffffffu, steps);
             const long long ws = lane == 0 ? 64 * (long long)wsteps : 0LL;
             long long total = 0;
             const long long pre = block_excl_scan(ws, scan_sh, total);
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             };
             int wi = qtr;
             uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
-            for (int64_t at = wbase + 2 * lane;; at += 64) {   // MODE 2, 3: this lane's slot of the step
+            for (int64_t at = wbase + 2 * lane;; at += 64) {   // MODE 2: this lane's slot of the step
                 while (cur == 0u && wi + kMvQ < nw) {
                     wi += kMvQ;
                     cur = MASK[wi * T + t];
@@ -280,18 +283,12 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                     const bool two = cur != 0u;
                     const int i1 = two ? wi * 32 + (__ffs(cur) - 1) : i0;
                     cur &= cur - (two ? 1u : 0u);
-                    if constexpr (MODE == 3) {
-                        const double2 kv = __ldg(reinterpret_cast<const double2*>(FS.val + at));
-                        acc = fma(kv.x, SW[i0], acc);
-                        if (two) acc = fma(kv.y, SW[i1], acc);
+                    const double k0 = kval(i0), k1 = kval(i1);
+                    if constexpr (MODE == 2) {
+                        *reinterpret_cast<double2*>(FS.val + at) = make_double2(k0, two ? k1 : 0.0);
                     } else {
-                        const double k0 = kval(i0), k1 = kval(i1);
-                        if constexpr (MODE == 2) {
-                            *reinterpret_cast<double2*>(FS.val + at) = make_double2(k0, two ? k1 : 0.0);
-                        } else {
-                            acc = fma(k0, SW[i0], acc);
-                            if (two) acc = fma(k1, SW[i1], acc);
-                        }
+                        acc = fma(k0, SW[i0], acc);
+                        if (two) acc = fma(k1, SW[i1], acc);
                     }
                 } else if constexpr (MODE == 2) {
                     *reinterpret_cast<double2*>(FS.val + at) = make_double2(0.0, 0.0);
@@ -299,7 +296,36 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             }
         };
         if constexpr (MODE == 3) {
-            walk(std::true_type{});   // the kernel-value branch is not taken
+            // the same walk over the stored masks, its step count known: the
+            // values of kReplayAhead steps are loaded before they are used
+            // (lane l's slot of step j at 64 j + 2 l); a lane's j-th step is
+            // the walk's j-th, as when they were stored
+            const double2* vp = reinterpret_cast<const double2*>(FS.val + wbase) + lane;
+            int wi = qtr;
+            uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
+            for (int j0 = 0; j0 < wsteps; j0 += kReplayAhead) {
+                double2 kv[kReplayAhead];
+#pragma unroll
+                for (int k = 0; k < kReplayAhead; ++k)
+                    kv[k] = j0 + k < wsteps ? __ldg(vp + (int64_t)(j0 + k) * 32) : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int k = 0; k < kReplayAhead; ++k) {
+                    while (cur == 0u && wi + kMvQ < nw) {
+                        wi += kMvQ;
+                        cur = MASK[wi * T + t];
+                    }
+                    if (cur != 0u) {
+                        const int i0 = wi * 32 + (__ffs(cur) - 1);
+                        cur &= cur - 1u;
+                        acc = fma(kv[k].x, SW[i0], acc);
+                        if (cur != 0u) {
+                            const int i1 = wi * 32 + (__ffs(cur) - 1);
+                            cur &= cur - 1u;
+                            acc = fma(kv[k].y, SW[i1], acc);
+                        }
+                    }
+                }
+            }
         } else {
             if (F == 52) walk(std::true_type{});   // block-uniform
             else walk(std::false_type{});
