@@ -68,6 +68,41 @@ MATVEC_F64_REV = "fixed-point-v5"
 # DRAM read + write of one launch on the 1024 x 1024 lattice (ncu, this revision)
 MATVEC_F64_TRAFFIC = {"fixed-point-v5": 37_978_112}
 FLOPS_PER_PAIR_F64 = 26   # FP64-equivalent flops of one pair (dx, dy 2; r2 3; argument 1; exp 18; accumulate 2)
+# The replay of kept pair values (RBF_OPT_STORE_F64) reads, per launch, the
+# values and masks (rbf_store_f64_bytes) plus w and y (16 B per point), and
+# issues one DFMA per pair: bound by the larger of the two times.
+MATVEC_F64_REPLAY_REV = "replay-v2"
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    """The measured copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def f64_replay_roofline(pairs: int, n: int, store_bytes: int, avg_s: float, launches: int, note: str = "") -> dict:
+    """Roofline object of the FP64 replay: the HBM bytes it must read and write
+    against the measured copy bandwidth, and its DFMAs against the FP64 pipe."""
+    hbm_gbs, src = hbm_peak_gbs()
+    nbytes = store_bytes + 16 * n
+    t_hbm = nbytes / (hbm_gbs * 1e9)
+    t_dfma = pairs / FP64_DFMA_PEAK_PAIRS
+    hbm = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+           "frac": t_hbm / avg_s, "peak_note": f"copy bandwidth, {src}"}
+    alu = {"bound": "alu", "achieved": pairs / avg_s / 1e9, "peak": FP64_DFMA_PEAK_PAIRS / 1e9, "unit": "Gpair/s",
+           "frac": t_dfma / avg_s,
+           "peak_note": "FP64 pipe: one DFMA per in-cutoff pair, 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    main, other = (hbm, alu) if t_hbm >= t_dfma else (alu, hbm)
+    out = {"kernel": "k_matvec_f64 (replay of the kept pair values)", **main, "traffic": None,
+           "other_bound": other, "kernel_rev": MATVEC_F64_REPLAY_REV, "pairs_per_launch": pairs,
+           "algorithmic_bytes_per_launch": nbytes, "store_bytes": store_bytes,
+           "store_bytes_per_pair": store_bytes / pairs, "avg_launch_ms": avg_s * 1e3, "launches": launches}
+    if note:
+        out["note"] = note
+    return out
 
 
 def f64_matvec_roofline(pairs: int, avg_s: float, launches: int, traffic, note: str = "") -> dict:
@@ -465,6 +500,7 @@ def run_ours(args, ws, rank, local):
     # dominant kernel: the truncated matvec of the timed precision
     roofline, roof64 = None, None
     pairs = rbf.rbf_count_neighbors(h)
+    store_bytes = rbf.rbf_store_f64_bytes(h)   # the FP64 products replayed kept values
     n_mv, t_mv = prof[dominant]
     if n_mv and mode == "mixed":
         inner = args.inner_cutoff > 0
@@ -481,6 +517,8 @@ def run_ours(args, ws, rank, local):
             roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
                                         "7168 x 7168 lattice x N / 51,380,224; algorithmic 16 B per point plus "
                                         "40 B per point of slots")
+    elif n_mv and store_bytes:
+        roofline = f64_replay_roofline(pairs, p.n, store_bytes, t_mv / n_mv / 1e3, n_mv)
     elif n_mv:
         default_cfg = (cfg.cell_size in (0.0, p.cutoff)) and cfg.tile_f64 in (0, 128)
         traffic = MATVEC_F64_TRAFFIC.get(MATVEC_F64_REV) if default_cfg else None
@@ -488,14 +526,16 @@ def run_ours(args, ws, rank, local):
             traffic = traffic * p.n / 1048576.0
         roofline = f64_matvec_roofline(pairs, t_mv / n_mv / 1e3, n_mv, traffic)
         if traffic is not None:
-            roofline["traffic_note"] = ("ncu DRAM read + write of one launch (symmetric kernel and gather) on the "
-                                        "7168 x 7168 lattice x N / 51,380,224; algorithmic 16 B per point plus "
-                                        "40 B per point of slots")
+            roofline["traffic_note"] = ("ncu DRAM read + write of one launch on the 1024 x 1024 lattice x "
+                                        "N / 1,048,576")
     # the FP64 matvec (outer residuals of the mixed form) from the breakdown step
     n64, t64 = prof_all[rbf.RBF_PROF_MATVEC_F64]
     if mode == "mixed" and n64:
-        roof64 = f64_matvec_roofline(pairs, t64 / n64 / 1e3, n64, None,
-                                     note="outer FP64 residuals of the mixed solve, from the breakdown step")
+        note = "outer FP64 residuals of the mixed solve, from the breakdown step"
+        if store_bytes:
+            roof64 = f64_replay_roofline(pairs, p.n, store_bytes, t64 / n64 / 1e3, n64, note=note)
+        else:
+            roof64 = f64_matvec_roofline(pairs, t64 / n64 / 1e3, n64, None, note=note)
     breakdown = {nm: {"launches": prof_all[k][0], "ms": round(prof_all[k][1], 3)} for nm, k in
                  (("matvec_f64", 0), ("matvec_f32", 1), ("rasm_apply", 2), ("orthogonalisation", 3),
                   ("rasm_setup", 4), ("binning", 5))}

@@ -409,6 +409,11 @@ const char* rbf_last_error(rbf_ctx* ctx);
 uint64_t rbf_launch_count(rbf_ctx* ctx);
 /* Device bytes the context currently holds. */
 int64_t rbf_device_bytes(rbf_ctx* ctx);
+/* Bytes of the FP64 pair values and accept masks kept for the current
+ * binning (RBF_OPT_STORE_F64; every FP64 product reads them once), 0 when
+ * none are kept: before the first solve after a binning, when they did not
+ * fit, or with the option off. */
+int64_t rbf_store_f64_bytes(rbf_ctx* ctx);
 /* Context options (no counterpart in the paper). */
 enum {
     /* The fused Arnoldi step of a batched mixed solve on the inner grid: each

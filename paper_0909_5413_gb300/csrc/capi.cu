@@ -277,6 +277,8 @@ uint64_t rbf_launch_count(rbf_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int64_t rbf_device_bytes(rbf_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
 
+int64_t rbf_store_f64_bytes(rbf_ctx* ctx) { return ctx && ctx->f64s.valid ? ctx->f64s.bytes : 0; }
+
 rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
 {
     if (!ctx) return RBF_ERR_INVALID_ARG;

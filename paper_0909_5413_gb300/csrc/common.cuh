@@ -76,6 +76,7 @@ struct Prob {
 struct F64Keep {
     bool valid = false;
     int tile = 0;
+    int64_t bytes = 0;   // values and masks of the current binning
     rbf::DevArray<int64_t> cnt, nwords, val_off, mask_off;
     rbf::DevArray<double> val;
     rbf::DevArray<uint32_t> mask;

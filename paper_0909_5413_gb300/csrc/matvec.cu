@@ -934,6 +934,7 @@ rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st)
     RBF_CHECK(dispatch_f64_mode<2>(ctx, P, nwork, nullptr, nullptr, FS, st));
     K.valid = true;
     K.tile = ctx->tile64;
+    K.bytes = (int64_t)need;
     return RBF_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTED = ["rbf_create", "rbf_destroy", "rbf_bin", "rbf_matvec", "rbf_rasm_setu
             "rbf_request_footprint", "rbf_debug_kernel_pairs", "rbf_eval", "rbf_tune",
             "rbf_count_candidates", "rbf_profile_classes", "rbf_set_memory_limit",
             "rbf_count_pairs", "rbf_rasm_factor_counts",
-            "rbf_debug_inner_matvec", "rbf_set_option"]
+            "rbf_debug_inner_matvec", "rbf_set_option", "rbf_store_f64_bytes"]
 
 RBF_OPT_FUSED_STEP, RBF_OPT_SYMMETRIC_F32, RBF_OPT_BARRIER_SPIN_LIMIT, RBF_OPT_BARRIER_EXTRA_BLOCK = 1, 2, 3, 4
 RBF_OPT_SYMMETRIC_F64 = 5
@@ -136,6 +136,8 @@ def load(path: str | None = None):
     L.rbf_launch_count.restype = C.c_uint64
     L.rbf_device_bytes.argtypes = [P]
     L.rbf_device_bytes.restype = C.c_int64
+    L.rbf_store_f64_bytes.argtypes = [P]
+    L.rbf_store_f64_bytes.restype = C.c_int64
     L.rbf_set_memory_limit.argtypes = [P, C.c_int64]
     L.rbf_set_option.argtypes = [P, C.c_int, C.c_int64]
     L.rbf_profile_enable.argtypes = [P, C.c_int]
@@ -162,7 +164,8 @@ def load(path: str | None = None):
     L.rbf_request_footprint.restype = C.c_int64
     for name in EXPORTED:
         if name not in ("rbf_destroy", "rbf_status_string", "rbf_last_error", "rbf_launch_count",
-                        "rbf_device_bytes", "rbf_server_destroy", "rbf_server_clock", "rbf_request_footprint"):
+                        "rbf_device_bytes", "rbf_store_f64_bytes", "rbf_server_destroy", "rbf_server_clock",
+                        "rbf_request_footprint"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -343,6 +346,11 @@ def rbf_launch_count(ctx) -> int:
 
 def rbf_device_bytes(ctx) -> int:
     return int(load().rbf_device_bytes(ctx))
+
+
+def rbf_store_f64_bytes(ctx) -> int:
+    """Bytes of the FP64 pair values and masks kept for the current binning (0: none)."""
+    return int(load().rbf_store_f64_bytes(ctx))
 
 
 def rbf_set_option(ctx, option: int, value: int) -> None:

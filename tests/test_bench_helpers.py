@@ -34,6 +34,25 @@ def test_f64_roofline_object():
     assert bench.f64_matvec_roofline(pairs, avg_s, 185, None)["traffic"] is None
 
 
+def test_f64_replay_roofline_takes_the_larger_bound():
+    """The replay's two bounds: bytes over the measured copy bandwidth and one
+    DFMA per pair; the slower one is the object's bound, the other beside it."""
+    hbm, _ = bench.hbm_peak_gbs()
+    pairs, n = 18_543_323_276, 51_380_224
+    dfma_s = pairs / bench.FP64_DFMA_PEAK_PAIRS
+    # bytes that take exactly twice the DFMA time: HBM-bound at half speed
+    store = int(2 * dfma_s * hbm * 1e9) - 16 * n
+    r = bench.f64_replay_roofline(pairs, n, store, 4 * dfma_s, 7)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == hbm
+    assert abs(r["frac"] - 0.5) < 1e-9
+    assert abs(r["achieved"] / r["peak"] - r["frac"]) < 1e-9
+    assert r["other_bound"]["bound"] == "alu" and abs(r["other_bound"]["frac"] - 0.25) < 1e-9
+    assert r["algorithmic_bytes_per_launch"] == store + 16 * n and r["traffic"] is None
+    # few bytes: the FP64 pipe bounds it
+    r = bench.f64_replay_roofline(pairs, n, 8 * n, 2 * dfma_s, 7)
+    assert r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-9 and r["other_bound"]["bound"] == "hbm"
+
+
 def test_f32_roofline_counts_in_cutoff_pairs_not_candidates():
     pairs, cand, avg_s = 191_000_000, 542_600_000, 127e-6
     r = bench.f32_matvec_roofline(pairs, cand, avg_s, 180, None, "inner")

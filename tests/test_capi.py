@@ -40,6 +40,28 @@ def test_binding_covers_header(lib):
     assert sorted(rbf.EXPORTED) == header_functions()
 
 
+def test_binding_return_types_follow_the_header(lib):
+    """Each function's ctypes return type matches its declaration (a 64-bit
+    count read as a C int would wrap above 2^31)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"^\s*((?:const\s+)?[a-z_0-9]+\s*\**)\s*(rbf_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    want = {"rbf_status": C.c_int, "int": C.c_int, "int64_t": C.c_int64, "uint64_t": C.c_uint64,
+            "double": C.c_double, "void": None, "constchar*": C.c_char_p}
+    seen = 0
+    for ret, name in decls:
+        key = re.sub(r"\s+", "", ret)
+        assert key in want, (name, ret)
+        got = getattr(lib, name).restype
+        exp = want[key]
+        if exp is None:
+            assert got is None, name
+        else:
+            assert got is not None and C.sizeof(got) == C.sizeof(exp), (name, got, exp)
+            assert (got in (C.c_char_p, C.c_double)) == (exp in (C.c_char_p, C.c_double)), name
+        seen += 1
+    assert seen == len(header_functions())
+
+
 def test_status_strings(lib):
     from paper_0909_5413_gb300 import rbf
     assert rbf.rbf_status_string(0) == "ok"

@@ -56,11 +56,13 @@ def run(rbf, p, store, mixed, limit=0, tile=0):
         w.zero_()
     st, info = ctx.solve(fd, w, cfg, check=False)
     held = rbf.rbf_device_bytes(h)
+    d = info.as_dict()
+    d["store_bytes"] = rbf.rbf_store_f64_bytes(h)
     # a product after the solve (a replay when the values were kept)
     v = np.random.default_rng(4).standard_normal(p.n)
     y = torch.empty(p.n, dtype=torch.float64, device="cuda")
     rbf.rbf_matvec(h, dev(v), y)
-    out = (st, info.as_dict(), host(w), host(y), v, held, pairs)
+    out = (st, d, host(w), host(y), v, held, pairs)
     ctx.close()
     return out
 
@@ -75,8 +77,9 @@ def test_replay_matches_matrix_free_bit_for_bit(rbf, n_side, ratio, mixed):
     np.testing.assert_array_equal(w1, w0)
     np.testing.assert_array_equal(y1, y0)
     assert i1["iters"] == i0["iters"]
-    # one FP64 value per nonzero of the truncated matrix is kept
-    assert held1 - held0 >= 8 * pairs
+    # at least one FP64 value per nonzero of the truncated matrix is kept
+    assert held1 - held0 >= i1["store_bytes"] >= 8 * pairs
+    assert i0["store_bytes"] == 0
     ref = O.matvec_cutoff(p.xy, v, p.sigma, p.cutoff)
     assert np.max(np.abs(y1 - ref)) <= 1e-13 * np.max(np.abs(ref))
 
@@ -90,6 +93,7 @@ def test_values_that_do_not_fit_stay_matrix_free(rbf):
     assert 8 * pairs > 1 << 20
     assert s1 == 0 and s0 == 0
     assert held1 - held0 < 1 << 18
+    assert i1["store_bytes"] == 0
     np.testing.assert_array_equal(w1, w0)
     np.testing.assert_array_equal(y1, y0)
 
@@ -113,10 +117,12 @@ def test_kept_values_follow_a_new_binning(rbf):
         p = W.lattice_problem(n_side, ratio, seed=970 + k, rhs="four_gaussians")
         cfg = rbf.config_for(p)
         ctx.bin(dev(p.xy), cfg)
+        assert rbf.rbf_store_f64_bytes(ctx.handle) == 0   # the previous binning's values are gone
         ctx.rasm_setup(cfg)
         w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
         st, info = ctx.solve(dev(p.f), w, cfg, check=False)
         assert st == 0
+        assert rbf.rbf_store_f64_bytes(ctx.handle) >= 8 * rbf.rbf_count_pairs(ctx.handle, 0)
         v = np.random.default_rng(k).standard_normal(p.n)
         y = torch.empty(p.n, dtype=torch.float64, device="cuda")
         rbf.rbf_matvec(ctx.handle, dev(v), y)
@@ -147,8 +153,10 @@ def test_switching_the_store_off_frees_it(rbf):
     st, _ = ctx.solve(dev(p.f), w, cfg, check=False)
     assert st == 0
     held = rbf.rbf_device_bytes(h)
+    assert rbf.rbf_store_f64_bytes(h) >= 8 * pairs
     rbf.rbf_set_option(h, rbf.RBF_OPT_STORE_F64, 0)
     assert held - rbf.rbf_device_bytes(h) >= 8 * pairs
+    assert rbf.rbf_store_f64_bytes(h) == 0
     # matrix-free from here, the same bits
     v = dev(np.random.default_rng(5).standard_normal(p.n))
     y0 = torch.empty(p.n, dtype=torch.float64, device="cuda")
