@@ -9,14 +9,16 @@
 // fixed-point offsets, table-driven exp in 64-bit fixed point, FP64 bits
 // assembled at the end) and the FP64 pipe only does the accumulate FMA. One
 // block per (cell, T targets), T = 32, 64 or 128 (the tile; autotuned with the
-// cell size by rbf_tune), with four warps per target set: the stencil's
-// sources are staged in shared memory and split by 32-source word among the
-// four quarters (word w goes to quarter w mod 4); each target tests its
-// candidates in FP32 on scaled cell-local offsets (a thin band around the
-// cutoff is re-tested exactly in FP64 with the same IEEE operations as the
-// index-list definition) and keeps a bitmask of accepted sources; each warp
-// then walks its lanes' accepted sources in lockstep. The four partial sums of
-// a target are added in quarter order (deterministic).
+// cell size by rbf_tune), with four threads per target (its quarters) mapped
+// densely onto the block's 4T threads, so that a cell with fewer than T
+// targets leaves whole warps idle rather than lanes of every warp. The
+// stencil's sources are staged in shared memory; each target tests its
+// candidates in FP32 on scaled cell-local offsets, word w of 32 sources by
+// quarter w mod 4 (a thin band around the cutoff is re-tested exactly in FP64
+// with the same IEEE operations as the index-list definition), keeping a
+// bitmask of accepted sources; each quarter then walks one of four near-equal
+// contiguous parts of its target's accepted sources, two per step. The four
+// partial sums of a target are added in quarter order (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -59,7 +61,8 @@ __host__ __device__ constexpr size_t mv64_smem(int T, int S)
 // two values of that step at 2l and 2l + 1 (a slot of a lane with nothing at
 // that step is written as zeros and never read), so that a step loads 512
 // contiguous bytes per warp. A warp takes, per pass, as many steps as its
-// busiest lane: sum over the lane's words of ceil(popcount / 2).
+// busiest lane: ceil(share / 2), its share being a quarter of its target's
+// accepted sources in the pass.
 constexpr int kReplayAhead = 4;   // replay: walk steps whose values are in flight together
 
 struct F64Store {
@@ -120,9 +123,9 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     uint32_t* MASK = (uint32_t*)(SF + 2 * kStage);
     __shared__ int row_beg[kMvMaxRows], row_pre[kMvMaxRows + 1];
     __shared__ long long scan_sh[kThreads / 32];
+    __shared__ int CNT[kThreads];   // accepted sources per (quarter, target) in this pass
 
-    const int tid = threadIdx.x;
-    const int t = tid & (T - 1), qtr = tid / T;   // target, quarter (warp-uniform)
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t item = blockIdx.x;
     const int cell = P.work[2 * item], first = P.work[2 * item + 1];
     const int pcell = P.pid_cell[cell];
@@ -136,8 +139,13 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     const unsigned long long M = pr.fx_M;
     const float ca = pr.ca, rc2f_lo = pr.rc2f_lo, rc2f_hi = pr.rc2f_hi;
     const int cb = P.tcell_start[cell], ce = P.tcell_start[cell + 1];
+    // the item's targets (at most T) and their quarters, densely over the
+    // block's threads: thread k < kMvQ * nt takes target k % nt and quarter
+    // k / nt; the threads past them (whole warps but one) stay idle
+    const int nt = min(T, ce - cb - first);
+    const bool active = tid < kMvQ * nt;
+    const int t = active ? tid % nt : 0, qtr = active ? tid / nt : 0;
     const int p = cb + first + t;
-    const bool active = p < ce;
     const int cx = (cell - cbase) % ncx, cy = (cell - cbase) / ncx;
     const int y0 = max(cy - kst, 0), y1 = min(cy + kst, ncy - 1);
     const int x0 = max(cx - kst, 0), x1 = min(cx + kst, ncx - 1);
@@ -167,7 +175,6 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
     __syncthreads();
     const int S = row_pre[nrow];
     if (MODE == 1 && tid == 0) FS.nwords[item] = (S + 31) / 32;
-    const int lane = tid & 31;
     int64_t vbase = (MODE >= 2) ? FS.val_off[item] : 0;   // this pass's first slot (block-uniform)
     long long slots = 0;                                  // MODE 1: this warp's slots so far
     double acc = 0.0;
@@ -197,8 +204,8 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         __syncthreads();
         const int nw = (ns + 31) >> 5;
         const int64_t mbase = (MODE >= 2) ? (FS.mask_off[item] + (base >> 5)) * T : 0;
-        int steps = 0;   // MODE 1: this lane's walk steps in this pass
-        if (kFilter) {
+        int c = 0;   // accepted sources of this thread's target in its words (q, q + 4, ...)
+        if (kFilter && active) {
             // FP32 filter: one accept bit per staged source. Sources in the thin
             // band around the cutoff get a second bit and are settled afterwards
             // by the exact FP64 test, in a loop of its own so that no FP64
@@ -208,23 +215,21 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             const float2 fx2 = make_float2(fx, fx), fy2 = make_float2(fy, fy);
             for (int wi = qtr; wi < nw; wi += kMvQ) {
                 uint32_t m = 0, mh = 0;
-                if (active) {
-                    const float4* S4 = reinterpret_cast<const float4*>(SF) + wi * 16;
+                const float4* S4 = reinterpret_cast<const float4*>(SF) + wi * 16;
 #pragma unroll
-                    for (int b = 0; b < 32; b += 2) {
-                        const float4 v = S4[b >> 1];
-                        const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
-                        const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
-                        const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
-                        m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
-                        mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
-                    }
-                    const int lim = ns - wi * 32;
-                    if (lim < 32) {
-                        const uint32_t keep = (1u << lim) - 1u;
-                        m &= keep;
-                        mh &= keep;
-                    }
+                for (int b = 0; b < 32; b += 2) {
+                    const float4 v = S4[b >> 1];
+                    const float2 dx = f2_sub(fx2, make_float2(v.x, v.y));
+                    const float2 dy = f2_sub(fy2, make_float2(v.z, v.w));
+                    const float2 r2 = f2_fma(dy, dy, f2_mul(dx, dx));
+                    m |= (r2.x < rc2f_lo ? 1u << b : 0u) | (r2.y < rc2f_lo ? 2u << b : 0u);
+                    mh |= (r2.x <= rc2f_hi ? 1u << b : 0u) | (r2.y <= rc2f_hi ? 2u << b : 0u);
+                }
+                const int lim = ns - wi * 32;
+                if (lim < 32) {
+                    const uint32_t keep = (1u << lim) - 1u;
+                    m &= keep;
+                    mh &= keep;
                 }
                 uint32_t band = mh & ~m;
                 while (band != 0u) {
@@ -235,22 +240,60 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                     if (__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= rc2) m |= 1u << b;
                 }
                 MASK[wi * T + t] = m;
-                if (MODE == 1) steps += (__popc(m) + 1) >> 1;
+                c += __popc(m);
                 if (MODE == 2) FS.mask[mbase + (int64_t)wi * T + t] = m;
             }
-        } else {   // MODE 3: the stored masks of this lane's words
-            for (int wi = qtr; wi < nw; wi += kMvQ) MASK[wi * T + t] = __ldg(FS.mask + mbase + (int64_t)wi * T + t);
+        } else if (!kFilter && active) {   // MODE 3: the stored masks
+            for (int wi = qtr; wi < nw; wi += kMvQ) {
+                const uint32_t m = __ldg(FS.mask + mbase + (int64_t)wi * T + t);
+                MASK[wi * T + t] = m;
+                c += __popc(m);
+            }
         }
+        if (active) CNT[qtr * T + t] = c;
+        __syncthreads();
+        // this thread's share of its target's accepted sources in this pass:
+        // ranks [lo, hi) in source order, quarter q taking the q-th of four
+        // near-equal contiguous parts (word boundaries do not matter)
+        int lo = 0, cntq = 0;
+        if (active) {
+            int n = 0;
+#pragma unroll
+            for (int q = 0; q < kMvQ; ++q) n += CNT[q * T + t];
+            lo = (qtr * n) / kMvQ;
+            cntq = ((qtr + 1) * n) / kMvQ - lo;
+        }
+        const int steps = (cntq + 1) >> 1;   // walk steps: two sources per step
         if (MODE == 1) {
             slots += 64 * (long long)__reduce_max_sync(0xffffffffu, steps);
             continue;
         }
-        // this warp's slots in this pass: after the earlier warps' (warp
+        // the lo-th accepted source: its word wi and the word's bits from it on
+        int wi = 0;
+        uint32_t cur = 0u;
+        if (cntq > 0) {
+            int r = lo;
+            for (;;) {
+                cur = MASK[wi * T + t];
+                const int pc = __popc(cur);
+                if (r < pc) break;
+                r -= pc;
+                ++wi;
+            }
+            for (; r > 0; --r) cur &= cur - 1u;
+        }
+        // the next accepted source in order (called exactly cntq times)
+        auto next_src = [&]() -> int {
+            while (cur == 0u) cur = MASK[++wi * T + t];
+            const int i = wi * 32 + (__ffs(cur) - 1);
+            cur &= cur - 1u;
+            return i;
+        };
+        // this warp's value slots in this pass: after the earlier warps' (warp
         // order), after the block's earlier passes
         int64_t wbase = 0;
-        int wsteps = 0;   // MODE 2, 3: the warp's steps in this pass
+        int wsteps = 0;   // MODE 2, 3: the warp's steps (its busiest lane's)
         if (MODE >= 2) {
-            for (int wi = qtr; wi < nw; wi += kMvQ) steps += (__popc(MASK[wi * T + t]) + 1) >> 1;
             wsteps = __reduce_max_sync(0xffffffffu, steps);
             const long long ws = lane == 0 ? 64 * (long long)wsteps : 0LL;
             long long total = 0;
@@ -258,9 +301,8 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
             wbase = vbase + __shfl_sync(0xffffffffu, pre, 0);
             vbase += total;
         }
-        // pairs: each lane walks its own accepted sources of this quarter; the warp steps together
-        // (up to two sources of the current mask word per step: two independent
-        // evaluation chains, accumulated in source order)
+        // pairs: step s takes the share's sources 2s and 2s + 1 (two
+        // independent evaluation chains), accumulated in source order
         auto walk = [&](auto k52) {
             auto kval = [&](int idx) {
                 const long long du = (long long)((unsigned long long)xf - (unsigned long long)SXF[2 * idx]);
@@ -268,41 +310,37 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                 if constexpr (decltype(k52)::value) return kernel_fx52(du, dv, M, T1, T2);
                 else return kernel_fx(du, dv, F, M, T1, T2);
             };
-            int wi = qtr;
-            uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
-            for (int64_t at = wbase + 2 * lane;; at += 64) {   // MODE 2: this lane's slot of the step
-                while (cur == 0u && wi + kMvQ < nw) {
-                    wi += kMvQ;
-                    cur = MASK[wi * T + t];
-                }
-                const bool has = cur != 0u;
-                if (!__any_sync(0xffffffffu, has)) break;
-                if (has) {
-                    const int i0 = wi * 32 + (__ffs(cur) - 1);
-                    cur &= cur - 1u;
-                    const bool two = cur != 0u;
-                    const int i1 = two ? wi * 32 + (__ffs(cur) - 1) : i0;
-                    cur &= cur - (two ? 1u : 0u);
-                    const double k0 = kval(i0), k1 = kval(i1);
-                    if constexpr (MODE == 2) {
-                        *reinterpret_cast<double2*>(FS.val + at) = make_double2(k0, two ? k1 : 0.0);
-                    } else {
-                        acc = fma(k0, SW[i0], acc);
-                        if (two) acc = fma(k1, SW[i1], acc);
+            if constexpr (MODE == 2) {
+                // every lane writes its slot of each of the warp's steps (zeros
+                // past its own), 512 contiguous bytes per step
+                for (int st = 0; st < wsteps; ++st) {
+                    double2 v = make_double2(0.0, 0.0);
+                    if (st < steps) {
+                        const int i0 = next_src();
+                        const bool two = 2 * st + 1 < cntq;
+                        const int i1 = two ? next_src() : i0;
+                        v.x = kval(i0);
+                        if (two) v.y = kval(i1);
                     }
-                } else if constexpr (MODE == 2) {
-                    *reinterpret_cast<double2*>(FS.val + at) = make_double2(0.0, 0.0);
+                    *reinterpret_cast<double2*>(FS.val + wbase + (int64_t)st * 64 + 2 * lane) = v;
+                }
+            } else {
+                for (int st = 0; st < steps; ++st) {
+                    const int i0 = next_src();
+                    const bool two = 2 * st + 1 < cntq;
+                    const int i1 = two ? next_src() : i0;
+                    const double k0 = kval(i0), k1 = kval(i1);
+                    acc = fma(k0, SW[i0], acc);
+                    if (two) acc = fma(k1, SW[i1], acc);
                 }
             }
         };
         if constexpr (MODE == 3) {
-            // the same walk over the stored masks, its step count known: the
-            // values of kReplayAhead steps are loaded before they are used
-            // (lane l's slot of step j at 64 j + 2 l); a lane's j-th step is
-            // the walk's j-th, as when they were stored
+            // the same shares over the stored masks, the warp's step count
+            // known: the values of kReplayAhead steps are loaded before they
+            // are used (lane l's slot of step s at 64 s + 2 l), as they were
+            // stored
             const double2* vp = reinterpret_cast<const double2*>(FS.val + wbase) + lane;
-            int wi = qtr;
-            uint32_t cur = wi < nw ? MASK[wi * T + t] : 0u;
             for (int j0 = 0; j0 < wsteps; j0 += kReplayAhead) {
                 double2 kv[kReplayAhead];
 #pragma unroll
@@ -310,17 +348,12 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                     kv[k] = j0 + k < wsteps ? __ldg(vp + (int64_t)(j0 + k) * 32) : make_double2(0.0, 0.0);
 #pragma unroll
                 for (int k = 0; k < kReplayAhead; ++k) {
-                    while (cur == 0u && wi + kMvQ < nw) {
-                        wi += kMvQ;
-                        cur = MASK[wi * T + t];
-                    }
-                    if (cur != 0u) {
-                        const int i0 = wi * 32 + (__ffs(cur) - 1);
-                        cur &= cur - 1u;
+                    const int st = j0 + k;
+                    if (st < steps) {
+                        const int i0 = next_src();
                         acc = fma(kv[k].x, SW[i0], acc);
-                        if (cur != 0u) {
-                            const int i1 = wi * 32 + (__ffs(cur) - 1);
-                            cur &= cur - 1u;
+                        if (2 * st + 1 < cntq) {
+                            const int i1 = next_src();
                             acc = fma(kv[k].y, SW[i1], acc);
                         }
                     }
@@ -336,9 +369,9 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         block_excl_scan(lane == 0 ? slots : 0LL, scan_sh, total);
         if (tid == 0) FS.cnt[item] = total;
     } else if constexpr (MODE == 0 || MODE == 3) {
-        PART[qtr * T + t] = acc;
+        if (active) PART[qtr * T + t] = acc;
         __syncthreads();
-        if (qtr == 0 && active) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
+        if (active && qtr == 0) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
     }
 }
 
