@@ -64,14 +64,14 @@ SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
 FP64_DFMA_PEAK_PAIRS = SM_COUNT * 2 * SM_CLOCK_HZ
 ISSUE_PEAK_LANE_INSTR = SM_COUNT * 4 * 32 * SM_CLOCK_HZ
 F64_ISSUE_BUDGET_PER_PAIR = 92.0
-MATVEC_F64_REV = "fixed-point-v5"
+MATVEC_F64_REV = "fixed-point-v6"
 # DRAM read + write of one launch on the 1024 x 1024 lattice (ncu, this revision)
-MATVEC_F64_TRAFFIC = {"fixed-point-v5": 37_978_112}
+MATVEC_F64_TRAFFIC = {"fixed-point-v5": 37_978_112, "fixed-point-v6": 38_016_427}
 FLOPS_PER_PAIR_F64 = 26   # FP64-equivalent flops of one pair (dx, dy 2; r2 3; argument 1; exp 18; accumulate 2)
 # The replay of kept pair values (RBF_OPT_STORE_F64) reads, per launch, the
 # values and masks (rbf_store_f64_bytes) plus w and y (16 B per point), and
 # issues one DFMA per pair: bound by the larger of the two times.
-MATVEC_F64_REPLAY_REV = "replay-v2"
+MATVEC_F64_REPLAY_REV = "replay-v3"
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -192,6 +192,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-precision measurement")
+    ap.add_argument("--no-store", action="store_true",
+                    help="keep no FP64 pair values: every FP64 product evaluates its pairs")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of a single-problem line")
     ap.add_argument("--serve-requests", type=int, default=16, help="requests of the short serving run")
     ap.add_argument("--window", type=int, default=0,
@@ -442,6 +444,8 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     ctx = rbf.Context(local)
     h = ctx.handle
+    if args.no_store:   # every FP64 product evaluates its pairs (nothing kept)
+        rbf.rbf_set_option(h, rbf.RBF_OPT_STORE_F64, 0)
 
     def step(c):
         w.zero_()
@@ -609,7 +613,8 @@ def run_ours(args, ws, rank, local):
         out = {"metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64" if mode == "f64" else "f32-inner/f64-outer", "data": "synthetic",
-               "config": {**workload_config(name, p, mode, args.inner_cutoff), "tuned": tuned},
+               "config": {**workload_config(name, p, mode, args.inner_cutoff), "tuned": tuned,
+                          "fp64_products": "replay kept values" if store_bytes else "evaluated"},
                "value_is": f"{mode} solve (bin + RASM setup + GMRES) to relres 1e-13, mean of the timed steps",
                "ok": ok, "solve": info, "step_ms": [round(t, 3) for t in times], "roofline": roofline,
                "roofline_f64_matvec": roof64, "breakdown_ms": breakdown, "rasm_factors": factors,

@@ -458,7 +458,7 @@ enum {
     RBF_OPT_STREAM_WAIT_CHECK = 7,
     /* 1 (default): at the start of a solve, the FP64 matvec's accept masks and
      * kernel values of the current binning are computed once and kept in
-     * device memory (about 10.7 B per in-cutoff pair: 8 B values in slots
+     * device memory (about 8.9 B per in-cutoff pair: 8 B values in slots
      * padded to the walk's warp steps, and the masks; 363 pairs per point at
      * h/sigma = 0.8), if they fit in the device's free memory less 8 GiB and in
      * the context's memory limit; the FP64 products then read them instead of

@@ -63,7 +63,7 @@ __host__ __device__ constexpr size_t mv64_smem(int T, int S)
 // contiguous bytes per warp. A warp takes, per pass, as many steps as its
 // busiest lane: ceil(share / 2), its share being a quarter of its target's
 // accepted sources in the pass.
-constexpr int kReplayAhead = 4;   // replay: walk steps whose values are in flight together
+constexpr int kReplayAhead = 3;   // replay: walk steps whose values are in flight
 
 struct F64Store {
     int64_t* cnt;               // MODE 1: value slots of each item (doubles, a multiple of 64)
@@ -337,24 +337,27 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         };
         if constexpr (MODE == 3) {
             // the same shares over the stored masks, the warp's step count
-            // known: the values of kReplayAhead steps are loaded before they
-            // are used (lane l's slot of step s at 64 s + 2 l), as they were
-            // stored
+            // known: a ring of kReplayAhead loads stays in flight, the load of
+            // step s + kReplayAhead issued as step s's value is taken (lane
+            // l's slot of step s at 64 s + 2 l, as they were stored)
             const double2* vp = reinterpret_cast<const double2*>(FS.val + wbase) + lane;
-            for (int j0 = 0; j0 < wsteps; j0 += kReplayAhead) {
-                double2 kv[kReplayAhead];
+            double2 kv[kReplayAhead];
 #pragma unroll
-                for (int k = 0; k < kReplayAhead; ++k)
-                    kv[k] = j0 + k < wsteps ? __ldg(vp + (int64_t)(j0 + k) * 32) : make_double2(0.0, 0.0);
+            for (int k = 0; k < kReplayAhead; ++k)
+                kv[k] = k < wsteps ? __ldg(vp + (int64_t)k * 32) : make_double2(0.0, 0.0);
+            for (int j0 = 0; j0 < wsteps; j0 += kReplayAhead) {
 #pragma unroll
                 for (int k = 0; k < kReplayAhead; ++k) {
                     const int st = j0 + k;
+                    const double2 v = kv[k];
+                    const int nx = st + kReplayAhead;
+                    kv[k] = nx < wsteps ? __ldg(vp + (int64_t)nx * 32) : make_double2(0.0, 0.0);
                     if (st < steps) {
                         const int i0 = next_src();
-                        acc = fma(kv[k].x, SW[i0], acc);
+                        acc = fma(v.x, SW[i0], acc);
                         if (2 * st + 1 < cntq) {
                             const int i1 = next_src();
-                            acc = fma(kv[k].y, SW[i1], acc);
+                            acc = fma(v.y, SW[i1], acc);
                         }
                     }
                 }
