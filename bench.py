@@ -644,7 +644,8 @@ def batch_config(args, probs, mode: str) -> dict:
             "rasm": "4x4 lattice-point cores + 1-point ring", "gmres_restart": 30, "rtol": 1e-13,
             "max_iters_per_problem": args.max_iters, "precision": mode,
             "inner_cutoff_sigmas": args.inner_cutoff if mode == "mixed" else None,
-            "l2": "flushed (256 MB write) before each timed step", "parallelism": "replicas"}
+            "l2": "flushed (256 MB write) before each timed step", "parallelism": "replicas",
+            "fp64_products": "evaluated" if args.no_store else "kept values replayed while every problem runs"}
 
 
 def batch_summary(probs, infos, stats_w=None) -> dict:
@@ -757,6 +758,8 @@ def run_batch(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     ctx = rbf.Context(local)
     h = ctx.handle
+    if args.no_store:   # every FP64 product evaluates its pairs (nothing kept)
+        rbf.rbf_set_option(h, rbf.RBF_OPT_STORE_F64, 0)
 
     def sparams(md):
         return rbf.RbfSolveParams(1e-13, 30, args.max_iters, int(md == "mixed"), args.max_iters, 1e-5,
