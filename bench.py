@@ -477,7 +477,7 @@ def run_ours(args, ws, rank, local):
     dominant = rbf.RBF_PROF_MATVEC_F64 if mode == "f64" else rbf.RBF_PROF_MATVEC_F32
     rbf.rbf_profile_classes(h, 1 << dominant)
     rbf.rbf_profile_enable(h, True)
-    for k in range(6):
+    for k in range(rbf.RBF_PROF_COUNT):
         rbf.rbf_profile_read(h, k)   # discard warm-up records
     launches0 = ctx.launches
     clocks = ClockSampler(local)
@@ -489,12 +489,12 @@ def run_ours(args, ws, rank, local):
         outs.append(r)
     clk = clocks.stop()
     launches = ctx.launches - launches0
-    prof = {k: rbf.rbf_profile_read(h, k) for k in range(6)}
+    prof = {k: rbf.rbf_profile_read(h, k) for k in range(rbf.RBF_PROF_COUNT)}
     rbf.rbf_profile_classes(h, 0xFFFFFFFF)
     flush.zero_()
     step(cfg)                             # the breakdown step (untimed, every class recorded)
     torch.cuda.synchronize()
-    prof_all = {k: rbf.rbf_profile_read(h, k) for k in range(6)}
+    prof_all = {k: rbf.rbf_profile_read(h, k) for k in range(rbf.RBF_PROF_COUNT)}
     rbf.rbf_profile_enable(h, False)
     ms = max_over_ranks(statistics.mean(times), dist, "cuda")
     stats = [st for st, _ in outs]
@@ -542,7 +542,7 @@ def run_ours(args, ws, rank, local):
             roof64 = f64_matvec_roofline(pairs, t64 / n64 / 1e3, n64, None, note=note)
     breakdown = {nm: {"launches": prof_all[k][0], "ms": round(prof_all[k][1], 3)} for nm, k in
                  (("matvec_f64", 0), ("matvec_f32", 1), ("rasm_apply", 2), ("orthogonalisation", 3),
-                  ("rasm_setup", 4), ("binning", 5))}
+                  ("rasm_setup", 4), ("binning", 5), ("fp64_values_kept", 6))}
     tc, f64 = rbf.rbf_rasm_factor_counts(h)
     factors = {"precision": "fp32 tensor cores" if mode == "mixed" else "fp64", "tensor_core_subdomains": tc,
                "fp64_subdomains": f64}
@@ -806,7 +806,7 @@ def run_batch(args, ws, rank, local):
 
     # FP64 matvec over the whole batch (every problem active), kernel time from the profiler
     rbf.rbf_profile_enable(h, True)
-    for k in range(6):
+    for k in range(rbf.RBF_PROF_COUNT):
         rbf.rbf_profile_read(h, k)
     y = torch.empty_like(w)
     for _ in range(5):

@@ -365,7 +365,9 @@ enum {
     RBF_PROF_ORTHO = 3,        /* one Arnoldi orthogonalisation (three passes over V + reductions) */
     RBF_PROF_RASM_SETUP = 4,   /* subdomain factor/inverse launch */
     RBF_PROF_BIN = 5,          /* the whole binning sequence */
-    RBF_PROF_COUNT = 6
+    RBF_PROF_STORE_F64 = 6,    /* counting and keeping the FP64 pair values (RBF_OPT_STORE_F64), with the
+                                  product a mixed solve's first outer residual needs formed in the same pass */
+    RBF_PROF_COUNT = 7
 };
 /* enable != 0: record a CUDA event pair on the launching stream around every
  * launch of the classes above (a fixed cost of two event records each). */
@@ -456,13 +458,14 @@ enum {
      * wait on a barrier that no copy completes (and copy nothing), so that it
      * runs out and the solve returns RBF_ERR_TIMEOUT. */
     RBF_OPT_STREAM_WAIT_CHECK = 7,
-    /* 1 (default): at the start of a solve, the FP64 matvec's accept masks and
-     * kernel values of the current binning are computed once and kept in
-     * device memory (about 8.9 B per in-cutoff pair: 8 B values in slots
+    /* 1 (default): the FP64 matvec's accept masks and kernel values of the
+     * current binning are computed once (at the start of an FP64 solve; with
+     * the first outer residual product of a mixed solve, which that pass forms
+     * as well) and kept in device memory (about 8.9 B per in-cutoff pair: 8 B values in slots
      * padded to the walk's warp steps, and the masks; 363 pairs per point at
      * h/sigma = 0.8), if they fit in the device's free memory less 8 GiB and in
      * the context's memory limit; the FP64 products then read them instead of
-     * evaluating the kernel, with the same sums bit for bit. Recomputed at
+     * evaluating the kernel, with the same sums bit for bit. Recomputed in
      * the first solve after each binning; freed by rbf_destroy or by setting
      * 0. Not used by the symmetric FP64 kernel (RBF_OPT_SYMMETRIC_F64), by a
      * batched solve once some of its problems have stopped (their products

@@ -352,7 +352,10 @@ rbf_status matvec_sorted_f64_plain(rbf_ctx* ctx, const double* w, double* y, cud
 // Computes and keeps the FP64 matvec's accept masks and pair values of the
 // current binning when the store is enabled and they fit in free memory (the
 // following FP64 products replay them, bit for bit); a no-op otherwise.
-rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st);
+rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st);   // keep the FP64 pair values (no product)
+// y = A~ w (cell order), keeping the FP64 pair values in the same pass when
+// they are not kept yet and may be (matvec_sorted_f64 otherwise)
+rbf_status matvec_sorted_f64_keep(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st);
 void f64_store_release(rbf_ctx* ctx);   // frees the kept values (the small per-item tables stay)
 // The FP64 kernel for targets binned by bin_targets (cell-sorted; s in target order).
 rbf_status eval_sorted_f64(rbf_ctx* ctx, const double* txy, const float* tloc, const int32_t* tcell_start,

@@ -748,9 +748,12 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     std::vector<int32_t> act(nprob, 1), zmask(nprob, 0);
     RBF_CUDA(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int32_t) * nprob, cudaMemcpyHostToDevice, st));
 
-    // the FP64 products of this solve replay kept pair values when they fit
-    // (computed here, before any cycle is captured)
-    RBF_CHECK(f64_store_prepare(ctx, st));
+    // the FP64 products of this solve replay kept pair values when they fit:
+    // an FP64 solve keeps them here, before any cycle (whose products they
+    // serve) is captured; a mixed solve keeps them with its first outer
+    // residual product, which they then form as well (outside the captured
+    // inner cycles)
+    if (!mixed) RBF_CHECK(f64_store_prepare(ctx, st));
     int max_chunks = 0;
     for (int b = 0; b < nprob; ++b) max_chunks = std::max(max_chunks, cptr[b + 1] - cptr[b]);
     BatchWork B{ctx, st, C, nprob, gm, active, run, ctx->partial.p, false, ctx->pid.p, n,
@@ -848,7 +851,7 @@ rbf_status gmres_solve_batch(rbf_ctx* ctx, const double* f, double* w, const rbf
     bool w_zero = w_nonzero == 0;
     for (;;) {
         // true FP64 residual of the active problems
-        if (!w_zero) RBF_CHECK(matvec_sorted_f64(ctx, w, ctx->vec_a.p, st));
+        if (!w_zero) RBF_CHECK(matvec_sorted_f64_keep(ctx, w, ctx->vec_a.p, st));
         RBF_LAUNCH(ctx, k_bresidual, (unsigned)B.C.nc, kDotThreads, 0, st, f, w_zero ? nullptr : ctx->vec_a.p, r64,
                    B.C, active, B.partial);
         RBF_LAUNCH(ctx, k_breduce, (unsigned)nprob, 32 * B.red_warps, 0, st, B.partial, B.C, nprob, 1, gm, F_BETA2,

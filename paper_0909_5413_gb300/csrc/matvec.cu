@@ -54,9 +54,10 @@ __host__ __device__ constexpr size_t mv64_smem(int T, int S)
 
 // The FP64 matvec's pair values kept in device memory: MODE 1 counts, per work
 // item of the full list, its value slots and its 32-source words; MODE 2
-// stores the accept masks and the kernel values; MODE 3 replays the matvec
-// from them: the same values, the same sums, bit for bit, without the filter
-// or the kernel evaluations. The values are laid out for the lockstep walk
+// stores the accept masks and the kernel values (MODE 4 also forms the product
+// with them, as MODE 0 would); MODE 3 replays the matvec from them: the same
+// values, the same sums, bit for bit, without the filter or the kernel
+// evaluations. The values are laid out for the lockstep walk
 // below: per pass, per warp, per step of the walk, 64 doubles, lane l's one or
 // two values of that step at 2l and 2l + 1 (a slot of a lane with nothing at
 // that step is written as zeros and never read), so that a step loads 512
@@ -109,8 +110,10 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                                                                  double* __restrict__ y, F64Store FS)
 {
     constexpr int kThreads = T * kMvQ;
-    constexpr bool kEval = MODE == 0 || MODE == 2;   // kernel values computed here
-    constexpr bool kFilter = MODE <= 2;              // accept masks computed here
+    constexpr bool kEval = MODE == 0 || MODE == 2 || MODE == 4;   // kernel values computed here
+    constexpr bool kFilter = MODE != 3;                            // accept masks computed here
+    constexpr bool kStore = MODE == 2 || MODE == 4;                // masks and values written
+    constexpr bool kSum = MODE == 0 || MODE == 3 || MODE == 4;     // the product formed
     const int kStage = P.stage;
     extern __shared__ unsigned long long smem_u64[];
     unsigned long long* T1 = smem_u64;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                 SF[4 * (idx >> 1) + (idx & 1)] = P.loc[2 * q] + (float)(cq % ncx - cx) * ca;
                 SF[4 * (idx >> 1) + 2 + (idx & 1)] = P.loc[2 * q + 1] + (float)(cq / ncx - cy) * ca;
             }
-            if (MODE == 0 || MODE == 3) SW[idx] = w[q];
+            if (kSum) SW[idx] = w[q];
         }
         __syncthreads();
         const int nw = (ns + 31) >> 5;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                 }
                 MASK[wi * T + t] = m;
                 c += __popc(m);
-                if (MODE == 2) FS.mask[mbase + (int64_t)wi * T + t] = m;
+                if (kStore) FS.mask[mbase + (int64_t)wi * T + t] = m;
             }
         } else if (!kFilter && active) {   // MODE 3: the stored masks
             for (int wi = qtr; wi < nw; wi += kMvQ) {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         // this warp's value slots in this pass: after the earlier warps' (warp
         // order), after the block's earlier passes
         int64_t wbase = 0;
-        int wsteps = 0;   // MODE 2, 3: the warp's steps (its busiest lane's)
+        int wsteps = 0;   // MODE 2, 3, 4: the warp's steps (its busiest lane's)
         if (MODE >= 2) {
             wsteps = __reduce_max_sync(0xffffffffu, steps);
             const long long ws = lane == 0 ? 64 * (long long)wsteps : 0LL;
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                 if constexpr (decltype(k52)::value) return kernel_fx52(du, dv, M, T1, T2);
                 else return kernel_fx(du, dv, F, M, T1, T2);
             };
-            if constexpr (MODE == 2) {
+            if constexpr (kStore) {
                 // every lane writes its slot of each of the warp's steps (zeros
                 // past its own), 512 contiguous bytes per step
                 for (int st = 0; st < wsteps; ++st) {
@@ -321,6 +324,10 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
                         const int i1 = two ? next_src() : i0;
                         v.x = kval(i0);
                         if (two) v.y = kval(i1);
+                        if constexpr (MODE == 4) {   // the sums of MODE 0
+                            acc = fma(v.x, SW[i0], acc);
+                            if (two) acc = fma(v.y, SW[i1], acc);
+                        }
                     }
                     *reinterpret_cast<double2*>(FS.val + wbase + (int64_t)st * 64 + 2 * lane) = v;
                 }
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(T * kMvQ, 256 / T) k_matvec_f64(MvParams P, co
         long long total = 0;
         block_excl_scan(lane == 0 ? slots : 0LL, scan_sh, total);
         if (tid == 0) FS.cnt[item] = total;
-    } else if constexpr (MODE == 0 || MODE == 3) {
+    } else if constexpr (kSum) {
         if (active) PART[qtr * T + t] = acc;
         __syncthreads();
         if (active && qtr == 0) y[p] = (((PART[t] + PART[T + t]) + PART[2 * T + t]) + PART[3 * T + t]) * knorm;
@@ -787,7 +794,8 @@ rbf_status prepare_f64(rbf_ctx* ctx)
     RBF_CHECK((prepare_f64_mode<T, 0>(ctx)));
     RBF_CHECK((prepare_f64_mode<T, 1>(ctx)));
     RBF_CHECK((prepare_f64_mode<T, 2>(ctx)));
-    return prepare_f64_mode<T, 3>(ctx);
+    RBF_CHECK((prepare_f64_mode<T, 3>(ctx)));
+    return prepare_f64_mode<T, 4>(ctx);
 }
 
 template <int T, int MODE>
@@ -921,12 +929,20 @@ void f64_store_release(rbf_ctx* ctx)
     K.mask = {};
 }
 
-rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st)
+namespace {
+
+// Counts and keeps the pair values of the current binning when they fit; with
+// w, forms y = A~ w from them in the same pass (*formed). Nothing is kept, and
+// *formed stays false, when the option is off, the values are kept already,
+// the symmetric FP64 kernel serves the products, a cycle is being captured, or
+// (with w) a batched solve runs on the lists of its active problems.
+rbf_status f64_store_build(rbf_ctx* ctx, const double* w, double* y, bool* formed, cudaStream_t st)
 {
+    *formed = false;
     F64Keep& K = ctx->f64s;
     if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64) || ctx->n_work == 0) return RBF_OK;
     if (ctx->sym64 && ctx->sym64_mode == 0) return RBF_OK;   // the symmetric kernel serves those problems
-    if (ctx->capturing) return RBF_OK;
+    if (ctx->capturing || (w && ctx->al.on)) return RBF_OK;
     K.valid = false;
     const int64_t nwork = ctx->n_work;
     MvParams P = mv_params(ctx);
@@ -967,11 +983,41 @@ rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st)
     FS.mask_off = K.mask_off.p;
     FS.val = K.val.p;
     FS.mask = K.mask.p;
-    RBF_CHECK(dispatch_f64_mode<2>(ctx, P, nwork, nullptr, nullptr, FS, st));
+    if (w) {
+        RBF_CHECK(dispatch_f64_mode<4>(ctx, P, nwork, w, y, FS, st));
+        *formed = true;
+    } else {
+        RBF_CHECK(dispatch_f64_mode<2>(ctx, P, nwork, nullptr, nullptr, FS, st));
+    }
     K.valid = true;
     K.tile = ctx->tile64;
     K.bytes = (int64_t)need;
     return RBF_OK;
+}
+
+rbf_status f64_store_build_timed(rbf_ctx* ctx, const double* w, double* y, bool* formed, cudaStream_t st)
+{
+    *formed = false;
+    const F64Keep& K = ctx->f64s;
+    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64)) return RBF_OK;   // nothing to time
+    RBF_CHECK(prof_begin(ctx, RBF_PROF_STORE_F64, st));
+    RBF_CHECK(f64_store_build(ctx, w, y, formed, st));
+    return prof_end(ctx, RBF_PROF_STORE_F64, st);
+}
+
+}  // namespace
+
+rbf_status f64_store_prepare(rbf_ctx* ctx, cudaStream_t st)
+{
+    bool formed = false;
+    return f64_store_build_timed(ctx, nullptr, nullptr, &formed, st);
+}
+
+rbf_status matvec_sorted_f64_keep(rbf_ctx* ctx, const double* w, double* y, cudaStream_t st)
+{
+    bool formed = false;
+    RBF_CHECK(f64_store_build_timed(ctx, w, y, &formed, st));
+    return formed ? RBF_OK : matvec_sorted_f64(ctx, w, y, st);
 }
 
 // s = sum_j k(|t - x_j|) w_j for the cell-sorted targets of another point

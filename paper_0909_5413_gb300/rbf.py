@@ -38,8 +38,9 @@ RBF_OPT_FUSED_STEP, RBF_OPT_SYMMETRIC_F32, RBF_OPT_BARRIER_SPIN_LIMIT, RBF_OPT_B
 RBF_OPT_SYMMETRIC_F64 = 5
 RBF_OPT_STREAM_GS, RBF_OPT_STREAM_WAIT_CHECK, RBF_OPT_STORE_F64 = 6, 7, 8
 
-RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN = \
-    range(6)
+RBF_PROF_MATVEC_F64, RBF_PROF_MATVEC_F32, RBF_PROF_RASM_APPLY, RBF_PROF_ORTHO, RBF_PROF_RASM_SETUP, RBF_PROF_BIN, \
+    RBF_PROF_STORE_F64 = range(7)
+RBF_PROF_COUNT = 7
 
 
 class RbfParams(C.Structure):

@@ -170,3 +170,44 @@ def test_switching_the_store_off_frees_it(rbf):
     np.testing.assert_array_equal(host(y0), host(y1))
     np.testing.assert_array_equal(host(w), host(w1))
     ctx.close()
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_where_the_values_are_kept(rbf, mixed):
+    """A mixed solve keeps the values with its first outer residual product
+    (formed in the same pass: one record of the profiler's store class, the
+    other outer products replays); an FP64 solve keeps them at its start."""
+    p = W.lattice_problem(100, 0.8, seed=990, rhs="four_gaussians")
+    cfg = rbf.config_for(p, mixed=mixed, factor_precision=rbf.RBF_FP32 if mixed else rbf.RBF_FP64,
+                         inner_cutoff=6.1 if mixed else 0.0)
+    ctx = rbf.Context(0)
+    h = ctx.handle
+    rbf.rbf_set_option(h, rbf.RBF_OPT_FUSED_STEP, 0)
+    rbf.rbf_profile_enable(h, True)
+    ctx.bin(dev(p.xy), cfg)
+    ctx.rasm_setup(cfg)
+    for k in range(rbf.RBF_PROF_COUNT):
+        rbf.rbf_profile_read(h, k)   # only the solve's records below
+    w = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+    assert st == 0
+    n_keep, t_keep = rbf.rbf_profile_read(h, rbf.RBF_PROF_STORE_F64)
+    n_mv, _ = rbf.rbf_profile_read(h, rbf.RBF_PROF_MATVEC_F64)
+    assert n_keep == 1 and t_keep > 0.0
+    assert rbf.rbf_store_f64_bytes(h) >= 8 * rbf.rbf_count_pairs(h, 0)
+    if mixed:
+        outer = info.matvecs - info.iters   # w0 = 0: r0 = f needs no product
+        assert outer == info.refinements >= 2
+        assert n_mv == outer - 1
+    # a second solve on the same binning keeps nothing more: every outer
+    # product of a mixed solve is a replay
+    w.zero_()
+    st, info = ctx.solve(dev(p.f), w, cfg, check=False)
+    assert st == 0
+    n_keep, _ = rbf.rbf_profile_read(h, rbf.RBF_PROF_STORE_F64)
+    n_mv, _ = rbf.rbf_profile_read(h, rbf.RBF_PROF_MATVEC_F64)
+    assert n_keep == 0
+    if mixed:
+        assert n_mv == info.matvecs - info.iters
+    rbf.rbf_profile_enable(h, False)
+    ctx.close()
