@@ -471,7 +471,8 @@ enum {
      * batched solve once some of its problems have stopped (their products
      * run on lists of the active problems' items), or by a solve under
      * stream capture; an allocation that fails leaves the solve matrix-free.
-     * 0: never (matrix-free). */
+     * Values that did not fit are not tried again for the same binning until
+     * this option or the memory limit is set again. 0: never (matrix-free). */
     RBF_OPT_STORE_F64 = 8
 };
 /* Set a context option. INVALID_ARG for an unknown option or value. */

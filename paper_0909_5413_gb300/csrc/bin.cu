@@ -504,6 +504,7 @@ rbf_status select_work_into(rbf_ctx* ctx, const int32_t* work, int64_t nwork, co
 rbf_status bin_points(rbf_ctx* ctx, const double* xy, cudaStream_t st)
 {
     ctx->f64s.valid = false;   // the kept pair values belong to the previous binning
+    ctx->f64s.tried = false;
     const int64_t n = ctx->n;
     const int nprob = (int)ctx->nprob;
     std::vector<Prob>& P = ctx->prob_h;

@@ -315,6 +315,7 @@ rbf_status rbf_set_option(rbf_ctx* ctx, int option, int64_t value)
         if (value != 0 && value != 1) break;
         ctx->store_mode = (int)value;
         if (value == 0) f64_store_release(ctx);
+        ctx->f64s.tried = false;
         return RBF_OK;
     default:
         return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_option: unknown option %d", option);
@@ -328,6 +329,7 @@ rbf_status rbf_set_memory_limit(rbf_ctx* ctx, int64_t bytes)
     if (!ctx) return RBF_ERR_INVALID_ARG;
     if (bytes < 0) return fail(ctx, RBF_ERR_INVALID_ARG, "rbf_set_memory_limit: negative limit");
     ctx->mem_limit = bytes;
+    ctx->f64s.tried = false;   // the kept FP64 values may fit now
     return RBF_OK;
 }
 

@@ -75,6 +75,7 @@ struct Prob {
 // order its walk takes them (per work item of the full list).
 struct F64Keep {
     bool valid = false;
+    bool tried = false;   // did not fit for the current binning and settings: not tried again
     int tile = 0;
     int64_t bytes = 0;   // values and masks of the current binning
     rbf::DevArray<int64_t> cnt, nwords, val_off, mask_off;

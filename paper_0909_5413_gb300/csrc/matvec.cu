@@ -940,7 +940,7 @@ rbf_status f64_store_build(rbf_ctx* ctx, const double* w, double* y, bool* forme
 {
     *formed = false;
     F64Keep& K = ctx->f64s;
-    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64) || ctx->n_work == 0) return RBF_OK;
+    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64) || K.tried || ctx->n_work == 0) return RBF_OK;
     if (ctx->sym64 && ctx->sym64_mode == 0) return RBF_OK;   // the symmetric kernel serves those problems
     if (ctx->capturing || (w && ctx->al.on)) return RBF_OK;
     K.valid = false;
@@ -970,12 +970,17 @@ rbf_status f64_store_build(rbf_ctx* ctx, const double* w, double* y, bool* forme
     RBF_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
     const size_t have = (K.val.count * sizeof(double) + K.mask.count * sizeof(uint32_t));
     const size_t margin = (size_t)8 << 30;
-    if (need > have && need - have + margin > free_b) return RBF_OK;
-    if (ctx->mem_limit > 0 && ctx->dev_bytes + (int64_t)(need > have ? need - have : 0) > ctx->mem_limit) return RBF_OK;
+    const bool fits = !(need > have && need - have + margin > free_b) &&
+                      !(ctx->mem_limit > 0 && ctx->dev_bytes + (int64_t)(need > have ? need - have : 0) > ctx->mem_limit);
+    if (!fits) {
+        K.tried = true;   // the later products of this binning stay matrix-free without counting again
+        return RBF_OK;
+    }
     // an allocation that fails all the same (the device shared with another
     // process) leaves the matvec matrix-free rather than failing the solve
     if (ensure(ctx, K.val, (size_t)tot[0]) != RBF_OK || ensure(ctx, K.mask, (size_t)nmask) != RBF_OK) {
         f64_store_release(ctx);
+        K.tried = true;
         return RBF_OK;
     }
     FS = F64Store{};
@@ -999,7 +1004,7 @@ rbf_status f64_store_build_timed(rbf_ctx* ctx, const double* w, double* y, bool*
 {
     *formed = false;
     const F64Keep& K = ctx->f64s;
-    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64)) return RBF_OK;   // nothing to time
+    if (ctx->store_mode == 0 || (K.valid && K.tile == ctx->tile64) || K.tried) return RBF_OK;   // nothing to time
     RBF_CHECK(prof_begin(ctx, RBF_PROF_STORE_F64, st));
     RBF_CHECK(f64_store_build(ctx, w, y, formed, st));
     return prof_end(ctx, RBF_PROF_STORE_F64, st);
