@@ -62,6 +62,21 @@ def test_binding_return_types_follow_the_header(lib):
     assert seen == len(header_functions())
 
 
+def test_binding_constants_follow_the_header():
+    """Options, profiler classes, precisions and status codes: the values the
+    binding passes are the header's."""
+    from paper_0909_5413_gb300 import rbf
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {name: int(val) for name, val in re.findall(r"\b(RBF_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    assert len(consts) >= 28
+    for name, val in consts.items():
+        if name.startswith(("RBF_OPT_", "RBF_PROF_", "RBF_FP")):
+            assert getattr(rbf, name) == val, name
+        else:   # status codes
+            assert rbf.STATUS_NAMES[val] == name, name
+    assert len(rbf.STATUS_NAMES) == sum(1 for n in consts if not n.startswith(("RBF_OPT_", "RBF_PROF_", "RBF_FP")))
+
+
 def test_status_strings(lib):
     from paper_0909_5413_gb300 import rbf
     assert rbf.rbf_status_string(0) == "ok"
