@@ -72,6 +72,9 @@ FLOPS_PER_PAIR_F64 = 26   # FP64-equivalent flops of one pair (dx, dy 2; r2 3; a
 # values and masks (rbf_store_f64_bytes) plus w and y (16 B per point), and
 # issues one DFMA per pair: bound by the larger of the two times.
 MATVEC_F64_REPLAY_REV = "replay-v3"
+# DRAM read + write of one replay on the 1024 x 1024 lattice (ncu, this revision) and the
+# in-cutoff pairs it replayed: scaled to another workload by its pairs
+MATVEC_F64_REPLAY_TRAFFIC = {"replay-v3": (3_378_374_981, 375_552_506)}
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -96,10 +99,17 @@ def f64_replay_roofline(pairs: int, n: int, store_bytes: int, avg_s: float, laun
            "frac": t_dfma / avg_s,
            "peak_note": "FP64 pipe: one DFMA per in-cutoff pair, 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     main, other = (hbm, alu) if t_hbm >= t_dfma else (alu, hbm)
-    out = {"kernel": "k_matvec_f64 (replay of the kept pair values)", **main, "traffic": None,
+    traffic = None
+    if MATVEC_F64_REPLAY_REV in MATVEC_F64_REPLAY_TRAFFIC:
+        t_cap, pairs_cap = MATVEC_F64_REPLAY_TRAFFIC[MATVEC_F64_REPLAY_REV]
+        traffic = t_cap * pairs / pairs_cap
+    out = {"kernel": "k_matvec_f64 (replay of the kept pair values)", **main, "traffic": traffic,
            "other_bound": other, "kernel_rev": MATVEC_F64_REPLAY_REV, "pairs_per_launch": pairs,
            "algorithmic_bytes_per_launch": nbytes, "store_bytes": store_bytes,
            "store_bytes_per_pair": store_bytes / pairs, "avg_launch_ms": avg_s * 1e3, "launches": launches}
+    if traffic is not None:
+        out["traffic_note"] = ("ncu DRAM read + write of one replay on the 1024 x 1024 lattice (3.378 GB, "
+                               "1.00x its algorithmic bytes) x in-cutoff pairs / 375,552,506")
     if note:
         out["note"] = note
     return out

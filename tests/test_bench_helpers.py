@@ -47,7 +47,11 @@ def test_f64_replay_roofline_takes_the_larger_bound():
     assert abs(r["frac"] - 0.5) < 1e-9
     assert abs(r["achieved"] / r["peak"] - r["frac"]) < 1e-9
     assert r["other_bound"]["bound"] == "alu" and abs(r["other_bound"]["frac"] - 0.25) < 1e-9
-    assert r["algorithmic_bytes_per_launch"] == store + 16 * n and r["traffic"] is None
+    assert r["algorithmic_bytes_per_launch"] == store + 16 * n
+    # the measured traffic, scaled by pairs: at least the 8 B value of each pair
+    t_cap, pairs_cap = bench.MATVEC_F64_REPLAY_TRAFFIC[bench.MATVEC_F64_REPLAY_REV]
+    assert t_cap >= 8 * pairs_cap
+    assert abs(r["traffic"] - t_cap * pairs / pairs_cap) < 1.0
     # few bytes: the FP64 pipe bounds it
     r = bench.f64_replay_roofline(pairs, n, 8 * n, 2 * dfma_s, 7)
     assert r["bound"] == "alu" and abs(r["frac"] - 0.5) < 1e-9 and r["other_bound"]["bound"] == "hbm"
